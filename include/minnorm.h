@@ -1,0 +1,210 @@
+/*
+ * minnorm.h -- C ABI of the GB300 (sm_103a) randomized minimal-norm solver.
+ *
+ * Computes x ~ p, the minimal-Euclidean-norm solution of A p = b for a
+ * full-rank complex A (m x n, m < n), with ||x - p|| <= eps ||p||, by the
+ * algorithm of M. Tygert, "A fast algorithm for computing minimal-norm
+ * solutions to underdetermined systems of linear equations" (arXiv:0905.4745):
+ *   Step 1 (Eq. randmat)   Y = T A^*, T the l x n SRFT of Section 3
+ *                           (Eqs. SRFT, SRFT2, Rokhlin_trans, big_def);
+ *   Step 2 (Eq. lineq)     the pivoted Householder QR  Y P = Q R;
+ *   Steps 3-4 (Eq. overdet) conjugate gradients preconditioned by R, one
+ *                           A^* w and one A v pass over A per iteration;
+ *   Step 5 (Eq. output)    x = A^* y.
+ * Steps 2-3 enter only through R and P: since A c = b (Lemma 5.1, Eq. easy),
+ * the CG of Step 4 runs on (R^{-*} P^T A A^* P R^{-1}) u = R^{-*} P^T b and
+ * never forms z or c. An outer refinement loop with double-double residuals
+ * (an extension of Remark 4.2's extra CG iterations) reaches eps below the
+ * FP64 limit kappa * 2^-53.
+ *
+ * Conventions (every entry point):
+ *   - "device" pointers are CUDA device (or managed) memory on the plan's
+ *     device; "host" pointers are ordinary host memory. The caller owns every
+ *     buffer it passes; the plan owns its own workspace (allocated by
+ *     minnorm_plan_create, freed by minnorm_plan_destroy). No other entry point
+ *     allocates device memory except minnorm_solve_host (see there).
+ *   - complex arrays are interleaved (re, im) pairs: complex128 = 2 doubles,
+ *     complex64 = 2 floats, i.e. the layout of C99 `double complex` and of
+ *     torch.complex128/complex64 contiguous tensors.
+ *   - A is row-major m x n with leading dimension lda >= n (row i at A + i*lda).
+ *   - all work is enqueued on the plan's stream (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream) and is stream-ordered; calls
+ *     that return values in host memory synchronize that stream.
+ *   - one plan serves one stream and one host thread at a time.
+ *   - errors are returned as minnorm_status; a CUDA error inside a call is
+ *     reported as MINNORM_ECUDA and leaves the plan usable only for destroy.
+ */
+#ifndef MINNORM_H
+#define MINNORM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct minnorm_plan_s *minnorm_plan_t;
+
+typedef enum {
+  MINNORM_C128 = 0,          /* A stored as complex128 */
+  MINNORM_C64 = 1            /* A stored as complex64  */
+} minnorm_dtype;
+
+typedef enum {
+  /* plain: sketch and CG products in complex FP64 */
+  MINNORM_FP64 = 0,
+  /* mixed: sketch FFT/chains and CG products in complex FP32 (from a
+   * complex64 copy of A kept in the plan when A is complex128); pivoted QR,
+   * R^{-1}, the CG scalars and vectors of length m, and the refinement
+   * residuals stay FP64 / double-double */
+  MINNORM_MIXED = 1
+} minnorm_precision;
+
+typedef enum {
+  MINNORM_OK = 0,
+  MINNORM_EINVAL = 1,        /* invalid argument (null pointer, m >= n, l not in (m, n], eps not in (0,1), ...) */
+  MINNORM_ESTATE = 2,        /* minnorm_solve before minnorm_sketch, or a plan already failed */
+  MINNORM_ENOMEM = 3,        /* device or host allocation failed */
+  MINNORM_ECUDA = 4,         /* a CUDA call failed */
+  MINNORM_ERANK = 5,         /* the sketch Y is numerically rank deficient (Remark 4.1): re-plan with another seed */
+  MINNORM_ENOCONV = 6,       /* the refinement hit its step cap before eps; x holds the last iterate */
+  MINNORM_EFLOOR = 7,        /* the refinement stagnated above eps; x holds the best iterate */
+  MINNORM_ETIMEOUT = 8,      /* a bounded device-side wait expired (grid barrier); results are invalid */
+  MINNORM_ENOTSUP = 9        /* a size this build does not handle (see minnorm_plan_create) */
+} minnorm_status;
+
+/* Flags for minnorm_plan_create. */
+#define MINNORM_FLAG_TIMING 1u  /* record CUDA events around the phases and the hot kernels */
+
+typedef struct {
+  int32_t outer_steps;       /* refinement steps taken */
+  int32_t cg_iters;          /* CG iterations summed over all steps */
+  int32_t dd_passes;         /* passes over A with double-double sums */
+  int32_t fp64_passes;       /* incremental FP64 residual passes */
+  double err_bound;          /* a-posteriori bound on ||x - p|| / ||x|| (uses sigma_min(A^* P R^{-1}) >= 1) */
+  double resid_rel;          /* ||b - A x|| / ||b|| from the last residual */
+  double rdiag_max;          /* |R_11| */
+  double rdiag_min;          /* |R_mm| */
+  float ms_sketch;           /* with MINNORM_FLAG_TIMING: Step 1 (sketch) of the last minnorm_sketch */
+  float ms_qr;               /* with MINNORM_FLAG_TIMING: Step 2 (QR + R^{-1}) of the last minnorm_sketch */
+  float ms_solve;            /* with MINNORM_FLAG_TIMING: Steps 3-5 of the last minnorm_solve */
+  float reserved;
+} minnorm_info;
+
+/*
+ * Create a plan for m x n systems (Section 4: m < l < n; l = 0 selects l = 4m,
+ * the choice of Remark 5.6 and Section 7; l = n is also accepted so that tiny
+ * systems with 4m >= n still run, T then being a random unitary matrix).
+ * Draws one SRFT realization (Section 3) from `seed` with SplitMix64 streams
+ * (d, zeta, zeta~ uniform on the unit circle; Pi, Pi~ uniform permutations;
+ * theta, theta~ uniform on [0, 2 pi); l rows of F sampled without
+ * replacement, as the paper's implementation does) and uploads it.
+ * Allocates all device workspace for (m, n, l, dtype, precision).
+ *   plan:   out, host pointer to the new handle (set to NULL on failure).
+ *   m, n:   1 <= m < n; n >= 2.
+ *   flags:  0 or MINNORM_FLAG_TIMING.
+ *   stream: cudaStream_t as void*.
+ * Errors: EINVAL (sizes, enums), ENOMEM, ECUDA, ENOTSUP (a random Givens
+ * chain needing a halo longer than the kernels hold; probability ~0).
+ */
+minnorm_status minnorm_plan_create(minnorm_plan_t *plan, int64_t m, int64_t n, int64_t l,
+                                   minnorm_dtype dtype, minnorm_precision precision,
+                                   uint64_t seed, uint32_t flags, void *stream);
+
+/*
+ * Replace the plan's SRFT realization by caller-supplied parameters (host
+ * arrays, read during the call): zeta_t, zeta, d: n complex128 of modulus 1;
+ * pi_t, pi: n int64, permutations of 0..n-1, acting by gathering
+ * ((Pi v)[j] = v[pi[j]]); theta_t, theta: n-1 doubles; s: l int64, strictly
+ * increasing in [0, n). Invalidates a previous sketch.
+ * Errors: EINVAL (null pointer, a value out of range), ENOTSUP (halo), ECUDA.
+ */
+minnorm_status minnorm_plan_set_params(minnorm_plan_t plan,
+                                       const double *zeta_t, const int64_t *pi_t, const double *theta_t,
+                                       const double *zeta, const int64_t *pi, const double *theta,
+                                       const double *d, const int64_t *s);
+
+/*
+ * Steps 1-2 for the matrix A (device, row-major m x n, dtype of the plan):
+ * Y = T A^* (Eq. randmat), then Y P = Q R by Householder QR with column
+ * pivoting (Step 2), then the plan keeps P R^{-1}. A is read, never written.
+ * Errors: EINVAL (null A, lda < n), ERANK (|R_mm| <= 64 m 2^-53 |R_11|),
+ * ETIMEOUT, ECUDA. Synchronizes the stream (it reads the rank test).
+ */
+minnorm_status minnorm_sketch(minnorm_plan_t plan, const void *A, int64_t lda);
+
+/*
+ * Steps 3-5 for the A of the last minnorm_sketch and the right-hand side b
+ * (device, m complex128): writes x (device, n complex128) with
+ * ||x - p|| <= eps ||p|| when it returns MINNORM_OK. A must hold the same
+ * values as at minnorm_sketch.
+ *   eps:  in (0, 1); the refinement stops once its a-posteriori bound is <= eps.
+ *   info: host pointer or NULL.
+ * Errors: EINVAL, ESTATE (no sketch), ENOCONV, EFLOOR (x still written),
+ * ECUDA. Synchronizes the stream once per refinement step.
+ */
+minnorm_status minnorm_solve(minnorm_plan_t plan, const void *A, int64_t lda, const void *b,
+                             double eps, void *x, minnorm_info *info);
+
+/*
+ * minnorm_sketch + minnorm_solve on HOST buffers: copies A (m x n, lda) and b
+ * to the device, solves, and copies x (n complex128) back. The device copy of
+ * A and b is plan-owned and allocated on the first call (and again only if
+ * that allocation is missing). Pinned host memory makes the copies
+ * asynchronous. Errors: those of minnorm_sketch and minnorm_solve, ENOMEM.
+ */
+minnorm_status minnorm_solve_host(minnorm_plan_t plan, const void *A_host, int64_t lda,
+                                  const void *b_host, double eps, void *x_host, minnorm_info *info);
+
+/* Free the plan and its workspace (synchronizes its stream). NULL is accepted. */
+minnorm_status minnorm_plan_destroy(minnorm_plan_t plan);
+
+/* Static string naming a status. */
+const char *minnorm_status_string(minnorm_status status);
+
+/* ------------------------------------------------------------------------
+ * Component entry points: the individual steps of the hot path, exposed so
+ * that each can be checked on its own. They use the plan's workspace and its
+ * stream and allocate nothing.
+ * ---------------------------------------------------------------------- */
+
+/* Copy the sketch Y = T A^* of the last minnorm_sketch (Step 1, Eq. randmat),
+ * taken before the QR overwrote it, to Y_out (device, l x m complex128,
+ * column-major: column i = T conj(A[i, :])). Requires a plan created with
+ * MINNORM_FLAG_KEEP_SKETCH. Errors: ESTATE, EINVAL. */
+#define MINNORM_FLAG_KEEP_SKETCH 2u
+minnorm_status minnorm_get_sketch(minnorm_plan_t plan, void *Y_out);
+
+/* Copy R (device, m x m complex128, column-major, upper triangular, real
+ * diagonal) and the pivots (device, m int64: column k of R belongs to column
+ * piv[k] of Y) of the last minnorm_sketch (Step 2). Errors: ESTATE, EINVAL. */
+minnorm_status minnorm_get_factor(minnorm_plan_t plan, void *R_out, void *piv_out);
+
+/* One CG product pair of Step 4 in the plan's precision, on device vectors:
+ * q = A^* w (w: m complex128 -> q: n complex128) and t = A q (t: m complex128).
+ * In MINNORM_MIXED the products read the complex64 copy of A made by
+ * minnorm_sketch and are computed in FP32; otherwise FP64. Either output
+ * pointer may be NULL to skip it. Errors: ESTATE, EINVAL. */
+minnorm_status minnorm_cg_products(minnorm_plan_t plan, const void *A, int64_t lda,
+                                   const void *w, void *q, void *t);
+
+/* The double-double residual of the refinement: for y = y_hi + y_lo (device,
+ * m complex128 each; y_lo may be NULL) computes x = A^* y with double-double
+ * sums into x_hi, x_lo (device, n complex128 each) and r = b - A x (device,
+ * m complex128, rounded to FP64). Errors: ESTATE, EINVAL. */
+minnorm_status minnorm_residual_dd(minnorm_plan_t plan, const void *A, int64_t lda,
+                                   const void *y_hi, const void *y_lo, const void *b,
+                                   void *r, void *x_hi, void *x_lo);
+
+/* Kernel timing of the last minnorm_solve when the plan has MINNORM_FLAG_TIMING:
+ * for kernel class k (0: CG product A^* w, 1: CG product A q, 2: double-double
+ * pass, 3: QR, 4: sketch) the number of launches timed and their summed
+ * milliseconds (CUDA events on the plan's stream). Errors: EINVAL. */
+minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *launches, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

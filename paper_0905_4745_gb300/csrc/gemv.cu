@@ -1,0 +1,429 @@
+// gemv.cu -- the passes over A of Step 4 (one A^* w and one A q per CG
+// iteration, Eq. overdet), of Step 5 (x = A^* y, Eq. output) and of the
+// refinement residuals, for a row-major A (row i contiguous).
+//
+//   adjoint  out[j] = sum_i conj(A[i,j]) v[i]: a CTA owns 512 consecutive
+//            columns and streams a range of rows, each row segment read as
+//            one contiguous 4 or 8 KiB span; row ranges are split across CTAs
+//            (adj_split) so that the grid covers the GPU, and a second kernel
+//            adds the splits (also forming ||out||^2 per CTA).
+//   forward  out[i] = sum_j A[i,j] v[j]: a CTA owns `fwd_rows` rows and a
+//            column chunk; each thread keeps one accumulator per row, so the
+//            chunk of v is read once per CTA; chunk partials are added by a
+//            second kernel in FP64.
+//   *_dd     the same two products with every real product split exactly
+//            (TwoProd) and summed in double-double (TwoSum), for the
+//            refinement residual b - A A^* y and the final x = A^* y.
+//
+// Modes: 0 = complex128 A, FP64 arithmetic; 1 = complex64 A, FP32 arithmetic
+// (mixed precision); 2 = complex64 A, FP64 arithmetic.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mn {
+
+constexpr int kAdjThreads = 256;
+constexpr int kAdjVpt = 2;                       // columns per thread
+constexpr int kAdjCols = kAdjThreads * kAdjVpt;  // columns per CTA
+constexpr int kFwdThreads = 256;
+
+template <typename T> struct ComputeOf;
+template <> struct ComputeOf<zd> { using R = double; };
+template <> struct ComputeOf<zf> { using R = float; };
+
+// ---- adjoint ------------------------------------------------------------
+template <typename T, typename R>
+__global__ void __launch_bounds__(kAdjThreads)
+adj_kernel(const T *__restrict__ A, int64_t rows, int64_t cols, int64_t ld, const cx<R> *__restrict__ v,
+           cx<R> *__restrict__ out, int split, const int *__restrict__ skip) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<R> *sv = reinterpret_cast<cx<R> *>(smem_raw);
+  if (skip && *skip) return;
+  const int s = blockIdx.y;
+  const int64_t r0 = rows * s / split, r1 = rows * (s + 1) / split;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) sv[i - r0] = v[i];
+  __syncthreads();
+  const int64_t c = (int64_t)blockIdx.x * kAdjCols + (int64_t)threadIdx.x * kAdjVpt;
+  cx<R> acc[kAdjVpt];
+#pragma unroll
+  for (int q = 0; q < kAdjVpt; ++q) acc[q] = {R(0), R(0)};
+  if (c + kAdjVpt <= cols) {
+    const T *a = A + r0 * ld + c;
+    int64_t i = r0;
+    for (; i + 4 <= r1; i += 4) {
+      T x[4][kAdjVpt];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < kAdjVpt; ++q) x[u][q] = a[u * ld + q];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const cx<R> w = sv[i - r0 + u];
+#pragma unroll
+        for (int q = 0; q < kAdjVpt; ++q) macc(acc[q], cvt<R>(x[u][q]), w);
+      }
+      a += 4 * ld;
+    }
+    for (; i < r1; ++i) {
+      const cx<R> w = sv[i - r0];
+#pragma unroll
+      for (int q = 0; q < kAdjVpt; ++q) macc(acc[q], cvt<R>(a[q]), w);
+      a += ld;
+    }
+  } else {
+    for (int64_t i = r0; i < r1; ++i) {
+      const cx<R> w = sv[i - r0];
+#pragma unroll
+      for (int q = 0; q < kAdjVpt; ++q)
+        if (c + q < cols) macc(acc[q], cvt<R>(A[i * ld + c + q]), w);
+    }
+  }
+  cx<R> *o = out + (int64_t)s * cols;
+#pragma unroll
+  for (int q = 0; q < kAdjVpt; ++q)
+    if (c + q < cols) o[c + q] = acc[q];
+}
+
+// out[j] = sum_s partial[s][j] (in FP64), written as OutT; qq[block] = sum |out|^2
+template <typename R, typename OutT>
+__global__ void __launch_bounds__(256)
+adj_reduce_kernel(const cx<R> *__restrict__ partial, int split, int64_t cols, OutT *__restrict__ out,
+                  double *__restrict__ qq, const int *__restrict__ skip) {
+  __shared__ double sc[8];
+  if (skip && *skip) return;
+  double loc = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols; j += (int64_t)gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < split; ++s) {
+      const cx<R> p = partial[(int64_t)s * cols + j];
+      re += (double)p.re;
+      im += (double)p.im;
+    }
+    OutT o;
+    o.re = re;
+    o.im = im;
+    out[j] = o;
+    const double ore = (double)o.re, oim = (double)o.im;
+    loc = fma(ore, ore, fma(oim, oim, loc));
+  }
+  const double t = block_sum(loc, sc);
+  if (qq && threadIdx.x == 0) qq[blockIdx.x] = t;
+}
+
+// ---- forward ------------------------------------------------------------
+template <typename T, typename R, int ROWS>
+__global__ void __launch_bounds__(kFwdThreads)
+fwd_kernel(const T *__restrict__ A, int64_t rows, int64_t cols, int64_t ld, const cx<R> *__restrict__ v,
+           int64_t chunk, cx<R> *__restrict__ partial, const int *__restrict__ skip) {
+  __shared__ R scratch[(kFwdThreads / 32) * 2 * ROWS];
+  __shared__ R red[2 * ROWS];
+  if (skip && *skip) return;
+  const int64_t i0 = (int64_t)blockIdx.y * ROWS;
+  const int64_t c0 = (int64_t)blockIdx.x * chunk;
+  const int64_t c1 = c0 + chunk < cols ? c0 + chunk : cols;
+  R acc[2 * ROWS];
+#pragma unroll
+  for (int r = 0; r < 2 * ROWS; ++r) acc[r] = R(0);
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    const cx<R> x = v[c];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      if (i0 + r < rows) {
+        const cx<R> a = cvt<R>(A[(i0 + r) * ld + c]);
+        acc[2 * r] = fma(a.re, x.re, fma(-a.im, x.im, acc[2 * r]));
+        acc[2 * r + 1] = fma(a.re, x.im, fma(a.im, x.re, acc[2 * r + 1]));
+      }
+    }
+  }
+  block_sum_k<R, 2 * ROWS>(acc, scratch, red);
+  if (threadIdx.x < ROWS && i0 + threadIdx.x < rows) {
+    partial[(int64_t)blockIdx.x * rows + i0 + threadIdx.x] = {red[2 * threadIdx.x], red[2 * threadIdx.x + 1]};
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+fwd_reduce_kernel(const cx<R> *__restrict__ partial, int nchunk, int64_t rows, zd *__restrict__ out,
+                  const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      const cx<R> p = partial[(int64_t)c * rows + i];
+      re += (double)p.re;
+      im += (double)p.im;
+    }
+    out[i] = {re, im};
+  }
+}
+
+// ---- double-double ------------------------------------------------------
+constexpr int kDdThreads = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kDdThreads)
+adj_dd_kernel(const T *__restrict__ A, int64_t rows, int64_t cols, int64_t ld, const zd *__restrict__ yh,
+              const zd *__restrict__ yl, zd *__restrict__ xh, zd *__restrict__ xl) {
+  __shared__ zd sh[kDdThreads], sl[kDdThreads];
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  dd_acc re = {0.0, 0.0}, im = {0.0, 0.0};
+  for (int64_t i0 = 0; i0 < rows; i0 += kDdThreads) {
+    __syncthreads();
+    if (i0 + threadIdx.x < rows) {
+      sh[threadIdx.x] = yh[i0 + threadIdx.x];
+      sl[threadIdx.x] = yl ? yl[i0 + threadIdx.x] : zd{0.0, 0.0};
+    }
+    __syncthreads();
+    if (j < cols) {
+      const int64_t ie = (i0 + kDdThreads < rows ? i0 + kDdThreads : rows) - i0;
+      const T *a = A + i0 * ld + j;
+      for (int64_t u = 0; u < ie; ++u) {
+        const T av = a[u * ld];
+        const double ar = (double)av.re, ai = (double)av.im;
+        const zd y = sh[u], z = sl[u];
+        // conj(a) * y = (ar yr + ai yi) + i (ar yi - ai yr)
+        dd_prod(re, ar, y.re);
+        dd_prod(re, ai, y.im);
+        dd_prod(im, ar, y.im);
+        dd_prod(im, -ai, y.re);
+        dd_small(re, fma(ar, z.re, ai * z.im));
+        dd_small(im, fma(ar, z.im, -ai * z.re));
+      }
+    }
+  }
+  if (j < cols) {
+    double h, l;
+    dd_round(re, h, l);
+    double h2, l2;
+    dd_round(im, h2, l2);
+    xh[j] = {h, h2};
+    xl[j] = {l, l2};
+  }
+}
+
+__device__ __forceinline__ void dd_warp_sum(dd_acc &a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dd_acc b;
+    b.s = __shfl_xor_sync(0xffffffffu, a.s, o);
+    b.c = __shfl_xor_sync(0xffffffffu, a.c, o);
+    dd_add(a, b);
+  }
+}
+
+constexpr int kDdRows = 4;
+
+// partial[chunk][row] = sum over the chunk of A[row, j] (xh[j] + xl[j]), in dd (hi, lo as complex pairs)
+template <typename T>
+__global__ void __launch_bounds__(kFwdThreads)
+fwd_dd_kernel(const T *__restrict__ A, int64_t rows, int64_t cols, int64_t ld, const zd *__restrict__ xh,
+              const zd *__restrict__ xl, int64_t chunk, zd *__restrict__ ph, zd *__restrict__ pl) {
+  __shared__ dd_acc sred[(kFwdThreads / 32) * 2 * kDdRows];
+  const int64_t i0 = (int64_t)blockIdx.y * kDdRows;
+  const int64_t c0 = (int64_t)blockIdx.x * chunk;
+  const int64_t c1 = c0 + chunk < cols ? c0 + chunk : cols;
+  dd_acc acc[2 * kDdRows];
+#pragma unroll
+  for (int r = 0; r < 2 * kDdRows; ++r) acc[r] = {0.0, 0.0};
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    const zd x = xh[c], z = xl[c];
+#pragma unroll
+    for (int r = 0; r < kDdRows; ++r) {
+      if (i0 + r < rows) {
+        const T av = A[(i0 + r) * ld + c];
+        const double ar = (double)av.re, ai = (double)av.im;
+        // a * x = (ar xr - ai xi) + i (ar xi + ai xr)
+        dd_prod(acc[2 * r], ar, x.re);
+        dd_prod(acc[2 * r], -ai, x.im);
+        dd_prod(acc[2 * r + 1], ar, x.im);
+        dd_prod(acc[2 * r + 1], ai, x.re);
+        dd_small(acc[2 * r], fma(ar, z.re, -ai * z.im));
+        dd_small(acc[2 * r + 1], fma(ar, z.im, ai * z.re));
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int r = 0; r < 2 * kDdRows; ++r) dd_warp_sum(acc[r]);
+  if (lane == 0) {
+#pragma unroll
+    for (int r = 0; r < 2 * kDdRows; ++r) sred[wid * 2 * kDdRows + r] = acc[r];
+  }
+  __syncthreads();
+  if (threadIdx.x < kDdRows && i0 + threadIdx.x < rows) {
+    const int r = threadIdx.x;
+    dd_acc sr = sred[2 * r], si = sred[2 * r + 1];
+    for (int w = 1; w < nw; ++w) {
+      dd_add(sr, sred[w * 2 * kDdRows + 2 * r]);
+      dd_add(si, sred[w * 2 * kDdRows + 2 * r + 1]);
+    }
+    const int64_t o = (int64_t)blockIdx.x * rows + i0 + r;
+    double h1, l1, h2, l2;
+    dd_round(sr, h1, l1);
+    dd_round(si, h2, l2);
+    ph[o] = {h1, h2};
+    pl[o] = {l1, l2};
+  }
+}
+
+// v = sum over chunks (dd) -> (vh, vl)
+__global__ void fwd_dd_reduce_kernel(const zd *__restrict__ ph, const zd *__restrict__ pl, int nchunk,
+                                     int64_t rows, zd *__restrict__ vh, zd *__restrict__ vl) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
+    dd_acc sr = {0.0, 0.0}, si = {0.0, 0.0};
+    for (int c = 0; c < nchunk; ++c) {
+      const zd h = ph[(int64_t)c * rows + i], l = pl[(int64_t)c * rows + i];
+      dd_add(sr, dd_acc{h.re, l.re});
+      dd_add(si, dd_acc{h.im, l.im});
+    }
+    double h1, l1, h2, l2;
+    dd_round(sr, h1, l1);
+    dd_round(si, h2, l2);
+    vh[i] = {h1, h2};
+    if (vl) vl[i] = {l1, l2};
+  }
+}
+
+// ---- small dense m x m products (the preconditioner P R^{-1}) ------------
+__global__ void __launch_bounds__(256)
+small_gemv_kernel(const zd *__restrict__ M, int m, const zd *__restrict__ v, zd *__restrict__ out,
+                  zf *__restrict__ out32, const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= m) return;
+  const zd *row = M + (int64_t)i * m;
+  double re = 0.0, im = 0.0;
+  for (int k = lane; k < m; k += 32) {
+    const zd a = row[k], x = v[k];
+    re = fma(a.re, x.re, fma(-a.im, x.im, re));
+    im = fma(a.re, x.im, fma(a.im, x.re, im));
+  }
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if (lane == 0) {
+    out[i] = {re, im};
+    if (out32) out32[i] = {(float)re, (float)im};
+  }
+}
+
+// ---- configuration and launchers ------------------------------------------
+void gemv_configure(GemvPlan &g, int64_t rows, int64_t cols, int64_t ld, int mode, int num_sms) {
+  g.rows = rows;
+  g.cols = cols;
+  g.ld = ld;
+  g.mode = mode;
+  const int64_t col_blocks = (cols + kAdjCols - 1) / kAdjCols;
+  int split = 1;
+  while (col_blocks * split < 2 * num_sms && split * 2 <= rows && split < 64) split *= 2;
+  g.adj_split = split;
+  g.fwd_rows = 16;
+  const int64_t row_blocks = (rows + g.fwd_rows - 1) / g.fwd_rows;
+  int64_t nchunk = 1;
+  while (row_blocks * nchunk < 3 * num_sms && cols / (nchunk * 2) >= 1024) nchunk *= 2;
+  g.fwd_nchunk = (int)nchunk;
+  g.fwd_chunk = (int)((cols + nchunk - 1) / nchunk);
+}
+
+size_t gemv_adj_partial_elems(const GemvPlan &g) { return (size_t)g.adj_split * g.cols; }
+size_t gemv_fwd_partial_elems(const GemvPlan &g) { return (size_t)g.fwd_nchunk * g.rows; }
+size_t fwd_dd_partial_elems(const GemvPlan &g) {
+  const int64_t nchunk = g.fwd_nchunk;
+  return (size_t)nchunk * g.rows;
+}
+
+static int reduce_blocks(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
+}
+
+template <typename T, typename R, typename OutT>
+static cudaError_t adj_t(const GemvPlan &g, const void *A, const void *v, void *out, void *partial,
+                         double *qq, const int *skip, cudaStream_t st) {
+  const int64_t rows_per = (g.rows + g.adj_split - 1) / g.adj_split + 1;
+  const size_t smem = sizeof(cx<R>) * (size_t)rows_per;
+  cudaError_t e = cudaFuncSetAttribute(adj_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((g.cols + kAdjCols - 1) / kAdjCols), g.adj_split);
+  adj_kernel<T, R><<<grid, kAdjThreads, smem, st>>>((const T *)A, g.rows, g.cols, g.ld, (const cx<R> *)v,
+                                                     (cx<R> *)partial, g.adj_split, skip);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  adj_reduce_kernel<R, OutT><<<reduce_blocks(g.cols), 256, 0, st>>>((const cx<R> *)partial, g.adj_split,
+                                                                     g.cols, (OutT *)out, qq, skip);
+  return cudaGetLastError();
+}
+
+template <typename T, typename R>
+static cudaError_t fwd_t(const GemvPlan &g, const void *A, const void *v, void *out, void *partial,
+                         const int *skip, cudaStream_t st) {
+  dim3 grid(g.fwd_nchunk, (unsigned)((g.rows + 15) / 16));
+  fwd_kernel<T, R, 16><<<grid, kFwdThreads, 0, st>>>((const T *)A, g.rows, g.cols, g.ld, (const cx<R> *)v,
+                                                      g.fwd_chunk, (cx<R> *)partial, skip);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  fwd_reduce_kernel<R><<<reduce_blocks(g.rows), 256, 0, st>>>((const cx<R> *)partial, g.fwd_nchunk, g.rows,
+                                                              (zd *)out, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_adj(const GemvPlan &g, const void *A, const void *v, void *out, void *partial,
+                            double *qq, const int *skip, cudaStream_t st) {
+  if (g.mode == 0) return adj_t<zd, double, zd>(g, A, v, out, partial, qq, skip, st);
+  if (g.mode == 2) return adj_t<zf, double, zd>(g, A, v, out, partial, qq, skip, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gemv_fwd(const GemvPlan &g, const void *A, const void *v, void *out, void *partial,
+                            const int *skip, cudaStream_t st) {
+  if (g.mode == 0) return fwd_t<zd, double>(g, A, v, out, partial, skip, st);
+  if (g.mode == 2) return fwd_t<zf, double>(g, A, v, out, partial, skip, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gemv_adj_f32(const GemvPlan &g, const void *A, const void *v32, void *out32,
+                                void *partial, double *qq, const int *skip, cudaStream_t st) {
+  return adj_t<zf, float, zf>(g, A, v32, out32, partial, qq, skip, st);
+}
+
+cudaError_t launch_gemv_fwd_f32(const GemvPlan &g, const void *A, const void *v32, void *out64,
+                                void *partial, const int *skip, cudaStream_t st) {
+  return fwd_t<zf, float>(g, A, v32, out64, partial, skip, st);
+}
+
+cudaError_t launch_adj_dd(const GemvPlan &g, const void *A, const void *yh, const void *yl, void *xh,
+                          void *xl, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((g.cols + kDdThreads - 1) / kDdThreads);
+  if (g.mode == 0)
+    adj_dd_kernel<zd><<<blocks, kDdThreads, 0, st>>>((const zd *)A, g.rows, g.cols, g.ld, (const zd *)yh,
+                                                     (const zd *)yl, (zd *)xh, (zd *)xl);
+  else
+    adj_dd_kernel<zf><<<blocks, kDdThreads, 0, st>>>((const zf *)A, g.rows, g.cols, g.ld, (const zd *)yh,
+                                                     (const zd *)yl, (zd *)xh, (zd *)xl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_dd(const GemvPlan &g, const void *A, const void *xh, const void *xl, void *vh,
+                          void *vl, void *partial, cudaStream_t st) {
+  zd *ph = (zd *)partial;
+  zd *pl = ph + fwd_dd_partial_elems(g);
+  dim3 grid(g.fwd_nchunk, (unsigned)((g.rows + kDdRows - 1) / kDdRows));
+  if (g.mode == 0)
+    fwd_dd_kernel<zd><<<grid, kFwdThreads, 0, st>>>((const zd *)A, g.rows, g.cols, g.ld, (const zd *)xh,
+                                                    (const zd *)xl, g.fwd_chunk, ph, pl);
+  else
+    fwd_dd_kernel<zf><<<grid, kFwdThreads, 0, st>>>((const zf *)A, g.rows, g.cols, g.ld, (const zd *)xh,
+                                                    (const zd *)xl, g.fwd_chunk, ph, pl);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  fwd_dd_reduce_kernel<<<reduce_blocks(g.rows), 256, 0, st>>>(ph, pl, g.fwd_nchunk, g.rows, (zd *)vh, (zd *)vl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_gemv(const void *M, int m, const void *v, void *out, void *out32, const int *skip,
+                              cudaStream_t st) {
+  small_gemv_kernel<<<(m + 7) / 8, 256, 0, st>>>((const zd *)M, m, (const zd *)v, (zd *)out, (zf *)out32, skip);
+  return cudaGetLastError();
+}
+
+}  // namespace mn

@@ -1,0 +1,104 @@
+// kernels.h -- host-side launchers of the sm_103a kernels (internal to the
+// library; the public interface is include/minnorm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mn {
+
+struct GridBarrier;
+
+// ---- sketch.cu ------------------------------------------------------------
+struct ChainArgs {
+  const void *src;       // rows x n, complex128 (src_c64 = 0) or complex64
+  int64_t ld_src;
+  void *dst;             // rows x n complex of the compute precision
+  int64_t ld_dst;
+  const int32_t *idx;    // gather permutation (n)
+  const void *phase;     // n unit phases (compute precision), applied after the gather
+  const void *cs;        // n (cos, sin) pairs, entry n-1 = (1, 0)
+  const void *post;      // n phases applied to the output, or nullptr
+  const int32_t *halo;   // per-segment right halo
+  int n, seg, cap, rows;
+  bool src_c64, conj, real_fp32;
+};
+cudaError_t launch_chain(const ChainArgs &a, cudaStream_t st);
+
+struct FftArgs {
+  const void *src;        // rows x n (compute precision), rows of ld
+  int64_t ld;
+  void *work;             // rows x n scratch for the four-step path
+  const void *tw;         // n twiddles e^{-2 pi i k/n}
+  int logn, logN1;        // logN1 = 0: single-pass row FFT
+  int tj, tk;             // tile widths of pass A / B
+  const int32_t *samp_off, *samp_t, *samp_loc;
+  int l, rows;
+  void *Y;                // l x m complex128, column-major
+  int64_t ldy;
+  int row_offset;
+  bool real_fp32;
+};
+cudaError_t launch_fft(const FftArgs &a, cudaStream_t st);
+cudaError_t launch_to_c64(const void *A, int64_t lda, void *B, int64_t ldb, int64_t rows, int64_t cols,
+                          cudaStream_t st);
+// vectors: complex128 -> complex64 and back
+cudaError_t launch_narrow(int64_t len, const void *src, void *dst, cudaStream_t st);
+cudaError_t launch_widen(int64_t len, const void *src, void *dst, cudaStream_t st);
+
+// ---- qr.cu ----------------------------------------------------------------
+struct QrArgs {
+  void *Y;                // l x m complex128 column-major, overwritten
+  int l, m;
+  double *vn1, *vn2;      // m
+  double *beta;           // m: real diagonal of R
+  int32_t *piv;           // m
+  void *R;                // m x m complex128 column-major (out)
+  GridBarrier *bar;
+  int *err;
+  uint64_t limit_ns;
+};
+cudaError_t launch_qrp(const QrArgs &a, cudaStream_t st);
+
+// Wp = P R^{-1} (row-major m x m) and WpH = Wp^* (row-major)
+cudaError_t launch_prinv(const void *R, const int32_t *piv, int m, void *Wp, void *WpH, cudaStream_t st);
+
+// ---- gemv.cu --------------------------------------------------------------
+// Element/compute types: 0 = complex128 matrix / FP64 compute, 1 = complex64
+// matrix / FP32 compute, 2 = complex64 matrix / FP64 compute.
+struct GemvPlan {
+  int64_t rows, cols, ld;
+  int mode;               // as above
+  int adj_split;          // row splits of the adjoint product
+  int fwd_rows;           // rows per CTA of the forward product
+  int fwd_chunk;          // columns per CTA of the forward product
+  int fwd_nchunk;
+};
+void gemv_configure(GemvPlan &g, int64_t rows, int64_t cols, int64_t ld, int mode, int num_sms);
+size_t gemv_adj_partial_elems(const GemvPlan &g);   // complex elements of partial storage (compute type)
+size_t gemv_fwd_partial_elems(const GemvPlan &g);
+
+// out = A^* v: v (rows, complex128), out (cols, complex128); partials scratch
+cudaError_t launch_gemv_adj(const GemvPlan &g, const void *A, const void *v, void *out, void *partial,
+                            double *qq_partial, const int *skip, cudaStream_t st);
+// out = A v: v (cols, complex128 or complex64 when compute is FP32), out (rows, complex128)
+cudaError_t launch_gemv_fwd(const GemvPlan &g, const void *A, const void *v, void *out, void *partial,
+                            const int *skip, cudaStream_t st);
+// mixed-precision entry points working on FP32 vectors
+cudaError_t launch_gemv_adj_f32(const GemvPlan &g, const void *A, const void *v32, void *out32,
+                                void *partial, double *qq, const int *skip, cudaStream_t st);
+cudaError_t launch_gemv_fwd_f32(const GemvPlan &g, const void *A, const void *v32, void *out64,
+                                void *partial, const int *skip, cudaStream_t st);
+
+// double-double: x = A^* (y_hi + y_lo) -> (x_hi, x_lo); v = A (x_hi + x_lo) -> (v_hi, v_lo)
+cudaError_t launch_adj_dd(const GemvPlan &g, const void *A, const void *yh, const void *yl, void *xh,
+                          void *xl, cudaStream_t st);
+cudaError_t launch_fwd_dd(const GemvPlan &g, const void *A, const void *xh, const void *xl, void *vh,
+                          void *vl, void *partial, cudaStream_t st);
+size_t fwd_dd_partial_elems(const GemvPlan &g);
+
+// small dense m x m FP64 products: out = M v (M row-major), optionally also an FP32 copy
+cudaError_t launch_small_gemv(const void *M, int m, const void *v, void *out, void *out32, const int *skip,
+                              cudaStream_t st);
+
+}  // namespace mn

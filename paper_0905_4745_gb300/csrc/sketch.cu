@@ -1,0 +1,356 @@
+// sketch.cu -- Step 1 of the algorithm (Eq. randmat): Y = T A^*, column i of Y
+// being T applied to the conjugated row i of A, with
+//   T = S F D Theta Pi Z Theta~ Pi~ Z~        (Eqs. SRFT, SRFT2, Rokhlin_trans)
+// applied right to left. Per row the work is split into three stages:
+//
+//   chain_kernel (twice)  gather through a permutation, multiply by a unit
+//                         phase, run a Givens chain (Eq. big_def), optionally
+//                         multiply by D; one CTA per (row, 2048-element segment)
+//   fft kernels           the unitary DFT F of Eq. (DFT) by radix-2 FFTs in
+//                         shared memory (one pass for n <= 4096/8192, otherwise
+//                         the four-step factorisation n = N1 N2), with the row
+//                         sample S applied while storing into Y
+//
+// The chain Theta = G_0 G_1 ... G_{n-2} (G_{n-2} acting first) is the reverse
+// affine recurrence
+//     C_{n-1} = v_{n-1},   C_k = cos(t_k) v_k + sin(t_k) C_{k+1},
+//     out_{k+1} = -sin(t_k) v_k + cos(t_k) C_{k+1},   out_0 = C_0,
+// with real coefficients. Inside a CTA it is evaluated exactly as a parallel
+// scan of the affine maps C -> s C + c v. Segments are independent: a segment
+// is extended to the right by a precomputed halo over which the product of
+// |sin t_k| falls below 2^-72 / sqrt(n) (FP64) or 2^-42 / sqrt(n) (FP32), so
+// starting the recurrence at the halo's end with a zero carry changes the
+// segment's outputs by less than that fraction of the row norm.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mn {
+
+constexpr int kChainThreads = 256;
+
+// Reverse (right-to-left) inclusive scan of affine maps x -> P x + Q across the
+// block; returns for each thread the carry entering its chunk from the right,
+// i.e. the composition of all maps to its right applied to 0.
+template <typename R>
+__device__ __forceinline__ cx<R> block_reverse_carry(R P, cx<R> Q, R *sP, cx<R> *sQ) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const R P2 = __shfl_down_sync(0xffffffffu, P, off);
+    const R Q2r = __shfl_down_sync(0xffffffffu, Q.re, off);
+    const R Q2i = __shfl_down_sync(0xffffffffu, Q.im, off);
+    if (lane + off < 32) {
+      Q.re = fma(P, Q2r, Q.re);
+      Q.im = fma(P, Q2i, Q.im);
+      P = P * P2;
+    }
+  }
+  // lane holds F_lane o ... o F_31 (within the warp)
+  if (lane == 0) { sP[wid] = P; sQ[wid] = Q; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cx<R> c = {R(0), R(0)};
+    for (int w = nw - 1; w >= 0; --w) {
+      const cx<R> q = sQ[w];
+      const R p = sP[w];
+      sQ[w] = c;  // carry entering warp w from the right
+      c = {fma(p, c.re, q.re), fma(p, c.im, q.im)};
+    }
+  }
+  __syncthreads();
+  const cx<R> wc = sQ[wid];
+  const R Pn = __shfl_down_sync(0xffffffffu, P, 1);
+  const R Qnr = __shfl_down_sync(0xffffffffu, Q.re, 1);
+  const R Qni = __shfl_down_sync(0xffffffffu, Q.im, 1);
+  cx<R> carry;
+  if (lane == 31) {
+    carry = wc;
+  } else {
+    carry = {fma(Pn, wc.re, Qnr), fma(Pn, wc.im, Qni)};
+  }
+  __syncthreads();  // sP/sQ may be reused by the caller
+  return carry;
+}
+
+// One Givens-chain stage for rows [row0, row0 + gridDim.y):
+//   v_j = phase[j] * (conj?) src[row, idx[j]]           (gather Pi and phase Z)
+//   out = Theta v                                          (chain of Eq. big_def)
+//   dst[row, j] = (post ? post[j] : 1) * out_j
+template <typename R, typename S, bool CONJ, bool POST>
+__global__ void __launch_bounds__(kChainThreads)
+chain_kernel(const S *__restrict__ src, int64_t ld_src, cx<R> *__restrict__ dst, int64_t ld_dst,
+             const int32_t *__restrict__ idx, const cx<R> *__restrict__ phase,
+             const cx<R> *__restrict__ cs, const cx<R> *__restrict__ post,
+             const int32_t *__restrict__ halo, int n, int seg, int cap) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<R> *V = reinterpret_cast<cx<R> *>(smem_raw);
+  cx<R> *CS = V + cap;
+  cx<R> *OUT = CS + cap;
+  __shared__ R sP[kChainThreads / 32];
+  __shared__ cx<R> sQ[kChainThreads / 32];
+
+  const int g = blockIdx.x;
+  const int64_t row = blockIdx.y;
+  const int j0 = g * seg;
+  const int len = min(seg, n - j0);
+  const int lo = j0 > 0 ? j0 - 1 : 0;
+  const int E = j0 + len + halo[g];
+  const int cnt = E - lo;
+  const S *srow = src + row * ld_src;
+
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const int j = lo + t;
+    const S a = srow[idx[j]];
+    const cx<R> v = {R(a.re), CONJ ? -R(a.im) : R(a.im)};
+    V[t] = v * phase[j];
+    CS[t] = cs[j];
+  }
+  __syncthreads();
+
+  const int per = (cnt + blockDim.x - 1) / blockDim.x;
+  const int a0 = min(threadIdx.x * per, cnt);
+  const int a1 = min(a0 + per, cnt);
+  R P = R(1);
+  cx<R> Q = {R(0), R(0)};
+  for (int t = a1 - 1; t >= a0; --t) {
+    const cx<R> c = CS[t];  // (cos, sin)
+    const cx<R> v = V[t];
+    Q = {fma(c.im, Q.re, c.re * v.re), fma(c.im, Q.im, c.re * v.im)};
+    P *= c.im;
+  }
+  cx<R> C = block_reverse_carry<R>(P, Q, sP, sQ);
+  for (int t = a1 - 1; t >= a0; --t) {
+    const cx<R> c = CS[t];
+    const cx<R> v = V[t];
+    const int k = lo + t;  // element index; C holds C_{k+1}
+    const int o = k + 1 - j0;
+    if (o >= 0 && o < len) OUT[o] = {fma(c.re, C.re, -c.im * v.re), fma(c.re, C.im, -c.im * v.im)};
+    C = {fma(c.im, C.re, c.re * v.re), fma(c.im, C.im, c.re * v.im)};
+  }
+  if (j0 == 0 && a0 == 0 && a1 > a0) OUT[0] = C;  // out_0 = C_0
+  __syncthreads();
+
+  cx<R> *drow = dst + row * ld_dst;
+  for (int t = threadIdx.x; t < len; t += blockDim.x) {
+    cx<R> o = OUT[t];
+    if (POST) o = o * post[j0 + t];
+    drow[j0 + t] = o;
+  }
+}
+
+// ---- FFT ----------------------------------------------------------------
+__device__ __forceinline__ int bitrev(int j, int logL) {
+  return logL == 0 ? 0 : (int)(__brev((unsigned)j) >> (32 - logL));
+}
+
+// In-place radix-2 DIT FFT (forward, e^{-2 pi i jk/L}) of B contiguous
+// sequences of length L = 2^logL stored in bit-reversed order; twiddles
+// e^{-2 pi i k / NT} from the table tw (L divides NT).
+template <typename R>
+__device__ __forceinline__ void smem_fft(cx<R> *data, int B, int logL, const cx<R> *__restrict__ tw,
+                                         int logNT) {
+  const int L = 1 << logL;
+  const int halfL = L >> 1;
+  const int total = B * halfL;
+  for (int lh = 0; lh < logL; ++lh) {
+    const int h = 1 << lh;
+    const int twshift = logNT - lh - 1;  // NT / (2h)
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+      const int seqi = b >> (logL - 1);
+      const int bb = b & (halfL - 1);
+      const int k = bb & (h - 1);
+      const int pos = ((bb >> lh) << (lh + 1)) + k;
+      cx<R> *d = data + seqi * L;
+      const cx<R> w = tw[k << twshift];
+      const cx<R> u = d[pos];
+      const cx<R> v = d[pos + h] * w;
+      d[pos] = u + v;
+      d[pos + h] = u - v;
+    }
+    __syncthreads();
+  }
+}
+
+// Whole-row FFT (n <= smem capacity) + sample: Y[t, row] = X[s_t] / sqrt(n).
+template <typename R>
+__global__ void __launch_bounds__(256)
+fft_row_kernel(const cx<R> *__restrict__ src, int64_t ld_src, int logn, const cx<R> *__restrict__ tw,
+               const int32_t *__restrict__ samp_t, const int32_t *__restrict__ samp_loc, int l,
+               zd *__restrict__ Y, int64_t ldy, int row_offset, double scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<R> *data = reinterpret_cast<cx<R> *>(smem_raw);
+  const int n = 1 << logn;
+  const int64_t row = blockIdx.y;
+  const cx<R> *s = src + row * ld_src;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) data[bitrev(j, logn)] = s[j];
+  __syncthreads();
+  smem_fft<R>(data, 1, logn, tw, logn);
+  zd *y = Y + (row + row_offset) * ldy;
+  for (int e = threadIdx.x; e < l; e += blockDim.x) {
+    const cx<R> v = data[samp_loc[e]];
+    y[samp_t[e]] = {double(v.re) * scale, double(v.im) * scale};
+  }
+}
+
+// Four-step pass A: for each j1 in this CTA's tile, the length-N2 FFT over j2 of
+// v[j1 + N1 j2], times e^{-2 pi i j1 k2 / n}, stored at W[k2 N1 + j1].
+template <typename R>
+__global__ void __launch_bounds__(256)
+fft_pass_a_kernel(const cx<R> *__restrict__ src, int64_t ld, cx<R> *__restrict__ W, int logn, int logN1,
+                  int tj, const cx<R> *__restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<R> *data = reinterpret_cast<cx<R> *>(smem_raw);
+  const int n = 1 << logn, N1 = 1 << logN1, logN2 = logn - logN1, N2 = 1 << logN2;
+  const int j1_0 = blockIdx.x * tj;
+  const int64_t row = blockIdx.y;
+  const cx<R> *s = src + row * ld;
+  const int total = tj * N2;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int jj = e % tj, j2 = e / tj;
+    data[jj * N2 + bitrev(j2, logN2)] = s[(j1_0 + jj) + (int64_t)N1 * j2];
+  }
+  __syncthreads();
+  smem_fft<R>(data, tj, logN2, tw, logn);
+  cx<R> *w = W + row * ld;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int jj = e % tj, k2 = e / tj;
+    const int j1 = j1_0 + jj;
+    const int64_t tix = ((int64_t)j1 * k2) & (n - 1);
+    w[(int64_t)k2 * N1 + j1] = data[jj * N2 + k2] * tw[tix];
+  }
+}
+
+// Four-step pass B: for each k2 in the tile, the length-N1 FFT over j1 of
+// W[k2 N1 + j1] gives X[N2 k1 + k2]; the sampled ones go to Y.
+template <typename R>
+__global__ void __launch_bounds__(256)
+fft_pass_b_kernel(const cx<R> *__restrict__ W, int64_t ld, int logn, int logN1, int tk,
+                  const cx<R> *__restrict__ tw, const int32_t *__restrict__ samp_off,
+                  const int32_t *__restrict__ samp_t, const int32_t *__restrict__ samp_loc,
+                  zd *__restrict__ Y, int64_t ldy, int row_offset, double scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<R> *data = reinterpret_cast<cx<R> *>(smem_raw);
+  const int N1 = 1 << logN1;
+  const int k2_0 = blockIdx.x * tk;
+  const int64_t row = blockIdx.y;
+  const cx<R> *w = W + row * ld + (int64_t)k2_0 * N1;
+  const int total = tk * N1;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int kk = e >> logN1, j1 = e & (N1 - 1);
+    data[kk * N1 + bitrev(j1, logN1)] = w[e];
+  }
+  __syncthreads();
+  smem_fft<R>(data, tk, logN1, tw, logn);
+  zd *y = Y + (row + row_offset) * ldy;
+  const int b0 = samp_off[blockIdx.x], b1 = samp_off[blockIdx.x + 1];
+  for (int e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
+    const cx<R> v = data[samp_loc[e]];
+    y[samp_t[e]] = {double(v.re) * scale, double(v.im) * scale};
+  }
+}
+
+__global__ void to_c64_kernel(const zd *__restrict__ A, int64_t lda, zf *__restrict__ B, int64_t ldb,
+                              int64_t cols) {
+  const int64_t i = blockIdx.y;
+  const zd *a = A + i * lda;
+  zf *b = B + i * ldb;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols; j += (int64_t)gridDim.x * blockDim.x) {
+    const zd v = a[j];
+    b[j] = {float(v.re), float(v.im)};
+  }
+}
+
+__global__ void widen_kernel(int64_t len, const zf *__restrict__ src, zd *__restrict__ dst) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
+    const zf v = src[j];
+    dst[j] = {double(v.re), double(v.im)};
+  }
+}
+
+// ---- host launchers -----------------------------------------------------
+template <typename R, typename S, bool CONJ, bool POST>
+static cudaError_t launch_chain_t(const ChainArgs &a, cudaStream_t st) {
+  const size_t smem = sizeof(cx<R>) * (size_t)(2 * a.cap + a.seg);
+  cudaError_t e = cudaFuncSetAttribute(chain_kernel<R, S, CONJ, POST>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int nseg = (a.n + a.seg - 1) / a.seg;
+  dim3 grid(nseg, a.rows);
+  chain_kernel<R, S, CONJ, POST><<<grid, kChainThreads, smem, st>>>(
+      (const S *)a.src, a.ld_src, (cx<R> *)a.dst, a.ld_dst, a.idx, (const cx<R> *)a.phase,
+      (const cx<R> *)a.cs, (const cx<R> *)a.post, a.halo, a.n, a.seg, a.cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chain(const ChainArgs &a, cudaStream_t st) {
+  // src kinds: 0 = complex128, 1 = complex64; real: 0 = double, 1 = float
+  if (a.real_fp32) {
+    if (a.src_c64) {
+      if (a.conj) return a.post ? launch_chain_t<float, zf, true, true>(a, st) : launch_chain_t<float, zf, true, false>(a, st);
+      return a.post ? launch_chain_t<float, zf, false, true>(a, st) : launch_chain_t<float, zf, false, false>(a, st);
+    }
+    if (a.conj) return a.post ? launch_chain_t<float, zd, true, true>(a, st) : launch_chain_t<float, zd, true, false>(a, st);
+    return a.post ? launch_chain_t<float, zd, false, true>(a, st) : launch_chain_t<float, zd, false, false>(a, st);
+  }
+  if (a.src_c64) {
+    if (a.conj) return a.post ? launch_chain_t<double, zf, true, true>(a, st) : launch_chain_t<double, zf, true, false>(a, st);
+    return a.post ? launch_chain_t<double, zf, false, true>(a, st) : launch_chain_t<double, zf, false, false>(a, st);
+  }
+  if (a.conj) return a.post ? launch_chain_t<double, zd, true, true>(a, st) : launch_chain_t<double, zd, true, false>(a, st);
+  return a.post ? launch_chain_t<double, zd, false, true>(a, st) : launch_chain_t<double, zd, false, false>(a, st);
+}
+
+template <typename R>
+static cudaError_t launch_fft_t(const FftArgs &a, cudaStream_t st) {
+  const double scale = 1.0 / sqrt((double)(1LL << a.logn));
+  cudaError_t e;
+  if (a.logN1 == 0) {
+    const size_t smem = sizeof(cx<R>) << a.logn;
+    e = cudaFuncSetAttribute(fft_row_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fft_row_kernel<R><<<dim3(1, a.rows), 256, smem, st>>>(
+        (const cx<R> *)a.src, a.ld, a.logn, (const cx<R> *)a.tw, a.samp_t, a.samp_loc, a.l, (zd *)a.Y,
+        a.ldy, a.row_offset, scale);
+    return cudaGetLastError();
+  }
+  const int N1 = 1 << a.logN1, N2 = 1 << (a.logn - a.logN1);
+  const size_t smemA = sizeof(cx<R>) * (size_t)a.tj * N2;
+  const size_t smemB = sizeof(cx<R>) * (size_t)a.tk * N1;
+  e = cudaFuncSetAttribute(fft_pass_a_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemA);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fft_pass_b_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemB);
+  if (e != cudaSuccess) return e;
+  fft_pass_a_kernel<R><<<dim3(N1 / a.tj, a.rows), 256, smemA, st>>>(
+      (const cx<R> *)a.src, a.ld, (cx<R> *)a.work, a.logn, a.logN1, a.tj, (const cx<R> *)a.tw);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  fft_pass_b_kernel<R><<<dim3(N2 / a.tk, a.rows), 256, smemB, st>>>(
+      (const cx<R> *)a.work, a.ld, a.logn, a.logN1, a.tk, (const cx<R> *)a.tw, a.samp_off, a.samp_t,
+      a.samp_loc, (zd *)a.Y, a.ldy, a.row_offset, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft(const FftArgs &a, cudaStream_t st) {
+  return a.real_fp32 ? launch_fft_t<float>(a, st) : launch_fft_t<double>(a, st);
+}
+
+cudaError_t launch_to_c64(const void *A, int64_t lda, void *B, int64_t ldb, int64_t rows, int64_t cols,
+                          cudaStream_t st) {
+  int64_t bx = (cols + 255) / 256;
+  if (bx > 64) bx = 64;
+  to_c64_kernel<<<dim3((unsigned)bx, (unsigned)rows), 256, 0, st>>>((const zd *)A, lda, (zf *)B, ldb, cols);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_narrow(int64_t len, const void *src, void *dst, cudaStream_t st) {
+  return launch_to_c64(src, len, dst, len, 1, len, st);
+}
+
+cudaError_t launch_widen(int64_t len, const void *src, void *dst, cudaStream_t st) {
+  int64_t b = (len + 255) / 256;
+  if (b > 1024) b = 1024;
+  widen_kernel<<<(unsigned)b, 256, 0, st>>>(len, (const zf *)src, (zd *)dst);
+  return cudaGetLastError();
+}
+
+}  // namespace mn

@@ -1,0 +1,777 @@
+// solver.cu -- the plan object and the C ABI of include/minnorm.h: Steps 1-5
+// of the randomized minimal-norm algorithm (Section 4) on one GPU.
+//
+// Steps 2-3 (z = Q R^{-*} P^T b, c = T^* z) enter Step 4 only through R and
+// P: with M = A^* P R^{-1}, the normal equations of min_u ||M u - c|| are
+// (R^{-*} P^T A A^* P R^{-1}) u = R^{-*} P^T A c = R^{-*} P^T b (Lemma 5.1,
+// Eq. easy: A c = b). So after the sketch and its QR, the solve runs CG on
+// that system (two passes over A per iteration: q = A^* (P R^{-1} p), then
+// A q), and Step 5 is x = A^* y with y = P R^{-1} u.
+//
+// Because the error of FP64 arithmetic in x = A^* y and in b - A x grows like
+// kappa(A) * 2^-53 (about 1e-10 at kappa = 1e6; the paper's Tables 2 and 4
+// show raw errors near 1e-9), the CG runs as the inner solver of an outer
+// refinement loop on A A^* y = b (a generalisation of Remark 4.2's extra CG
+// iterations): y is kept as a double-double pair, the residual r = b - A A^* y
+// and x = A^* y are formed with double-double sums when the size of the
+// correction makes FP64 insufficient, and otherwise updated in FP64 as
+// x += A^* dy, r -= A (A^* dy), whose rounding errors scale with the
+// correction rather than with x. Each step is stopped by the a-posteriori
+// bound ||x - p|| <= ||R^{-*} P^T r||, which holds because T has orthonormal
+// rows (sigma_min(M) >= 1, so ||x - p|| = ||M (u - u*)|| <= ||M^* M (u - u*)||).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/minnorm.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "params.h"
+#include "vec.h"
+
+using namespace mn;
+
+namespace {
+
+constexpr int kSeg = 2048;                 // chain segment (outputs per CTA)
+constexpr int kChainCap = 4096;            // loaded elements per chain CTA
+constexpr uint64_t kBarrierLimitNs = 2000000000ULL;  // 2 s per grid-barrier wait
+constexpr int kMaxOuter = 12;
+
+struct KernelTimer {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct minnorm_plan_s {
+  int64_t m = 0, n = 0, l = 0;
+  minnorm_dtype dtype = MINNORM_C128;
+  minnorm_precision prec = MINNORM_FP64;
+  uint32_t flags = 0;
+  cudaStream_t st = nullptr;
+  int device = 0, sms = 152;
+  bool fp32 = false;        // sketch and CG products in FP32
+  bool sketched = false;
+  bool failed = false;
+  SrftParams P;
+
+  // sketch tables
+  int logn = 0, logN1 = 0, tj = 0, tk = 0;
+  int cap1 = 0, cap2 = 0;
+  int32_t *d_idx1 = nullptr, *d_idx2 = nullptr, *d_halo1 = nullptr, *d_halo2 = nullptr;
+  void *d_ph1 = nullptr, *d_ph2 = nullptr, *d_cs1 = nullptr, *d_cs2 = nullptr, *d_post = nullptr, *d_tw = nullptr;
+  int32_t *d_samp_off = nullptr, *d_samp_t = nullptr, *d_samp_loc = nullptr;
+  void *d_S1 = nullptr, *d_S2 = nullptr;
+  zd *d_Y = nullptr, *d_Ykeep = nullptr;
+  // factor
+  double *d_vn1 = nullptr, *d_vn2 = nullptr, *d_beta = nullptr;
+  int32_t *d_piv = nullptr;
+  zd *d_R = nullptr, *d_Wp = nullptr, *d_WpH = nullptr;
+  GridBarrier *d_bar = nullptr;
+  int *d_err = nullptr;
+  double rdiag_max = 0, rdiag_min = 0;
+  // products
+  zf *d_A32 = nullptr;
+  GemvPlan g_cg{}, g_hp{};
+  void *d_part = nullptr;
+  size_t part_bytes = 0;
+  double *d_qq = nullptr;
+  int nqq = 0;
+  double *d_red = nullptr;     // reduction partials
+  double *d_norms = nullptr;   // [0] = ||g||^2, [1] = ||x||^2
+  CgScalars *d_cg = nullptr;
+  // vectors
+  zd *d_r = nullptr, *d_g = nullptr, *d_u = nullptr, *d_s = nullptr, *d_p = nullptr, *d_w = nullptr,
+     *d_t = nullptr, *d_np = nullptr, *d_dy = nullptr, *d_yh = nullptr, *d_yl = nullptr, *d_vh = nullptr,
+     *d_vl = nullptr;
+  zf *d_w32 = nullptr;
+  void *d_q = nullptr;
+  zd *d_xh = nullptr, *d_xl = nullptr, *d_d = nullptr;
+  // host staging (minnorm_solve_host)
+  void *d_Ah = nullptr;
+  zd *d_bh = nullptr, *d_xo = nullptr;
+  // host pinned scalars
+  double *h_norms = nullptr;
+  CgScalars *h_cg = nullptr;
+  // timing
+  std::vector<KernelTimer> timers;
+  std::vector<cudaEvent_t> event_pool;
+  size_t event_next = 0;
+  int stat_launches[5] = {0, 0, 0, 0, 0};
+  double stat_ms[5] = {0, 0, 0, 0, 0};
+  float ms_sketch = 0, ms_qr = 0, ms_solve = 0;
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+#define CK(expr)                                   \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) {                       \
+      plan->failed = true;                         \
+      return MINNORM_ECUDA;                        \
+    }                                              \
+  } while (0)
+
+template <typename T>
+minnorm_status dalloc(minnorm_plan_t plan, T **ptr, size_t bytes) {
+  void *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return MINNORM_ENOMEM;
+  }
+  plan->allocs.push_back(p);
+  *ptr = reinterpret_cast<T *>(p);
+  return MINNORM_OK;
+}
+
+#define ALLOC(ptr, bytes)                               \
+  do {                                                  \
+    minnorm_status s_ = dalloc(plan, &(ptr), (bytes));  \
+    if (s_ != MINNORM_OK) return s_;                    \
+  } while (0)
+
+int ilog2(int64_t v) {
+  int k = 0;
+  while ((int64_t(1) << k) < v) ++k;
+  return k;
+}
+
+cudaEvent_t next_event(minnorm_plan_t plan) {
+  if (plan->event_next >= plan->event_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    plan->event_pool.push_back(e);
+  }
+  return plan->event_pool[plan->event_next++];
+}
+
+// Record a timed region around a kernel class when timing is on.
+struct Timed {
+  minnorm_plan_t plan;
+  int cls;
+  cudaEvent_t b{};
+  bool on;
+  Timed(minnorm_plan_t p, int c) : plan(p), cls(c), on((p->flags & MINNORM_FLAG_TIMING) != 0) {
+    if (on) {
+      cudaEvent_t a = next_event(plan);
+      b = next_event(plan);
+      cudaEventRecord(a, plan->st);
+      plan->timers.push_back({cls, a, b});
+    }
+  }
+  ~Timed() {
+    if (on) cudaEventRecord(b, plan->st);
+  }
+};
+
+void reset_stats(minnorm_plan_t plan) {
+  for (int k = 0; k < 5; ++k) { plan->stat_launches[k] = 0; plan->stat_ms[k] = 0; }
+}
+
+void collect_timers(minnorm_plan_t plan) {
+  for (auto &t : plan->timers) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      plan->stat_launches[t.cls] += 1;
+      plan->stat_ms[t.cls] += ms;
+    }
+  }
+  plan->timers.clear();
+  plan->event_next = 0;
+}
+
+// Upload the derived tables of the current parameters.
+minnorm_status upload_params(minnorm_plan_t plan) {
+  const int64_t n = plan->n, l = plan->l;
+  const SrftParams &P = plan->P;
+  const bool f32 = plan->fp32;
+  const size_t csz = f32 ? sizeof(zf) : sizeof(zd);
+  auto put_complex = [&](void *dst, const std::vector<std::complex<double>> &v) -> cudaError_t {
+    std::vector<unsigned char> buf(v.size() * csz);
+    for (size_t i = 0; i < v.size(); ++i) {
+      if (f32) {
+        zf z{(float)v[i].real(), (float)v[i].imag()};
+        memcpy(&buf[i * csz], &z, csz);
+      } else {
+        zd z{v[i].real(), v[i].imag()};
+        memcpy(&buf[i * csz], &z, csz);
+      }
+    }
+    return cudaMemcpy(dst, buf.data(), buf.size(), cudaMemcpyHostToDevice);
+  };
+  std::vector<std::complex<double>> tmp(n);
+  std::vector<int32_t> idx(n);
+  // chain 1: gather Pi~ after Z~  => v[j] = zeta~[pi~[j]] * conj(a[pi~[j]])
+  for (int64_t j = 0; j < n; ++j) { idx[j] = (int32_t)P.pi_t[j]; tmp[j] = P.zeta_t[P.pi_t[j]]; }
+  CK(cudaMemcpy(plan->d_idx1, idx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+  CK(put_complex(plan->d_ph1, tmp));
+  for (int64_t j = 0; j < n; ++j) tmp[j] = j < n - 1 ? std::complex<double>(cos(P.theta_t[j]), sin(P.theta_t[j]))
+                                                     : std::complex<double>(1.0, 0.0);
+  CK(put_complex(plan->d_cs1, tmp));
+  // chain 2: Z then Pi  => v[j] = zeta[pi[j]] * w[pi[j]]
+  for (int64_t j = 0; j < n; ++j) { idx[j] = (int32_t)P.pi[j]; tmp[j] = P.zeta[P.pi[j]]; }
+  CK(cudaMemcpy(plan->d_idx2, idx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+  CK(put_complex(plan->d_ph2, tmp));
+  for (int64_t j = 0; j < n; ++j) tmp[j] = j < n - 1 ? std::complex<double>(cos(P.theta[j]), sin(P.theta[j]))
+                                                     : std::complex<double>(1.0, 0.0);
+  CK(put_complex(plan->d_cs2, tmp));
+  CK(put_complex(plan->d_post, P.d));
+  // halos
+  const double tol = (f32 ? 0x1.0p-42 : 0x1.0p-72) / std::sqrt((double)n);
+  int h1 = 0, h2 = 0;
+  std::vector<int32_t> halo1 = chain_halos(P.theta_t, n, kSeg, tol, &h1);
+  std::vector<int32_t> halo2 = chain_halos(P.theta, n, kSeg, tol, &h2);
+  if (std::min<int64_t>(kSeg, n) + std::max(h1, h2) + 1 > kChainCap) return MINNORM_ENOTSUP;
+  plan->cap1 = (int)std::min<int64_t>(kSeg, n) + h1 + 1;
+  plan->cap2 = (int)std::min<int64_t>(kSeg, n) + h2 + 1;
+  CK(cudaMemcpy(plan->d_halo1, halo1.data(), sizeof(int32_t) * halo1.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(plan->d_halo2, halo2.data(), sizeof(int32_t) * halo2.size(), cudaMemcpyHostToDevice));
+  // samples: for each output t, where X[s_t] sits in the pass that produces it
+  const int logn = plan->logn, logN1 = plan->logN1;
+  std::vector<int32_t> off, st_t(l), st_loc(l);
+  if (logN1 == 0) {
+    off = {0, (int32_t)l};
+    for (int64_t t = 0; t < l; ++t) { st_t[t] = (int32_t)t; st_loc[t] = (int32_t)P.s[t]; }
+  } else {
+    const int64_t N1 = int64_t(1) << logN1, N2 = int64_t(1) << (logn - logN1);
+    const int64_t nb = N2 / plan->tk;
+    std::vector<int32_t> cnt(nb + 1, 0);
+    for (int64_t t = 0; t < l; ++t) cnt[(P.s[t] % N2) / plan->tk + 1] += 1;
+    for (int64_t b = 0; b < nb; ++b) cnt[b + 1] += cnt[b];
+    off = cnt;
+    std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t t = 0; t < l; ++t) {
+      const int64_t k = P.s[t], k2 = k % N2, k1 = k / N2, b = k2 / plan->tk, kk = k2 - b * plan->tk;
+      const int32_t pos = fill[b]++;
+      st_t[pos] = (int32_t)t;
+      st_loc[pos] = (int32_t)(kk * N1 + k1);
+    }
+  }
+  CK(cudaMemcpy(plan->d_samp_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(plan->d_samp_t, st_t.data(), sizeof(int32_t) * l, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(plan->d_samp_loc, st_loc.data(), sizeof(int32_t) * l, cudaMemcpyHostToDevice));
+  // twiddles e^{-2 pi i k / n}
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int64_t k = 0; k < n; ++k) {
+    const double a = two_pi * (double)k / (double)n;
+    tmp[k] = std::complex<double>(cos(a), -sin(a));
+  }
+  CK(put_complex(plan->d_tw, tmp));
+  plan->sketched = false;
+  return MINNORM_OK;
+}
+
+minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l, minnorm_dtype dtype,
+                           minnorm_precision prec, uint64_t seed, uint32_t flags, void *stream) {
+  plan->m = m;
+  plan->n = n;
+  plan->l = l;
+  plan->dtype = dtype;
+  plan->prec = prec;
+  plan->flags = flags;
+  plan->st = (cudaStream_t)stream;
+  plan->fp32 = (prec == MINNORM_MIXED);
+  CK(cudaGetDevice(&plan->device));
+  CK(cudaDeviceGetAttribute(&plan->sms, cudaDevAttrMultiProcessorCount, plan->device));
+  // FFT geometry (powers of two)
+  plan->logn = ilog2(n);
+  const int cap = plan->fp32 ? 8192 : 4096;
+  if (n <= cap) {
+    plan->logN1 = 0;
+  } else {
+    plan->logN1 = plan->logn / 2;
+    const int64_t N1 = int64_t(1) << plan->logN1, N2 = n / N1;
+    if (N2 > cap) return MINNORM_ENOTSUP;
+    plan->tj = (int)std::min<int64_t>(N1, cap / N2);
+    plan->tk = (int)std::min<int64_t>(N2, cap / N1);
+  }
+  const size_t rc = plan->fp32 ? sizeof(zf) : sizeof(zd);  // compute complex size
+  const int64_t nseg = (n + kSeg - 1) / kSeg;
+  ALLOC(plan->d_idx1, sizeof(int32_t) * n);
+  ALLOC(plan->d_idx2, sizeof(int32_t) * n);
+  ALLOC(plan->d_halo1, sizeof(int32_t) * nseg);
+  ALLOC(plan->d_halo2, sizeof(int32_t) * nseg);
+  ALLOC(plan->d_ph1, rc * n);
+  ALLOC(plan->d_ph2, rc * n);
+  ALLOC(plan->d_cs1, rc * n);
+  ALLOC(plan->d_cs2, rc * n);
+  ALLOC(plan->d_post, rc * n);
+  ALLOC(plan->d_tw, rc * n);
+  const int64_t nbB = plan->logN1 ? ((n >> plan->logN1) / plan->tk) : 1;
+  ALLOC(plan->d_samp_off, sizeof(int32_t) * (nbB + 1));
+  ALLOC(plan->d_samp_t, sizeof(int32_t) * l);
+  ALLOC(plan->d_samp_loc, sizeof(int32_t) * l);
+  ALLOC(plan->d_S1, rc * (size_t)m * n);
+  ALLOC(plan->d_S2, rc * (size_t)m * n);
+  ALLOC(plan->d_Y, sizeof(zd) * (size_t)l * m);
+  if (flags & MINNORM_FLAG_KEEP_SKETCH) ALLOC(plan->d_Ykeep, sizeof(zd) * (size_t)l * m);
+  ALLOC(plan->d_vn1, sizeof(double) * 2 * m);
+  ALLOC(plan->d_vn2, sizeof(double) * m);
+  ALLOC(plan->d_beta, sizeof(double) * m);
+  ALLOC(plan->d_piv, sizeof(int32_t) * m);
+  ALLOC(plan->d_R, sizeof(zd) * (size_t)m * m);
+  ALLOC(plan->d_Wp, sizeof(zd) * (size_t)m * m);
+  ALLOC(plan->d_WpH, sizeof(zd) * (size_t)m * m);
+  ALLOC(plan->d_bar, sizeof(GridBarrier));
+  ALLOC(plan->d_err, sizeof(int));
+  if (plan->fp32 && dtype == MINNORM_C128) ALLOC(plan->d_A32, sizeof(zf) * (size_t)m * n);
+  // products: g_cg for the CG passes, g_hp for FP64 / double-double passes on the stored A
+  const int hp_mode = dtype == MINNORM_C128 ? 0 : 2;
+  gemv_configure(plan->g_hp, m, n, n, hp_mode, plan->sms);
+  gemv_configure(plan->g_cg, m, n, n, plan->fp32 ? 1 : hp_mode, plan->sms);
+  size_t pb = 0;
+  pb = std::max(pb, gemv_adj_partial_elems(plan->g_cg) * rc);
+  pb = std::max(pb, gemv_fwd_partial_elems(plan->g_cg) * rc);
+  pb = std::max(pb, gemv_adj_partial_elems(plan->g_hp) * sizeof(zd));
+  pb = std::max(pb, gemv_fwd_partial_elems(plan->g_hp) * sizeof(zd));
+  pb = std::max(pb, 2 * fwd_dd_partial_elems(plan->g_hp) * sizeof(zd));
+  plan->part_bytes = pb;
+  ALLOC(plan->d_part, pb);
+  plan->nqq = (int)std::min<int64_t>(1024, (n + 255) / 256);
+  ALLOC(plan->d_qq, sizeof(double) * 1024);
+  ALLOC(plan->d_red, sizeof(double) * 2048);
+  ALLOC(plan->d_norms, sizeof(double) * 4);
+  ALLOC(plan->d_cg, sizeof(CgScalars));
+  zd **mvecs[] = {&plan->d_r, &plan->d_g, &plan->d_u, &plan->d_s, &plan->d_p, &plan->d_w, &plan->d_t,
+                  &plan->d_np, &plan->d_dy, &plan->d_yh, &plan->d_yl, &plan->d_vh, &plan->d_vl};
+  for (zd **v : mvecs) ALLOC(*v, sizeof(zd) * m);
+  ALLOC(plan->d_w32, sizeof(zf) * m);
+  ALLOC(plan->d_q, rc * n);
+  ALLOC(plan->d_xh, sizeof(zd) * n);
+  ALLOC(plan->d_xl, sizeof(zd) * n);
+  ALLOC(plan->d_d, sizeof(zd) * n);
+  if (cudaMallocHost(&plan->h_norms, sizeof(double) * 4) != cudaSuccess) return MINNORM_ENOMEM;
+  if (cudaMallocHost(&plan->h_cg, sizeof(CgScalars)) != cudaSuccess) return MINNORM_ENOMEM;
+  draw_srft_params(seed, n, l, plan->P);
+  return upload_params(plan);
+}
+
+// ---- Step 1 + Step 2 --------------------------------------------------------
+minnorm_status sketch_impl(minnorm_plan_t plan, const void *A, int64_t lda) {
+  cudaStream_t st = plan->st;
+  const int64_t m = plan->m, n = plan->n, l = plan->l;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  const bool timing = plan->flags & MINNORM_FLAG_TIMING;
+  reset_stats(plan);
+  if (timing) {
+    e0 = next_event(plan); e1 = next_event(plan); e2 = next_event(plan);
+    CK(cudaEventRecord(e0, st));
+  }
+  const void *src = A;
+  int64_t lds = lda;
+  bool src_c64 = plan->dtype == MINNORM_C64;
+  if (plan->fp32 && plan->dtype == MINNORM_C128) {
+    CK(launch_to_c64(A, lda, plan->d_A32, n, m, n, st));
+    src = plan->d_A32;
+    lds = n;
+    src_c64 = true;
+  }
+  {
+    Timed tm(plan, 4);
+    ChainArgs c1{src, lds, plan->d_S1, n, plan->d_idx1, plan->d_ph1, plan->d_cs1, nullptr, plan->d_halo1,
+                 (int)n, kSeg, plan->cap1, (int)m, src_c64, true, plan->fp32};
+    CK(launch_chain(c1, st));
+    ChainArgs c2{plan->d_S1, n, plan->d_S2, n, plan->d_idx2, plan->d_ph2, plan->d_cs2, plan->d_post,
+                 plan->d_halo2, (int)n, kSeg, plan->cap2, (int)m, plan->fp32, false, plan->fp32};
+    CK(launch_chain(c2, st));
+    FftArgs f{plan->d_S2, n, plan->d_S1, plan->d_tw, plan->logn, plan->logN1, plan->tj, plan->tk,
+              plan->d_samp_off, plan->d_samp_t, plan->d_samp_loc, (int)l, (int)m, plan->d_Y, l, 0, plan->fp32};
+    CK(launch_fft(f, st));
+  }
+  if (plan->d_Ykeep) CK(cudaMemcpyAsync(plan->d_Ykeep, plan->d_Y, sizeof(zd) * l * m, cudaMemcpyDeviceToDevice, st));
+  if (timing) CK(cudaEventRecord(e1, st));
+  {
+    Timed tm(plan, 3);
+    CK(cudaMemsetAsync(plan->d_bar, 0, sizeof(GridBarrier), st));
+    CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
+    QrArgs q{plan->d_Y, (int)l, (int)m, plan->d_vn1, plan->d_vn2, plan->d_beta, plan->d_piv, plan->d_R,
+             plan->d_bar, plan->d_err, kBarrierLimitNs};
+    CK(launch_qrp(q, st));
+    CK(launch_prinv(plan->d_R, plan->d_piv, (int)m, plan->d_Wp, plan->d_WpH, st));
+  }
+  if (timing) CK(cudaEventRecord(e2, st));
+  int err = 0;
+  double b0 = 0, bm = 0;
+  CK(cudaMemcpyAsync(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&b0, plan->d_beta, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&bm, plan->d_beta + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (timing) {
+    cudaEventElapsedTime(&plan->ms_sketch, e0, e1);
+    cudaEventElapsedTime(&plan->ms_qr, e1, e2);
+    collect_timers(plan);
+  }
+  if (err) {
+    plan->failed = true;
+    return MINNORM_ETIMEOUT;
+  }
+  plan->rdiag_max = std::fabs(b0);
+  plan->rdiag_min = std::fabs(bm);
+  plan->sketched = true;
+  if (!(plan->rdiag_min > 64.0 * (double)m * 0x1.0p-53 * plan->rdiag_max)) return MINNORM_ERANK;
+  return MINNORM_OK;
+}
+
+// ---- Steps 3-5 --------------------------------------------------------------
+// Inner solve: CG on (Wp^* A A^* Wp) du = g, Wp = P R^{-1}; dy = Wp du.
+minnorm_status inner_cg(minnorm_plan_t plan, const void *Acg, double tol, int maxit, int *iters) {
+  cudaStream_t st = plan->st;
+  const int m = (int)plan->m;
+  const int *done = &plan->d_cg->done;
+  CK(launch_cg_init(m, plan->d_g, plan->d_u, plan->d_s, plan->d_p, plan->d_cg, st));
+  const int chunk = plan->fp32 ? 4 : 8;
+  int it = 0;
+  while (it < maxit) {
+    const int todo = std::min(chunk, maxit - it);
+    for (int k = 0; k < todo; ++k) {
+      if (plan->fp32) {
+        CK(launch_small_gemv(plan->d_Wp, m, plan->d_p, plan->d_w, plan->d_w32, done, st));
+        { Timed tm(plan, 0); CK(launch_gemv_adj_f32(plan->g_cg, Acg, plan->d_w32, plan->d_q, plan->d_part, plan->d_qq, done, st)); }
+        { Timed tm(plan, 1); CK(launch_gemv_fwd_f32(plan->g_cg, Acg, plan->d_q, plan->d_t, plan->d_part, done, st)); }
+      } else {
+        CK(launch_small_gemv(plan->d_Wp, m, plan->d_p, plan->d_w, nullptr, done, st));
+        { Timed tm(plan, 0); CK(launch_gemv_adj(plan->g_cg, Acg, plan->d_w, plan->d_q, plan->d_part, plan->d_qq, done, st)); }
+        { Timed tm(plan, 1); CK(launch_gemv_fwd(plan->g_cg, Acg, plan->d_q, plan->d_t, plan->d_part, done, st)); }
+      }
+      CK(launch_small_gemv(plan->d_WpH, m, plan->d_t, plan->d_np, nullptr, done, st));
+      CK(launch_cg_update(m, plan->d_qq, plan->nqq, plan->d_np, plan->d_u, plan->d_s, plan->d_p, plan->d_cg,
+                          tol * tol, st));
+    }
+    it += todo;
+    CK(cudaMemcpyAsync(plan->h_cg, plan->d_cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (plan->h_cg->done) break;
+  }
+  *iters = plan->h_cg->iters;
+  // dy = Wp u
+  CK(launch_small_gemv(plan->d_Wp, m, plan->d_u, plan->d_dy, nullptr, nullptr, st));
+  return MINNORM_OK;
+}
+
+minnorm_status norms(minnorm_plan_t plan, bool with_x, double *gnorm, double *xnorm) {
+  cudaStream_t st = plan->st;
+  CK(launch_sumsq(plan->m, plan->d_g, plan->d_red, plan->d_norms, st));
+  if (with_x) CK(launch_sumsq(plan->n, plan->d_xh, plan->d_red + 1024, plan->d_norms + 1, st));
+  CK(cudaMemcpyAsync(plan->h_norms, plan->d_norms, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *gnorm = std::sqrt(plan->h_norms[0]);
+  *xnorm = with_x ? std::sqrt(plan->h_norms[1]) : 0.0;
+  return MINNORM_OK;
+}
+
+minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const void *b, double eps, void *x,
+                          minnorm_info *info) {
+  cudaStream_t st = plan->st;
+  const int64_t m = plan->m, n = plan->n;
+  (void)lda;
+  const bool timing = plan->flags & MINNORM_FLAG_TIMING;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (timing) { e0 = next_event(plan); e1 = next_event(plan); CK(cudaEventRecord(e0, st)); }
+  const void *Acg = plan->d_A32 ? (const void *)plan->d_A32 : A;
+  // y = 0, x = 0, r = b
+  CK(cudaMemsetAsync(plan->d_yh, 0, sizeof(zd) * m, st));
+  CK(cudaMemsetAsync(plan->d_yl, 0, sizeof(zd) * m, st));
+  CK(cudaMemsetAsync(plan->d_xh, 0, sizeof(zd) * n, st));
+  CK(cudaMemsetAsync(plan->d_xl, 0, sizeof(zd) * n, st));
+  CK(cudaMemcpyAsync(plan->d_r, b, sizeof(zd) * m, cudaMemcpyDeviceToDevice, st));
+  const double kappa = plan->rdiag_max / std::max(plan->rdiag_min, 1e-300);
+  const double tol_inner = plan->fp32 ? 1e-3 : 1e-11;
+  const int maxit = plan->fp32 ? 40 : 300;
+  double err = INFINITY, best = INFINITY, prev = INFINITY;
+  int cg_total = 0, dd_passes = 0, fp_passes = 0, outer = 0, stagnant = 0;
+  minnorm_status status = MINNORM_ENOCONV;
+  for (outer = 0; outer < kMaxOuter; ++outer) {
+    // g = Wp^* r (the preconditioned residual), and the bound ||x - p|| <= ||g||
+    CK(launch_small_gemv(plan->d_WpH, (int)m, plan->d_r, plan->d_g, nullptr, nullptr, st));
+    double gnorm = 0, xnorm = 0;
+    minnorm_status s = norms(plan, outer > 0, &gnorm, &xnorm);
+    if (s != MINNORM_OK) return s;
+    if (outer > 0) {
+      err = xnorm > 0 ? gnorm / xnorm : INFINITY;
+      if (err <= eps) { status = MINNORM_OK; break; }
+      if (err < best) best = err;
+      stagnant = (err > 0.5 * prev) ? stagnant + 1 : 0;
+      if (stagnant >= 2) { status = MINNORM_EFLOOR; break; }
+      prev = err;
+    } else if (gnorm == 0.0) {
+      err = 0.0;
+      status = MINNORM_OK;
+      break;
+    }
+    int it = 0;
+    s = inner_cg(plan, Acg, tol_inner, maxit, &it);
+    if (s != MINNORM_OK) return s;
+    cg_total += it;
+    CK(launch_dd_accumulate(m, plan->d_yh, plan->d_yl, plan->d_dy, st));
+    // correction relative size ~ err (the bound before this step); FP64 suffices
+    // for the update when its cancellation error kappa * 2^-53 * err stays well below eps
+    const bool use_dd = (outer == 0) || (8.0 * kappa * 0x1.0p-53 * err > 0.25 * eps);
+    if (use_dd) {
+      Timed tm(plan, 2);
+      CK(launch_adj_dd(plan->g_hp, A, plan->d_yh, plan->d_yl, plan->d_xh, plan->d_xl, st));
+      CK(launch_fwd_dd(plan->g_hp, A, plan->d_xh, plan->d_xl, plan->d_vh, plan->d_vl, plan->d_part, st));
+      CK(launch_resid_finish(m, b, plan->d_vh, plan->d_vl, plan->d_r, st));
+      dd_passes += 2;
+    } else {
+      CK(launch_gemv_adj(plan->g_hp, A, plan->d_dy, plan->d_d, plan->d_part, nullptr, nullptr, st));
+      CK(launch_dd_accumulate(n, plan->d_xh, plan->d_xl, plan->d_d, st));
+      CK(launch_gemv_fwd(plan->g_hp, A, plan->d_d, plan->d_t, plan->d_part, nullptr, st));
+      CK(launch_sub(m, plan->d_r, plan->d_t, st));
+      fp_passes += 2;
+    }
+  }
+  if (status == MINNORM_ENOCONV && outer == kMaxOuter) {
+    // final bound for the last iterate
+    CK(launch_small_gemv(plan->d_WpH, (int)m, plan->d_r, plan->d_g, nullptr, nullptr, st));
+    double gnorm = 0, xnorm = 0;
+    minnorm_status s = norms(plan, true, &gnorm, &xnorm);
+    if (s != MINNORM_OK) return s;
+    err = xnorm > 0 ? gnorm / xnorm : INFINITY;
+    if (err <= eps) status = MINNORM_OK;
+  }
+  CK(cudaMemcpyAsync(x, plan->d_xh, sizeof(zd) * n, cudaMemcpyDeviceToDevice, st));
+  if (timing) CK(cudaEventRecord(e1, st));
+  if (info || timing) {
+    CK(launch_sumsq(m, plan->d_r, plan->d_red, plan->d_norms + 2, st));
+    CK(launch_sumsq(m, (const zd *)b, plan->d_red + 1024, plan->d_norms + 3, st));
+    CK(cudaMemcpyAsync(plan->h_norms, plan->d_norms, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  if (timing) {
+    cudaEventElapsedTime(&plan->ms_solve, e0, e1);
+    collect_timers(plan);
+  }
+  if (info) {
+    info->outer_steps = outer;
+    info->cg_iters = cg_total;
+    info->dd_passes = dd_passes;
+    info->fp64_passes = fp_passes;
+    info->err_bound = err;
+    const double bn = std::sqrt(plan->h_norms[3]);
+    info->resid_rel = bn > 0 ? std::sqrt(plan->h_norms[2]) / bn : 0.0;
+    info->rdiag_max = plan->rdiag_max;
+    info->rdiag_min = plan->rdiag_min;
+    info->ms_sketch = plan->ms_sketch;
+    info->ms_qr = plan->ms_qr;
+    info->ms_solve = plan->ms_solve;
+    info->reserved = 0;
+  }
+  return status;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+// =============================================================================
+extern "C" {
+
+const char *minnorm_status_string(minnorm_status s) {
+  switch (s) {
+    case MINNORM_OK: return "MINNORM_OK";
+    case MINNORM_EINVAL: return "MINNORM_EINVAL: invalid argument";
+    case MINNORM_ESTATE: return "MINNORM_ESTATE: call order or failed plan";
+    case MINNORM_ENOMEM: return "MINNORM_ENOMEM: allocation failed";
+    case MINNORM_ECUDA: return "MINNORM_ECUDA: a CUDA call failed";
+    case MINNORM_ERANK: return "MINNORM_ERANK: sketch numerically rank deficient";
+    case MINNORM_ENOCONV: return "MINNORM_ENOCONV: refinement step cap reached";
+    case MINNORM_EFLOOR: return "MINNORM_EFLOOR: refinement stagnated above eps";
+    case MINNORM_ETIMEOUT: return "MINNORM_ETIMEOUT: a bounded device wait expired";
+    case MINNORM_ENOTSUP: return "MINNORM_ENOTSUP: unsupported size";
+  }
+  return "MINNORM_UNKNOWN";
+}
+
+minnorm_status minnorm_plan_create(minnorm_plan_t *out, int64_t m, int64_t n, int64_t l, minnorm_dtype dtype,
+                                   minnorm_precision prec, uint64_t seed, uint32_t flags, void *stream) {
+  if (!out) return MINNORM_EINVAL;
+  *out = nullptr;
+  if (m < 1 || n < 2 || m >= n) return MINNORM_EINVAL;
+  if (l == 0) l = std::min<int64_t>(4 * m, n);
+  if (l <= m || l > n) return MINNORM_EINVAL;
+  if (dtype != MINNORM_C128 && dtype != MINNORM_C64) return MINNORM_EINVAL;
+  if (prec != MINNORM_FP64 && prec != MINNORM_MIXED) return MINNORM_EINVAL;
+  if ((flags & ~(MINNORM_FLAG_TIMING | MINNORM_FLAG_KEEP_SKETCH)) != 0) return MINNORM_EINVAL;
+  if ((n & (n - 1)) != 0) return MINNORM_ENOTSUP;        // the FFT handles powers of two
+  if (n > (int64_t(1) << 30) || m > 4864) return MINNORM_ENOTSUP;
+  minnorm_plan_t plan = new (std::nothrow) minnorm_plan_s();
+  if (!plan) return MINNORM_ENOMEM;
+  minnorm_status s = create_impl(plan, m, n, l, dtype, prec, seed, flags, stream);
+  if (s != MINNORM_OK) {
+    minnorm_plan_destroy(plan);
+    return s;
+  }
+  *out = plan;
+  return MINNORM_OK;
+}
+
+minnorm_status minnorm_plan_set_params(minnorm_plan_t plan, const double *zeta_t, const int64_t *pi_t,
+                                       const double *theta_t, const double *zeta, const int64_t *pi,
+                                       const double *theta, const double *d, const int64_t *s) {
+  if (!plan || !zeta_t || !pi_t || !theta_t || !zeta || !pi || !theta || !d || !s) return MINNORM_EINVAL;
+  const int64_t n = plan->n, l = plan->l;
+  SrftParams Q;
+  Q.n = n;
+  Q.l = l;
+  auto cplx = [&](const double *src, std::vector<std::complex<double>> &dst) {
+    dst.resize(n);
+    for (int64_t j = 0; j < n; ++j) dst[j] = std::complex<double>(src[2 * j], src[2 * j + 1]);
+  };
+  cplx(zeta_t, Q.zeta_t);
+  cplx(zeta, Q.zeta);
+  cplx(d, Q.d);
+  Q.pi_t.assign(pi_t, pi_t + n);
+  Q.pi.assign(pi, pi + n);
+  Q.theta_t.assign(theta_t, theta_t + (n - 1));
+  Q.theta.assign(theta, theta + (n - 1));
+  Q.s.assign(s, s + l);
+  if (!validate_srft_params(Q)) return MINNORM_EINVAL;
+  SrftParams old = plan->P;
+  plan->P = Q;
+  minnorm_status st = upload_params(plan);
+  if (st == MINNORM_ENOTSUP) {
+    plan->P = old;
+    minnorm_status back = upload_params(plan);
+    return back == MINNORM_OK ? MINNORM_ENOTSUP : back;
+  }
+  return st;
+}
+
+minnorm_status minnorm_sketch(minnorm_plan_t plan, const void *A, int64_t lda) {
+  if (!plan || !A) return MINNORM_EINVAL;
+  if (plan->failed) return MINNORM_ESTATE;
+  if (lda < plan->n) return MINNORM_EINVAL;
+  if (!aligned16(A) && plan->dtype == MINNORM_C128) return MINNORM_EINVAL;
+  plan->sketched = false;
+  plan->g_hp.ld = lda;
+  plan->g_cg.ld = plan->d_A32 ? plan->n : lda;
+  return sketch_impl(plan, A, lda);
+}
+
+minnorm_status minnorm_solve(minnorm_plan_t plan, const void *A, int64_t lda, const void *b, double eps, void *x,
+                             minnorm_info *info) {
+  if (!plan || !A || !b || !x) return MINNORM_EINVAL;
+  if (plan->failed) return MINNORM_ESTATE;
+  if (!plan->sketched) return MINNORM_ESTATE;
+  if (lda < plan->n) return MINNORM_EINVAL;
+  if (!(eps > 0.0 && eps < 1.0)) return MINNORM_EINVAL;
+  plan->g_hp.ld = lda;
+  plan->g_cg.ld = plan->d_A32 ? plan->n : lda;
+  return solve_impl(plan, A, lda, b, eps, x, info);
+}
+
+minnorm_status minnorm_solve_host(minnorm_plan_t plan, const void *A_host, int64_t lda, const void *b_host,
+                                  double eps, void *x_host, minnorm_info *info) {
+  if (!plan || !A_host || !b_host || !x_host) return MINNORM_EINVAL;
+  if (plan->failed) return MINNORM_ESTATE;
+  if (lda < plan->n) return MINNORM_EINVAL;
+  if (!(eps > 0.0 && eps < 1.0)) return MINNORM_EINVAL;
+  const int64_t m = plan->m, n = plan->n;
+  const size_t es = plan->dtype == MINNORM_C128 ? sizeof(zd) : sizeof(zf);
+  if (!plan->d_Ah) {
+    ALLOC(plan->d_Ah, es * (size_t)m * n);
+    ALLOC(plan->d_bh, sizeof(zd) * m);
+    ALLOC(plan->d_xo, sizeof(zd) * n);
+  }
+  cudaStream_t st = plan->st;
+  CK(cudaMemcpy2DAsync(plan->d_Ah, es * n, A_host, es * lda, es * n, m, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(plan->d_bh, b_host, sizeof(zd) * m, cudaMemcpyHostToDevice, st));
+  minnorm_status s = minnorm_sketch(plan, plan->d_Ah, n);
+  if (s != MINNORM_OK) return s;
+  minnorm_status r = minnorm_solve(plan, plan->d_Ah, n, plan->d_bh, eps, plan->d_xo, info);
+  if (r != MINNORM_OK && r != MINNORM_ENOCONV && r != MINNORM_EFLOOR) return r;
+  CK(cudaMemcpyAsync(x_host, plan->d_xo, sizeof(zd) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return r;
+}
+
+minnorm_status minnorm_plan_destroy(minnorm_plan_t plan) {
+  if (!plan) return MINNORM_OK;
+  if (plan->st) cudaStreamSynchronize(plan->st);
+  else cudaDeviceSynchronize();
+  for (void *p : plan->allocs) cudaFree(p);
+  for (cudaEvent_t e : plan->event_pool) cudaEventDestroy(e);
+  if (plan->h_norms) cudaFreeHost(plan->h_norms);
+  if (plan->h_cg) cudaFreeHost(plan->h_cg);
+  delete plan;
+  return MINNORM_OK;
+}
+
+minnorm_status minnorm_get_sketch(minnorm_plan_t plan, void *Y_out) {
+  if (!plan || !Y_out) return MINNORM_EINVAL;
+  if (!plan->d_Ykeep || !plan->sketched) return MINNORM_ESTATE;
+  if (cudaMemcpyAsync(Y_out, plan->d_Ykeep, sizeof(zd) * plan->l * plan->m, cudaMemcpyDeviceToDevice, plan->st) !=
+      cudaSuccess)
+    return MINNORM_ECUDA;
+  return MINNORM_OK;
+}
+
+namespace {
+__global__ void piv_widen_kernel(const int32_t *a, int64_t *b, int m) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) b[i] = a[i];
+}
+}  // namespace
+
+minnorm_status minnorm_get_factor(minnorm_plan_t plan, void *R_out, void *piv_out) {
+  if (!plan || !R_out || !piv_out) return MINNORM_EINVAL;
+  if (!plan->sketched) return MINNORM_ESTATE;
+  CK(cudaMemcpyAsync(R_out, plan->d_R, sizeof(zd) * plan->m * plan->m, cudaMemcpyDeviceToDevice, plan->st));
+  piv_widen_kernel<<<(int)((plan->m + 255) / 256), 256, 0, plan->st>>>(plan->d_piv, (int64_t *)piv_out, (int)plan->m);
+  CK(cudaGetLastError());
+  return MINNORM_OK;
+}
+
+minnorm_status minnorm_cg_products(minnorm_plan_t plan, const void *A, int64_t lda, const void *w, void *q,
+                                   void *t) {
+  if (!plan || !A || !w) return MINNORM_EINVAL;
+  if (lda < plan->n) return MINNORM_EINVAL;
+  if (!plan->sketched) return MINNORM_ESTATE;
+  plan->g_hp.ld = lda;
+  plan->g_cg.ld = plan->d_A32 ? plan->n : lda;
+  cudaStream_t st = plan->st;
+  const int64_t m = plan->m, n = plan->n;
+  const void *Acg = plan->d_A32 ? (const void *)plan->d_A32 : A;
+  if (plan->fp32) {
+    CK(launch_narrow(m, w, plan->d_w32, st));
+    CK(launch_gemv_adj_f32(plan->g_cg, Acg, plan->d_w32, plan->d_q, plan->d_part, plan->d_qq, nullptr, st));
+    if (q) CK(launch_widen(n, plan->d_q, q, st));
+    if (t) CK(launch_gemv_fwd_f32(plan->g_cg, Acg, plan->d_q, t, plan->d_part, nullptr, st));
+  } else {
+    CK(launch_gemv_adj(plan->g_cg, Acg, w, plan->d_q, plan->d_part, plan->d_qq, nullptr, st));
+    if (q) CK(cudaMemcpyAsync(q, plan->d_q, sizeof(zd) * n, cudaMemcpyDeviceToDevice, st));
+    if (t) CK(launch_gemv_fwd(plan->g_cg, Acg, plan->d_q, t, plan->d_part, nullptr, st));
+  }
+  return MINNORM_OK;
+}
+
+minnorm_status minnorm_residual_dd(minnorm_plan_t plan, const void *A, int64_t lda, const void *y_hi,
+                                   const void *y_lo, const void *b, void *r, void *x_hi, void *x_lo) {
+  if (!plan || !A || !y_hi || !b || !r || !x_hi || !x_lo) return MINNORM_EINVAL;
+  if (lda < plan->n) return MINNORM_EINVAL;
+  plan->g_hp.ld = lda;
+  cudaStream_t st = plan->st;
+  CK(launch_adj_dd(plan->g_hp, A, y_hi, y_lo, x_hi, x_lo, st));
+  CK(launch_fwd_dd(plan->g_hp, A, x_hi, x_lo, plan->d_vh, plan->d_vl, plan->d_part, st));
+  CK(launch_resid_finish(plan->m, b, plan->d_vh, plan->d_vl, r, st));
+  return MINNORM_OK;
+}
+
+minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *launches, double *ms) {
+  if (!plan || k < 0 || k > 4 || !launches || !ms) return MINNORM_EINVAL;
+  *launches = plan->stat_launches[k];
+  *ms = plan->stat_ms[k];
+  return MINNORM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+"""Python binding of libminnorm.so (include/minnorm.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls and passes plain
+pointers and sizes; torch tensors supply device memory and the current CUDA
+stream. All computation happens in the library's sm_103a kernels. If the
+library is missing or cannot be loaded this module raises: there is no CPU
+fallback.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libminnorm.so")
+
+OK, EINVAL, ESTATE, ENOMEM, ECUDA, ERANK, ENOCONV, EFLOOR, ETIMEOUT, ENOTSUP = range(10)
+STATUS_NAMES = ["OK", "EINVAL", "ESTATE", "ENOMEM", "ECUDA", "ERANK", "ENOCONV", "EFLOOR",
+                "ETIMEOUT", "ENOTSUP"]
+C128, C64 = 0, 1
+FP64, MIXED = 0, 1
+FLAG_TIMING, FLAG_KEEP_SKETCH = 1, 2
+
+# every symbol include/minnorm.h declares
+EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_sketch", "minnorm_solve",
+           "minnorm_solve_host", "minnorm_plan_destroy", "minnorm_status_string", "minnorm_get_sketch",
+           "minnorm_get_factor", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats"]
+
+
+class MinnormError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s" % (where, status_string(status)))
+
+
+class Info(C.Structure):
+    _fields_ = [("outer_steps", C.c_int32), ("cg_iters", C.c_int32), ("dd_passes", C.c_int32),
+                ("fp64_passes", C.c_int32), ("err_bound", C.c_double), ("resid_rel", C.c_double),
+                ("rdiag_max", C.c_double), ("rdiag_min", C.c_double), ("ms_sketch", C.c_float),
+                ("ms_qr", C.c_float), ("ms_solve", C.c_float), ("reserved", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lib = None
+
+
+def lib():
+    """Load libminnorm.so (build it first with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libminnorm.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        p, i64, u64, u32, i32, d = C.c_void_p, C.c_int64, C.c_uint64, C.c_uint32, C.c_int32, C.c_double
+        L.minnorm_plan_create.argtypes = [C.POINTER(p), i64, i64, i64, C.c_int, C.c_int, u64, u32, p]
+        L.minnorm_plan_set_params.argtypes = [p] * 9
+        L.minnorm_sketch.argtypes = [p, p, i64]
+        L.minnorm_solve.argtypes = [p, p, i64, p, d, p, C.POINTER(Info)]
+        L.minnorm_solve_host.argtypes = [p, p, i64, p, d, p, C.POINTER(Info)]
+        L.minnorm_plan_destroy.argtypes = [p]
+        L.minnorm_status_string.argtypes = [C.c_int]
+        L.minnorm_status_string.restype = C.c_char_p
+        L.minnorm_get_sketch.argtypes = [p, p]
+        L.minnorm_get_factor.argtypes = [p, p, p]
+        L.minnorm_cg_products.argtypes = [p, p, i64, p, p, p]
+        L.minnorm_residual_dd.argtypes = [p, p, i64, p, p, p, p, p, p]
+        L.minnorm_kernel_stats.argtypes = [p, i32, C.POINTER(i32), C.POINTER(d)]
+        for name in EXPORTS:
+            if name != "minnorm_status_string":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(status):
+    return lib().minnorm_status_string(int(status)).decode()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):
+        return t.ctypes.data
+    raise TypeError("expected a tensor, an array or an address")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _check(status, where, allow=(OK,)):
+    if status not in allow:
+        raise MinnormError(status, where)
+    return status
+
+
+def minnorm_plan_create(m, n, l=0, dtype=C128, precision=FP64, seed=1, flags=0, stream=None):
+    h = C.c_void_p()
+    st = lib().minnorm_plan_create(C.byref(h), int(m), int(n), int(l), int(dtype), int(precision),
+                                   int(seed) & 0xFFFFFFFFFFFFFFFF, int(flags), _stream(stream))
+    _check(st, "minnorm_plan_create")
+    return h
+
+
+def minnorm_plan_set_params(plan, zeta_t, pi_t, theta_t, zeta, pi, theta, d, s):
+    """Host numpy arrays: complex128 phases, int64 permutations/sample, float64 angles."""
+    import numpy as np
+    arrs = [np.ascontiguousarray(zeta_t, np.complex128), np.ascontiguousarray(pi_t, np.int64),
+            np.ascontiguousarray(theta_t, np.float64), np.ascontiguousarray(zeta, np.complex128),
+            np.ascontiguousarray(pi, np.int64), np.ascontiguousarray(theta, np.float64),
+            np.ascontiguousarray(d, np.complex128), np.ascontiguousarray(s, np.int64)]
+    st = lib().minnorm_plan_set_params(plan, *[a.ctypes.data for a in arrs])
+    return _check(st, "minnorm_plan_set_params")
+
+
+def minnorm_sketch(plan, A, lda=None, allow=(OK,)):
+    lda = A.shape[-1] if lda is None else lda
+    return _check(lib().minnorm_sketch(plan, _ptr(A), int(lda)), "minnorm_sketch", allow)
+
+
+def minnorm_solve(plan, A, b, eps, x, lda=None, info=True, allow=(OK,)):
+    lda = A.shape[-1] if lda is None else lda
+    inf = Info() if info else None
+    st = lib().minnorm_solve(plan, _ptr(A), int(lda), _ptr(b), float(eps), _ptr(x),
+                             C.byref(inf) if inf is not None else None)
+    _check(st, "minnorm_solve", allow)
+    return st, (inf.as_dict() if inf is not None else None)
+
+
+def minnorm_solve_host(plan, A, b, eps, x, lda=None, info=True, allow=(OK,)):
+    lda = A.shape[-1] if lda is None else lda
+    inf = Info() if info else None
+    st = lib().minnorm_solve_host(plan, _ptr(A), int(lda), _ptr(b), float(eps), _ptr(x),
+                                  C.byref(inf) if inf is not None else None)
+    _check(st, "minnorm_solve_host", allow)
+    return st, (inf.as_dict() if inf is not None else None)
+
+
+def minnorm_plan_destroy(plan):
+    return _check(lib().minnorm_plan_destroy(plan), "minnorm_plan_destroy")
+
+
+def minnorm_get_sketch(plan, Y_out):
+    return _check(lib().minnorm_get_sketch(plan, _ptr(Y_out)), "minnorm_get_sketch")
+
+
+def minnorm_get_factor(plan, R_out, piv_out):
+    return _check(lib().minnorm_get_factor(plan, _ptr(R_out), _ptr(piv_out)), "minnorm_get_factor")
+
+
+def minnorm_cg_products(plan, A, w, q=None, t=None, lda=None):
+    lda = A.shape[-1] if lda is None else lda
+    return _check(lib().minnorm_cg_products(plan, _ptr(A), int(lda), _ptr(w), _ptr(q), _ptr(t)),
+                  "minnorm_cg_products")
+
+
+def minnorm_residual_dd(plan, A, y_hi, y_lo, b, r, x_hi, x_lo, lda=None):
+    lda = A.shape[-1] if lda is None else lda
+    return _check(lib().minnorm_residual_dd(plan, _ptr(A), int(lda), _ptr(y_hi), _ptr(y_lo), _ptr(b),
+                                            _ptr(r), _ptr(x_hi), _ptr(x_lo)), "minnorm_residual_dd")
+
+
+def minnorm_kernel_stats(plan, k):
+    n = C.c_int32()
+    ms = C.c_double()
+    _check(lib().minnorm_kernel_stats(plan, int(k), C.byref(n), C.byref(ms)), "minnorm_kernel_stats")
+    return n.value, ms.value
