@@ -197,10 +197,15 @@ minnorm_status minnorm_residual_dd(minnorm_plan_t plan, const void *A, int64_t l
                                    const void *y_hi, const void *y_lo, const void *b,
                                    void *r, void *x_hi, void *x_lo);
 
-/* Kernel timing of the last minnorm_solve when the plan has MINNORM_FLAG_TIMING:
- * for kernel class k (0: CG product A^* w, 1: CG product A q, 2: double-double
- * pass, 3: QR, 4: sketch) the number of launches timed and their summed
- * milliseconds (CUDA events on the plan's stream). Errors: EINVAL. */
+/* Number of kernels this library has launched in the calling process so far
+ * (host-side count of every launch it enqueues, on any plan). */
+int64_t minnorm_launch_count(void);
+
+/* Kernel timing since the last minnorm_sketch when the plan has
+ * MINNORM_FLAG_TIMING: for kernel class k (0: CG product A^* w, 1: CG product
+ * A q, 2: a double-double residual (both passes), 3: QR and P R^{-1},
+ * 4: sketch (both chains and the FFT)) the number of timed regions and their
+ * summed milliseconds (CUDA events on the plan's stream). Errors: EINVAL. */
 minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *launches, double *ms);
 
 #ifdef __cplusplus

@@ -345,10 +345,12 @@ static cudaError_t adj_t(const GemvPlan &g, const void *A, const void *v, void *
   cudaError_t e = cudaFuncSetAttribute(adj_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((g.cols + kAdjCols - 1) / kAdjCols), g.adj_split);
+  note_launch();
   adj_kernel<T, R><<<grid, kAdjThreads, smem, st>>>((const T *)A, g.rows, g.cols, g.ld, (const cx<R> *)v,
                                                      (cx<R> *)partial, g.adj_split, skip);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  note_launch();
   adj_reduce_kernel<R, OutT><<<reduce_blocks(g.cols), 256, 0, st>>>((const cx<R> *)partial, g.adj_split,
                                                                      g.cols, (OutT *)out, qq, skip);
   return cudaGetLastError();
@@ -358,10 +360,12 @@ template <typename T, typename R>
 static cudaError_t fwd_t(const GemvPlan &g, const void *A, const void *v, void *out, void *partial,
                          const int *skip, cudaStream_t st) {
   dim3 grid(g.fwd_nchunk, (unsigned)((g.rows + 15) / 16));
+  note_launch();
   fwd_kernel<T, R, 16><<<grid, kFwdThreads, 0, st>>>((const T *)A, g.rows, g.cols, g.ld, (const cx<R> *)v,
                                                       g.fwd_chunk, (cx<R> *)partial, skip);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  note_launch();
   fwd_reduce_kernel<R><<<reduce_blocks(g.rows), 256, 0, st>>>((const cx<R> *)partial, g.fwd_nchunk, g.rows,
                                                               (zd *)out, skip);
   return cudaGetLastError();
@@ -394,6 +398,7 @@ cudaError_t launch_gemv_fwd_f32(const GemvPlan &g, const void *A, const void *v3
 cudaError_t launch_adj_dd(const GemvPlan &g, const void *A, const void *yh, const void *yl, void *xh,
                           void *xl, cudaStream_t st) {
   const unsigned blocks = (unsigned)((g.cols + kDdThreads - 1) / kDdThreads);
+  note_launch();
   if (g.mode == 0)
     adj_dd_kernel<zd><<<blocks, kDdThreads, 0, st>>>((const zd *)A, g.rows, g.cols, g.ld, (const zd *)yh,
                                                      (const zd *)yl, (zd *)xh, (zd *)xl);
@@ -408,6 +413,7 @@ cudaError_t launch_fwd_dd(const GemvPlan &g, const void *A, const void *xh, cons
   zd *ph = (zd *)partial;
   zd *pl = ph + fwd_dd_partial_elems(g);
   dim3 grid(g.fwd_nchunk, (unsigned)((g.rows + kDdRows - 1) / kDdRows));
+  note_launch();
   if (g.mode == 0)
     fwd_dd_kernel<zd><<<grid, kFwdThreads, 0, st>>>((const zd *)A, g.rows, g.cols, g.ld, (const zd *)xh,
                                                     (const zd *)xl, g.fwd_chunk, ph, pl);
@@ -416,12 +422,14 @@ cudaError_t launch_fwd_dd(const GemvPlan &g, const void *A, const void *xh, cons
                                                     (const zd *)xl, g.fwd_chunk, ph, pl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  note_launch();
   fwd_dd_reduce_kernel<<<reduce_blocks(g.rows), 256, 0, st>>>(ph, pl, g.fwd_nchunk, g.rows, (zd *)vh, (zd *)vl);
   return cudaGetLastError();
 }
 
 cudaError_t launch_small_gemv(const void *M, int m, const void *v, void *out, void *out32, const int *skip,
                               cudaStream_t st) {
+  note_launch();
   small_gemv_kernel<<<(m + 7) / 8, 256, 0, st>>>((const zd *)M, m, (const zd *)v, (zd *)out, (zf *)out32, skip);
   return cudaGetLastError();
 }

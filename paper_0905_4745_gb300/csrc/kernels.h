@@ -9,6 +9,10 @@ namespace mn {
 
 struct GridBarrier;
 
+// count of kernels launched by this library (every launch site calls it)
+void note_launch();
+long long launches_so_far();
+
 // ---- sketch.cu ------------------------------------------------------------
 struct ChainArgs {
   const void *src;       // rows x n, complex128 (src_c64 = 0) or complex64

@@ -220,6 +220,7 @@ static cudaError_t launch_qrp_t(const QrArgs &a, int G, cudaStream_t st) {
   uint64_t lim = a.limit_ns;
   void *args[] = {&Y, &l, &m, (void *)&a.vn1, &vnB, (void *)&a.vn2, (void *)&a.beta, (void *)&a.piv,
                   &R, (void *)&a.bar, (void *)&a.err, &lim};
+  note_launch();
   return cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(kQrThreads), args, 0, st);
 }
 
@@ -229,6 +230,7 @@ cudaError_t launch_qrp(const QrArgs &a, cudaStream_t st) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int G = a.m < sms ? a.m : sms;
   const int per = (a.m + G - 1) / G;
+  note_launch();
   qr_norms_kernel<<<a.m, kQrThreads, 0, st>>>((const zd *)a.Y, a.l, a.vn1, a.vn2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -283,6 +285,7 @@ cudaError_t launch_prinv(const void *R, const int32_t *piv, int m, void *Wp, voi
   const size_t smem = sizeof(zd) * 2 * (size_t)m;
   e = cudaFuncSetAttribute(prinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  note_launch();
   prinv_kernel<<<m, 128, smem, st>>>((const zd *)R, piv, m, (zd *)Wp, (zd *)WpH);
   return cudaGetLastError();
 }

@@ -276,6 +276,7 @@ static cudaError_t launch_chain_t(const ChainArgs &a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int nseg = (a.n + a.seg - 1) / a.seg;
   dim3 grid(nseg, a.rows);
+  note_launch();
   chain_kernel<R, S, CONJ, POST><<<grid, kChainThreads, smem, st>>>(
       (const S *)a.src, a.ld_src, (cx<R> *)a.dst, a.ld_dst, a.idx, (const cx<R> *)a.phase,
       (const cx<R> *)a.cs, (const cx<R> *)a.post, a.halo, a.n, a.seg, a.cap);
@@ -308,6 +309,7 @@ static cudaError_t launch_fft_t(const FftArgs &a, cudaStream_t st) {
     const size_t smem = sizeof(cx<R>) << a.logn;
     e = cudaFuncSetAttribute(fft_row_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    note_launch();
     fft_row_kernel<R><<<dim3(1, a.rows), 256, smem, st>>>(
         (const cx<R> *)a.src, a.ld, a.logn, (const cx<R> *)a.tw, a.samp_t, a.samp_loc, a.l, (zd *)a.Y,
         a.ldy, a.row_offset, scale);
@@ -320,10 +322,12 @@ static cudaError_t launch_fft_t(const FftArgs &a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(fft_pass_b_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemB);
   if (e != cudaSuccess) return e;
+  note_launch();
   fft_pass_a_kernel<R><<<dim3(N1 / a.tj, a.rows), 256, smemA, st>>>(
       (const cx<R> *)a.src, a.ld, (cx<R> *)a.work, a.logn, a.logN1, a.tj, (const cx<R> *)a.tw);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  note_launch();
   fft_pass_b_kernel<R><<<dim3(N2 / a.tk, a.rows), 256, smemB, st>>>(
       (const cx<R> *)a.work, a.ld, a.logn, a.logN1, a.tk, (const cx<R> *)a.tw, a.samp_off, a.samp_t,
       a.samp_loc, (zd *)a.Y, a.ldy, a.row_offset, scale);
@@ -338,6 +342,7 @@ cudaError_t launch_to_c64(const void *A, int64_t lda, void *B, int64_t ldb, int6
                           cudaStream_t st) {
   int64_t bx = (cols + 255) / 256;
   if (bx > 64) bx = 64;
+  note_launch();
   to_c64_kernel<<<dim3((unsigned)bx, (unsigned)rows), 256, 0, st>>>((const zd *)A, lda, (zf *)B, ldb, cols);
   return cudaGetLastError();
 }
@@ -349,6 +354,7 @@ cudaError_t launch_narrow(int64_t len, const void *src, void *dst, cudaStream_t 
 cudaError_t launch_widen(int64_t len, const void *src, void *dst, cudaStream_t st) {
   int64_t b = (len + 255) / 256;
   if (b > 1024) b = 1024;
+  note_launch();
   widen_kernel<<<(unsigned)b, 256, 0, st>>>(len, (const zf *)src, (zd *)dst);
   return cudaGetLastError();
 }

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -34,6 +35,12 @@
 #include "vec.h"
 
 using namespace mn;
+
+namespace mn {
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace mn
 
 namespace {
 
@@ -727,6 +734,7 @@ minnorm_status minnorm_get_factor(minnorm_plan_t plan, void *R_out, void *piv_ou
   if (!plan || !R_out || !piv_out) return MINNORM_EINVAL;
   if (!plan->sketched) return MINNORM_ESTATE;
   CK(cudaMemcpyAsync(R_out, plan->d_R, sizeof(zd) * plan->m * plan->m, cudaMemcpyDeviceToDevice, plan->st));
+  note_launch();
   piv_widen_kernel<<<(int)((plan->m + 255) / 256), 256, 0, plan->st>>>(plan->d_piv, (int64_t *)piv_out, (int)plan->m);
   CK(cudaGetLastError());
   return MINNORM_OK;
@@ -766,6 +774,8 @@ minnorm_status minnorm_residual_dd(minnorm_plan_t plan, const void *A, int64_t l
   CK(launch_resid_finish(plan->m, b, plan->d_vh, plan->d_vl, r, st));
   return MINNORM_OK;
 }
+
+int64_t minnorm_launch_count(void) { return (int64_t)launches_so_far(); }
 
 minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *launches, double *ms) {
   if (!plan || k < 0 || k > 4 || !launches || !ms) return MINNORM_EINVAL;

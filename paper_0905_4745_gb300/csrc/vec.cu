@@ -3,6 +3,7 @@
 // the CG loop takes `done`: once the loop's stopping test has fired, the
 // remaining (already enqueued) iterations return immediately.
 #include "common.cuh"
+#include "kernels.h"
 #include "vec.h"
 
 namespace mn {
@@ -137,38 +138,45 @@ static int blocks_for(int64_t len) {
 }
 
 cudaError_t launch_cg_init(int m, const void *g, void *u, void *s, void *p, CgScalars *sc, cudaStream_t st) {
+  note_launch();
   cg_init_kernel<<<1, 1024, 0, st>>>(m, (const zd *)g, (zd *)u, (zd *)s, (zd *)p, sc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_update(int m, const double *qq, int nqq, const void *np, void *u, void *s, void *p,
                              CgScalars *sc, double tol2, cudaStream_t st) {
+  note_launch();
   cg_update_kernel<<<1, 1024, 0, st>>>(m, qq, nqq, (const zd *)np, (zd *)u, (zd *)s, (zd *)p, sc, tol2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dd_accumulate(int64_t len, void *yh, void *yl, const void *d, cudaStream_t st) {
+  note_launch();
   dd_accumulate_kernel<<<blocks_for(len), 256, 0, st>>>(len, (zd *)yh, (zd *)yl, (const zd *)d);
   return cudaGetLastError();
 }
 
 cudaError_t launch_resid_finish(int64_t len, const void *b, const void *vh, const void *vl, void *r,
                                 cudaStream_t st) {
+  note_launch();
   resid_finish_kernel<<<blocks_for(len), 256, 0, st>>>(len, (const zd *)b, (const zd *)vh, (const zd *)vl,
                                                        (zd *)r);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sub(int64_t len, void *r, const void *t, cudaStream_t st) {
+  note_launch();
   sub_kernel<<<blocks_for(len), 256, 0, st>>>(len, (zd *)r, (const zd *)t);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sumsq(int64_t len, const void *v, double *part, double *out, cudaStream_t st) {
   const int nb = blocks_for(len);
+  note_launch();
   sumsq_kernel<<<nb, 256, 0, st>>>(len, (const zd *)v, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  note_launch();
   finish_sum_kernel<<<1, 256, 0, st>>>(part, nb, out);
   return cudaGetLastError();
 }

@@ -22,7 +22,8 @@ FLAG_TIMING, FLAG_KEEP_SKETCH = 1, 2
 # every symbol include/minnorm.h declares
 EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_sketch", "minnorm_solve",
            "minnorm_solve_host", "minnorm_plan_destroy", "minnorm_status_string", "minnorm_get_sketch",
-           "minnorm_get_factor", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats"]
+           "minnorm_get_factor", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats",
+           "minnorm_launch_count"]
 
 
 class MinnormError(RuntimeError):
@@ -65,8 +66,10 @@ def lib():
         L.minnorm_cg_products.argtypes = [p, p, i64, p, p, p]
         L.minnorm_residual_dd.argtypes = [p, p, i64, p, p, p, p, p, p]
         L.minnorm_kernel_stats.argtypes = [p, i32, C.POINTER(i32), C.POINTER(d)]
+        L.minnorm_launch_count.argtypes = []
+        L.minnorm_launch_count.restype = C.c_int64
         for name in EXPORTS:
-            if name != "minnorm_status_string":
+            if name not in ("minnorm_status_string", "minnorm_launch_count"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -174,3 +177,7 @@ def minnorm_kernel_stats(plan, k):
     ms = C.c_double()
     _check(lib().minnorm_kernel_stats(plan, int(k), C.byref(n), C.byref(ms)), "minnorm_kernel_stats")
     return n.value, ms.value
+
+
+def minnorm_launch_count():
+    return int(lib().minnorm_launch_count())

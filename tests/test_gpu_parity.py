@@ -341,7 +341,7 @@ def test_full_size_plain_workload(mn, prec):
         x = torch.empty(n, dtype=torch.complex128, device=_dev())
         st, info = mn.minnorm_solve(plan, A, b, eps, x)
         torch.cuda.synchronize()
-        Y, x = Y.cpu().numpy(), x.cpu().numpy()
+        Y, x = Y.cpu().numpy().T, x.cpu().numpy()
     finally:
         mn.minnorm_plan_destroy(plan)
     P = oracle.draw_params(n, l, 1)
