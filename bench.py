@@ -207,7 +207,8 @@ def main():
     import synth
 
     m, n, eps = W["m"], W["n"], W["eps"]
-    s = synth.make_system(m, n, W["exponent"], W["seed"] + 100 * rank, device=str(device))
+    cache = os.environ.get("MINNORM_INPUT_CACHE", os.path.join(tempfile.gettempdir(), "minnorm_inputs"))
+    s = synth.make_system(m, n, W["exponent"], W["seed"] + 100 * rank, device=str(device), cache_dir=cache)
     A, b = s.A, s.b
     stream = torch.cuda.current_stream()
     prec_main = mn.MIXED if args.precision == "mixed" else mn.FP64

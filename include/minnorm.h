@@ -80,8 +80,8 @@ typedef enum {
 typedef struct {
   int32_t outer_steps;       /* refinement steps taken */
   int32_t cg_iters;          /* CG iterations summed over all steps */
-  int32_t dd_passes;         /* passes over A with double-double sums */
-  int32_t fp64_passes;       /* incremental FP64 residual passes */
+  int32_t exact_passes;      /* passes over A in exact fixed-point arithmetic (x = A^* y, b - A x) */
+  int32_t reserved0;
   double err_bound;          /* a-posteriori bound on ||x - p|| / ||x|| (uses sigma_min(A^* P R^{-1}) >= 1) */
   double resid_rel;          /* ||b - A x|| / ||b|| from the last residual */
   double rdiag_max;          /* |R_11| */
@@ -189,10 +189,14 @@ minnorm_status minnorm_get_factor(minnorm_plan_t plan, void *R_out, void *piv_ou
 minnorm_status minnorm_cg_products(minnorm_plan_t plan, const void *A, int64_t lda,
                                    const void *w, void *q, void *t);
 
-/* The double-double residual of the refinement: for y = y_hi + y_lo (device,
- * m complex128 each; y_lo may be NULL) computes x = A^* y with double-double
- * sums into x_hi, x_lo (device, n complex128 each) and r = b - A x (device,
- * m complex128, rounded to FP64). Errors: ESTATE, EINVAL. */
+/* The accurate residual of the refinement: for y = y_hi + y_lo (device, m
+ * complex128 each; y_lo may be NULL) computes x = A^* y into x_hi + x_lo
+ * (device, n complex128 each, a double-double pair) and r = b - A x (device,
+ * m complex128, rounded to FP64). Both products are accumulated exactly in
+ * 128-bit fixed point: A with one exponent per row (exact for complex64
+ * storage; complex128 components more than 2^9 below their row's largest are
+ * rounded at 2^-62 of it), y and x with one exponent per vector and 109+
+ * bits. Re-derives the plan's fixed-point copy of A from A. Errors: EINVAL. */
 minnorm_status minnorm_residual_dd(minnorm_plan_t plan, const void *A, int64_t lda,
                                    const void *y_hi, const void *y_lo, const void *b,
                                    void *r, void *x_hi, void *x_lo);

@@ -11,9 +11,7 @@
 //            column chunk; each thread keeps one accumulator per row, so the
 //            chunk of v is read once per CTA; chunk partials are added by a
 //            second kernel in FP64.
-//   *_dd     the same two products with every real product split exactly
-//            (TwoProd) and summed in double-double (TwoSum), for the
-//            refinement residual b - A A^* y and the final x = A^* y.
+//   (the refinement's accurate products are in xprod.cu)
 //
 // Modes: 0 = complex128 A, FP64 arithmetic; 1 = complex64 A, FP32 arithmetic
 // (mixed precision); 2 = complex64 A, FP64 arithmetic.
@@ -157,133 +155,6 @@ fwd_reduce_kernel(const cx<R> *__restrict__ partial, int nchunk, int64_t rows, z
   }
 }
 
-// ---- double-double ------------------------------------------------------
-constexpr int kDdThreads = 128;
-
-template <typename T>
-__global__ void __launch_bounds__(kDdThreads)
-adj_dd_kernel(const T *__restrict__ A, int64_t rows, int64_t cols, int64_t ld, const zd *__restrict__ yh,
-              const zd *__restrict__ yl, zd *__restrict__ xh, zd *__restrict__ xl) {
-  __shared__ zd sh[kDdThreads], sl[kDdThreads];
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  dd_acc re = {0.0, 0.0}, im = {0.0, 0.0};
-  for (int64_t i0 = 0; i0 < rows; i0 += kDdThreads) {
-    __syncthreads();
-    if (i0 + threadIdx.x < rows) {
-      sh[threadIdx.x] = yh[i0 + threadIdx.x];
-      sl[threadIdx.x] = yl ? yl[i0 + threadIdx.x] : zd{0.0, 0.0};
-    }
-    __syncthreads();
-    if (j < cols) {
-      const int64_t ie = (i0 + kDdThreads < rows ? i0 + kDdThreads : rows) - i0;
-      const T *a = A + i0 * ld + j;
-      for (int64_t u = 0; u < ie; ++u) {
-        const T av = a[u * ld];
-        const double ar = (double)av.re, ai = (double)av.im;
-        const zd y = sh[u], z = sl[u];
-        // conj(a) * y = (ar yr + ai yi) + i (ar yi - ai yr)
-        dd_prod(re, ar, y.re);
-        dd_prod(re, ai, y.im);
-        dd_prod(im, ar, y.im);
-        dd_prod(im, -ai, y.re);
-        dd_small(re, fma(ar, z.re, ai * z.im));
-        dd_small(im, fma(ar, z.im, -ai * z.re));
-      }
-    }
-  }
-  if (j < cols) {
-    double h, l;
-    dd_round(re, h, l);
-    double h2, l2;
-    dd_round(im, h2, l2);
-    xh[j] = {h, h2};
-    xl[j] = {l, l2};
-  }
-}
-
-__device__ __forceinline__ void dd_warp_sum(dd_acc &a) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    dd_acc b;
-    b.s = __shfl_xor_sync(0xffffffffu, a.s, o);
-    b.c = __shfl_xor_sync(0xffffffffu, a.c, o);
-    dd_add(a, b);
-  }
-}
-
-constexpr int kDdRows = 4;
-
-// partial[chunk][row] = sum over the chunk of A[row, j] (xh[j] + xl[j]), in dd (hi, lo as complex pairs)
-template <typename T>
-__global__ void __launch_bounds__(kFwdThreads)
-fwd_dd_kernel(const T *__restrict__ A, int64_t rows, int64_t cols, int64_t ld, const zd *__restrict__ xh,
-              const zd *__restrict__ xl, int64_t chunk, zd *__restrict__ ph, zd *__restrict__ pl) {
-  __shared__ dd_acc sred[(kFwdThreads / 32) * 2 * kDdRows];
-  const int64_t i0 = (int64_t)blockIdx.y * kDdRows;
-  const int64_t c0 = (int64_t)blockIdx.x * chunk;
-  const int64_t c1 = c0 + chunk < cols ? c0 + chunk : cols;
-  dd_acc acc[2 * kDdRows];
-#pragma unroll
-  for (int r = 0; r < 2 * kDdRows; ++r) acc[r] = {0.0, 0.0};
-  for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-    const zd x = xh[c], z = xl[c];
-#pragma unroll
-    for (int r = 0; r < kDdRows; ++r) {
-      if (i0 + r < rows) {
-        const T av = A[(i0 + r) * ld + c];
-        const double ar = (double)av.re, ai = (double)av.im;
-        // a * x = (ar xr - ai xi) + i (ar xi + ai xr)
-        dd_prod(acc[2 * r], ar, x.re);
-        dd_prod(acc[2 * r], -ai, x.im);
-        dd_prod(acc[2 * r + 1], ar, x.im);
-        dd_prod(acc[2 * r + 1], ai, x.re);
-        dd_small(acc[2 * r], fma(ar, z.re, -ai * z.im));
-        dd_small(acc[2 * r + 1], fma(ar, z.im, ai * z.re));
-      }
-    }
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int r = 0; r < 2 * kDdRows; ++r) dd_warp_sum(acc[r]);
-  if (lane == 0) {
-#pragma unroll
-    for (int r = 0; r < 2 * kDdRows; ++r) sred[wid * 2 * kDdRows + r] = acc[r];
-  }
-  __syncthreads();
-  if (threadIdx.x < kDdRows && i0 + threadIdx.x < rows) {
-    const int r = threadIdx.x;
-    dd_acc sr = sred[2 * r], si = sred[2 * r + 1];
-    for (int w = 1; w < nw; ++w) {
-      dd_add(sr, sred[w * 2 * kDdRows + 2 * r]);
-      dd_add(si, sred[w * 2 * kDdRows + 2 * r + 1]);
-    }
-    const int64_t o = (int64_t)blockIdx.x * rows + i0 + r;
-    double h1, l1, h2, l2;
-    dd_round(sr, h1, l1);
-    dd_round(si, h2, l2);
-    ph[o] = {h1, h2};
-    pl[o] = {l1, l2};
-  }
-}
-
-// v = sum over chunks (dd) -> (vh, vl)
-__global__ void fwd_dd_reduce_kernel(const zd *__restrict__ ph, const zd *__restrict__ pl, int nchunk,
-                                     int64_t rows, zd *__restrict__ vh, zd *__restrict__ vl) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
-    dd_acc sr = {0.0, 0.0}, si = {0.0, 0.0};
-    for (int c = 0; c < nchunk; ++c) {
-      const zd h = ph[(int64_t)c * rows + i], l = pl[(int64_t)c * rows + i];
-      dd_add(sr, dd_acc{h.re, l.re});
-      dd_add(si, dd_acc{h.im, l.im});
-    }
-    double h1, l1, h2, l2;
-    dd_round(sr, h1, l1);
-    dd_round(si, h2, l2);
-    vh[i] = {h1, h2};
-    if (vl) vl[i] = {l1, l2};
-  }
-}
-
 // ---- small dense m x m products (the preconditioner P R^{-1}) ------------
 __global__ void __launch_bounds__(256)
 small_gemv_kernel(const zd *__restrict__ M, int m, const zd *__restrict__ v, zd *__restrict__ out,
@@ -327,10 +198,6 @@ void gemv_configure(GemvPlan &g, int64_t rows, int64_t cols, int64_t ld, int mod
 
 size_t gemv_adj_partial_elems(const GemvPlan &g) { return (size_t)g.adj_split * g.cols; }
 size_t gemv_fwd_partial_elems(const GemvPlan &g) { return (size_t)g.fwd_nchunk * g.rows; }
-size_t fwd_dd_partial_elems(const GemvPlan &g) {
-  const int64_t nchunk = g.fwd_nchunk;
-  return (size_t)nchunk * g.rows;
-}
 
 static int reduce_blocks(int64_t n) {
   int64_t b = (n + 255) / 256;
@@ -393,38 +260,6 @@ cudaError_t launch_gemv_adj_f32(const GemvPlan &g, const void *A, const void *v3
 cudaError_t launch_gemv_fwd_f32(const GemvPlan &g, const void *A, const void *v32, void *out64,
                                 void *partial, const int *skip, cudaStream_t st) {
   return fwd_t<zf, float>(g, A, v32, out64, partial, skip, st);
-}
-
-cudaError_t launch_adj_dd(const GemvPlan &g, const void *A, const void *yh, const void *yl, void *xh,
-                          void *xl, cudaStream_t st) {
-  const unsigned blocks = (unsigned)((g.cols + kDdThreads - 1) / kDdThreads);
-  note_launch();
-  if (g.mode == 0)
-    adj_dd_kernel<zd><<<blocks, kDdThreads, 0, st>>>((const zd *)A, g.rows, g.cols, g.ld, (const zd *)yh,
-                                                     (const zd *)yl, (zd *)xh, (zd *)xl);
-  else
-    adj_dd_kernel<zf><<<blocks, kDdThreads, 0, st>>>((const zf *)A, g.rows, g.cols, g.ld, (const zd *)yh,
-                                                     (const zd *)yl, (zd *)xh, (zd *)xl);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fwd_dd(const GemvPlan &g, const void *A, const void *xh, const void *xl, void *vh,
-                          void *vl, void *partial, cudaStream_t st) {
-  zd *ph = (zd *)partial;
-  zd *pl = ph + fwd_dd_partial_elems(g);
-  dim3 grid(g.fwd_nchunk, (unsigned)((g.rows + kDdRows - 1) / kDdRows));
-  note_launch();
-  if (g.mode == 0)
-    fwd_dd_kernel<zd><<<grid, kFwdThreads, 0, st>>>((const zd *)A, g.rows, g.cols, g.ld, (const zd *)xh,
-                                                    (const zd *)xl, g.fwd_chunk, ph, pl);
-  else
-    fwd_dd_kernel<zf><<<grid, kFwdThreads, 0, st>>>((const zf *)A, g.rows, g.cols, g.ld, (const zd *)xh,
-                                                    (const zd *)xl, g.fwd_chunk, ph, pl);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  note_launch();
-  fwd_dd_reduce_kernel<<<reduce_blocks(g.rows), 256, 0, st>>>(ph, pl, g.fwd_nchunk, g.rows, (zd *)vh, (zd *)vl);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_small_gemv(const void *M, int m, const void *v, void *out, void *out32, const int *skip,

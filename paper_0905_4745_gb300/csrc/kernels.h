@@ -61,7 +61,14 @@ struct QrArgs {
   GridBarrier *bar;
   int *err;
   uint64_t limit_ns;
+  // candidate slots of the shared-memory variant (nullptr: use the L2 variant)
+  double *cand_val;       // 2 x G
+  int32_t *cand_col;      // 2 x G
+  void *cand_data;        // 2 x G x l complex128
 };
+// shared memory the shared-memory variant needs; it is used when this is at most kQrSmemLimit
+constexpr size_t kQrSmemLimit = 200 * 1024;
+size_t qrp_smem_bytes(int l, int m, int sms);
 cudaError_t launch_qrp(const QrArgs &a, cudaStream_t st);
 
 // Wp = P R^{-1} (row-major m x m) and WpH = Wp^* (row-major)
@@ -94,12 +101,28 @@ cudaError_t launch_gemv_adj_f32(const GemvPlan &g, const void *A, const void *v3
 cudaError_t launch_gemv_fwd_f32(const GemvPlan &g, const void *A, const void *v32, void *out64,
                                 void *partial, const int *skip, cudaStream_t st);
 
-// double-double: x = A^* (y_hi + y_lo) -> (x_hi, x_lo); v = A (x_hi + x_lo) -> (v_hi, v_lo)
-cudaError_t launch_adj_dd(const GemvPlan &g, const void *A, const void *yh, const void *yl, void *xh,
-                          void *xl, cudaStream_t st);
-cudaError_t launch_fwd_dd(const GemvPlan &g, const void *A, const void *xh, const void *xl, void *vh,
-                          void *vl, void *partial, cudaStream_t st);
-size_t fwd_dd_partial_elems(const GemvPlan &g);
+
+// ---- xprod.cu --------------------------------------------------------------
+// exact fixed-point products of the refinement (see xprod.cu)
+struct XprodArgs {
+  const void *afix;       // rows x cols fixed-point A (2 int64 per element)
+  const int32_t *E;       // rows: per-row exponents
+  int64_t rows, cols;
+  const void *yh, *yl;    // rows complex128: y = yh + yl (yl may be nullptr)
+  void *yfix;             // rows x 32 bytes scratch
+  int *Fy, *Fx;           // device scalars
+  void *xh, *xl;          // cols complex128 out: x = A^* y as double-double
+  const void *b;          // rows complex128, or nullptr to stop after x
+  void *r;                // rows complex128 out: b - A x (may be nullptr)
+  void *th, *tl;          // rows complex128 out: A x as double-double (may be nullptr)
+  void *partial;          // xprod_partial_bytes(rows, nchunk)
+  int nchunk;
+  int64_t chunk;
+};
+cudaError_t launch_fix_prep(const void *A, int64_t lda, bool c64, int64_t rows, int64_t cols, void *afix,
+                            int32_t *E, void *A32, cudaStream_t st);
+cudaError_t launch_xresidual(const XprodArgs &a, cudaStream_t st);
+size_t xprod_partial_bytes(int64_t rows, int nchunk);
 
 // small dense m x m FP64 products: out = M v (M row-major), optionally also an FP32 copy
 cudaError_t launch_small_gemv(const void *M, int m, const void *v, void *out, void *out32, const int *skip,

@@ -210,6 +210,244 @@ qrp_kernel(zd *__restrict__ Y, int l, int m, double *__restrict__ vnA, double *_
   }
 }
 
+// ---- shared-memory variant ---------------------------------------------------
+// Same algorithm, for sizes where every CTA's own columns fit in shared
+// memory (ceil(m/G) + 1 columns of l entries). The columns never leave the
+// SM until R is written. Each CTA publishes, at the end of a step, its own
+// best remaining column (partial norm, index and rows k+1..l-1) in a
+// double-buffered candidate slot; after the grid barrier every CTA takes the
+// global maximum over the G candidates (first index on ties) and reads the
+// winning rows from L2, so one barrier per step suffices.
+constexpr int kQr2Threads = 512;
+
+template <int MAXC>
+__global__ void __launch_bounds__(kQr2Threads)
+qrp_smem_kernel(const zd *__restrict__ Y, int l, int m, double *__restrict__ cand_val,
+                int32_t *__restrict__ cand_col, zd *__restrict__ cand_data, double *__restrict__ beta,
+                int32_t *__restrict__ piv, zd *__restrict__ Rout, GridBarrier *bar, int *err,
+                uint64_t limit_ns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int K = 1 + 2 * MAXC;
+  constexpr int NW = kQr2Threads / 32;
+  __shared__ double red_scratch[NW * K];
+  __shared__ double red_out[K];
+  __shared__ double s_vn1[MAXC], s_vn2[MAXC], s_beta[MAXC];
+  __shared__ int s_step[MAXC];
+  __shared__ zd s_g[MAXC];
+  __shared__ int s_rec[MAXC];
+  __shared__ int s_nrec, s_w, s_p, s_cand;
+
+  const int G = gridDim.x, b = blockIdx.x;
+  const int nc = (m - b + G - 1) / G;  // own columns j = b + c G, c < nc
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  zd *cols = reinterpret_cast<zd *>(smem_raw);
+  zd *pbuf = cols + (size_t)nc * l;
+  const double tol3z = sqrt(0x1.0p-53);
+
+  for (int c = 0; c < nc; ++c) {
+    const zd *src = Y + (int64_t)(b + c * G) * l;
+    for (int r = tid; r < l; r += blockDim.x) cols[(size_t)c * l + r] = src[r];
+  }
+  if (tid < MAXC) s_step[tid] = -1;
+  __syncthreads();
+  {
+    double part[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) part[c] = 0.0;
+    for (int r = tid; r < l; r += blockDim.x) {
+#pragma unroll
+      for (int c = 0; c < MAXC; ++c)
+        if (c < nc) part[c] += abs2(cols[(size_t)c * l + r]);
+    }
+    block_sum_k<double, K>(part, red_scratch, red_out);
+    if (tid < nc) { s_vn1[tid] = sqrt(red_out[tid]); s_vn2[tid] = s_vn1[tid]; }
+    __syncthreads();
+  }
+
+  // publish this CTA's best remaining column (rows row0..l-1) into `slot`
+  auto publish = [&](int slot, int row0) {
+    if (tid == 0) {
+      int best = -1;
+      double bv = -1.0;
+      for (int c = 0; c < nc; ++c)
+        if (s_step[c] < 0 && s_vn1[c] > bv) { bv = s_vn1[c]; best = c; }
+      s_cand = best;
+      cand_val[slot * G + b] = best >= 0 ? bv : -1.0;
+      cand_col[slot * G + b] = best >= 0 ? b + best * G : 0x7fffffff;
+    }
+    __syncthreads();
+    const int c = s_cand;
+    if (c >= 0) {
+      zd *dst = cand_data + (size_t)(slot * G + b) * l;
+      for (int r = row0 + tid; r < l; r += blockDim.x) dst[r] = cols[(size_t)c * l + r];
+    }
+  };
+
+  publish(0, 0);
+  if (!grid_sync(bar, G, limit_ns)) { if (tid == 0) atomicExch(err, 1); return; }
+
+  for (int k = 0; k < m; ++k) {
+    const int slot = k & 1;
+    // 1. global pivot among the published candidates
+    if (wid == 0) {
+      double bv = -2.0;
+      int bc = 0x7fffffff, bw = -1;
+      for (int gi = lane; gi < G; gi += 32) {
+        const double v = cand_val[slot * G + gi];
+        const int cc = cand_col[slot * G + gi];
+        if (v > bv || (v == bv && cc < bc)) { bv = v; bc = cc; bw = gi; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+        const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
+        if (ov > bv || (ov == bv && oc < bc)) { bv = ov; bc = oc; bw = ow; }
+      }
+      if (lane == 0) { s_w = bw; s_p = bc; }
+    }
+    __syncthreads();
+    const int w = s_w, p = s_p;
+    {
+      const zd *src = cand_data + (size_t)(slot * G + w) * l;
+      for (int r = k + tid; r < l; r += blockDim.x) pbuf[r] = src[r];
+    }
+    if (b == w && tid == 0) {
+      const int c = (p - b) / G;
+      s_step[c] = k;
+      piv[k] = p;
+    }
+    __syncthreads();
+
+    // 2. ||pbuf[k+1:]||^2 and conj(pbuf[k+1:])^T col_c[k+1:] in one reduction
+    double part[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) part[c] = 0.0;
+    for (int r = k + 1 + tid; r < l; r += blockDim.x) {
+      const zd a = pbuf[r];
+      part[0] = fma(a.re, a.re, fma(a.im, a.im, part[0]));
+#pragma unroll
+      for (int c = 0; c < MAXC; ++c) {
+        if (c < nc && s_step[c] < 0) {
+          const zd y = cols[(size_t)c * l + r];
+          part[1 + 2 * c] = fma(a.re, y.re, fma(a.im, y.im, part[1 + 2 * c]));
+          part[2 + 2 * c] = fma(a.re, y.im, fma(-a.im, y.re, part[2 + 2 * c]));
+        }
+      }
+    }
+    block_sum_k<double, K>(part, red_scratch, red_out);
+
+    // 3. reflector and per-column factors (identical in every CTA)
+    if (tid == 0) {
+      const zd alpha = pbuf[k];
+      const double xn2 = red_out[0];
+      zd tau = {0.0, 0.0}, scale = {0.0, 0.0};
+      double bt;
+      if (xn2 == 0.0 && alpha.im == 0.0) {
+        bt = alpha.re;
+      } else {
+        const double mag = sqrt(alpha.re * alpha.re + alpha.im * alpha.im + xn2);
+        bt = alpha.re >= 0.0 ? -mag : mag;
+        tau = {(bt - alpha.re) / bt, -alpha.im / bt};
+        const double dr = alpha.re - bt, di = alpha.im;
+        const double den = dr * dr + di * di;
+        scale = {dr / den, -di / den};
+      }
+      if (b == w) {
+        beta[k] = bt;
+        s_beta[(p - b) / G] = bt;
+      }
+      int nrec = 0;
+      for (int c = 0; c < nc; ++c) {
+        if (s_step[c] >= 0) continue;
+        const zd d = {red_out[1 + 2 * c], red_out[2 + 2 * c]};
+        zd wv = cols[(size_t)c * l + k];
+        macc(wv, scale, d);
+        const zd f = conjg(tau) * wv;
+        s_g[c] = f * scale;
+        const zd rk = cols[(size_t)c * l + k] - f;
+        cols[(size_t)c * l + k] = rk;
+        const double v1 = s_vn1[c];
+        if (v1 != 0.0) {
+          const double t = sqrt(abs2(rk)) / v1;
+          double temp = 1.0 - t * t;
+          temp = temp < 0.0 ? 0.0 : temp;
+          const double ratio = v1 / s_vn2[c];
+          if (temp * ratio * ratio <= tol3z) s_rec[nrec++] = c;
+          else s_vn1[c] = v1 * sqrt(temp);
+        }
+      }
+      s_nrec = nrec;
+    }
+    __syncthreads();
+
+    // 4. apply H^* to the own trailing columns
+    for (int r = k + 1 + tid; r < l; r += blockDim.x) {
+      const zd a = pbuf[r];
+#pragma unroll
+      for (int c = 0; c < MAXC; ++c) {
+        if (c < nc && s_step[c] < 0) {
+          zd v = cols[(size_t)c * l + r];
+          const zd g = s_g[c];
+          v.re = fma(-g.re, a.re, fma(g.im, a.im, v.re));
+          v.im = fma(-g.re, a.im, fma(-g.im, a.re, v.im));
+          cols[(size_t)c * l + r] = v;
+        }
+      }
+    }
+    __syncthreads();
+    const int nrec = s_nrec;
+    for (int q = 0; q < nrec; ++q) {
+      const int c = s_rec[q];
+      double acc = 0.0;
+      for (int r = k + 1 + tid; r < l; r += blockDim.x) acc += abs2(cols[(size_t)c * l + r]);
+      const double t = sqrt(block_sum(acc, red_scratch));
+      if (tid == 0) {
+        const double v = (k < l - 1) ? t : 0.0;
+        s_vn1[c] = v;
+        s_vn2[c] = v;
+      }
+      __syncthreads();
+    }
+    if (k + 1 < m) publish((k + 1) & 1, k + 1);
+    if (!grid_sync(bar, G, limit_ns)) { if (tid == 0) atomicExch(err, 1); return; }
+  }
+
+  // R in pivot order, from the columns still in shared memory
+  for (int c = 0; c < nc; ++c) {
+    const int kc = s_step[c];
+    const double bt = s_beta[c];
+    for (int i = tid; i < m; i += blockDim.x) {
+      zd v = {0.0, 0.0};
+      if (i < kc) v = cols[(size_t)c * l + i];
+      else if (i == kc) v = {bt, 0.0};
+      Rout[i + (int64_t)kc * m] = v;
+    }
+  }
+}
+
+template <int MAXC>
+static cudaError_t launch_qrp_smem_t(const QrArgs &a, int G, size_t smem, cudaStream_t st) {
+  auto kern = qrp_smem_kernel<MAXC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const zd *Y = (const zd *)a.Y;
+  int l = a.l, m = a.m;
+  zd *R = (zd *)a.R;
+  zd *cd = (zd *)a.cand_data;
+  uint64_t lim = a.limit_ns;
+  void *args[] = {(void *)&Y, &l, &m, (void *)&a.cand_val, (void *)&a.cand_col, &cd, (void *)&a.beta,
+                  (void *)&a.piv, &R, (void *)&a.bar, (void *)&a.err, &lim};
+  note_launch();
+  return cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(kQr2Threads), args, smem, st);
+}
+
+size_t qrp_smem_bytes(int l, int m, int sms) {
+  const int G = m < sms ? m : sms;
+  const int per = (m + G - 1) / G;
+  return sizeof(zd) * (size_t)(per + 1) * l;
+}
+
 template <int MAXC>
 static cudaError_t launch_qrp_t(const QrArgs &a, int G, cudaStream_t st) {
   auto kern = qrp_kernel<MAXC>;
@@ -230,6 +468,12 @@ cudaError_t launch_qrp(const QrArgs &a, cudaStream_t st) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int G = a.m < sms ? a.m : sms;
   const int per = (a.m + G - 1) / G;
+  const size_t smem = qrp_smem_bytes(a.l, a.m, sms);
+  if (a.cand_data && per <= 8 && smem <= kQrSmemLimit) {
+    if (per <= 2) return launch_qrp_smem_t<2>(a, G, smem, st);
+    if (per <= 4) return launch_qrp_smem_t<4>(a, G, smem, st);
+    return launch_qrp_smem_t<8>(a, G, smem, st);
+  }
   note_launch();
   qr_norms_kernel<<<a.m, kQrThreads, 0, st>>>((const zd *)a.Y, a.l, a.vn1, a.vn2);
   cudaError_t e = cudaGetLastError();

@@ -12,13 +12,11 @@
 // kappa(A) * 2^-53 (about 1e-10 at kappa = 1e6; the paper's Tables 2 and 4
 // show raw errors near 1e-9), the CG runs as the inner solver of an outer
 // refinement loop on A A^* y = b (a generalisation of Remark 4.2's extra CG
-// iterations): y is kept as a double-double pair, the residual r = b - A A^* y
-// and x = A^* y are formed with double-double sums when the size of the
-// correction makes FP64 insufficient, and otherwise updated in FP64 as
-// x += A^* dy, r -= A (A^* dy), whose rounding errors scale with the
-// correction rather than with x. Each step is stopped by the a-posteriori
-// bound ||x - p|| <= ||R^{-*} P^T r||, which holds because T has orthonormal
-// rows (sigma_min(M) >= 1, so ||x - p|| = ||M (u - u*)|| <= ||M^* M (u - u*)||).
+// iterations): y is kept as a double-double pair, and after every inner solve
+// x = A^* y and r = b - A x are formed exactly in fixed point on the integer
+// pipe (xprod.cu). The loop stops on the a-posteriori bound
+// ||x - p|| <= ||R^{-*} P^T r||, which holds because T has orthonormal rows
+// (sigma_min(M) >= 1, so ||x - p|| = ||M (u - u*)|| <= ||M^* M (u - u*)||).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -82,6 +80,9 @@ struct minnorm_plan_s {
   zd *d_R = nullptr, *d_Wp = nullptr, *d_WpH = nullptr;
   GridBarrier *d_bar = nullptr;
   int *d_err = nullptr;
+  double *d_cand_val = nullptr;
+  int32_t *d_cand_col = nullptr;
+  zd *d_cand_data = nullptr;
   double rdiag_max = 0, rdiag_min = 0;
   // products
   zf *d_A32 = nullptr;
@@ -100,6 +101,13 @@ struct minnorm_plan_s {
   zf *d_w32 = nullptr;
   void *d_q = nullptr;
   zd *d_xh = nullptr, *d_xl = nullptr, *d_d = nullptr;
+  // fixed-point A for the exact residual
+  void *d_afix = nullptr;
+  int32_t *d_E = nullptr;
+  void *d_yfix = nullptr, *d_xpart = nullptr;
+  int *d_F = nullptr;   // [0] = Fy, [1] = Fx
+  int x_nchunk = 1;
+  int64_t x_chunk = 1;
   // host staging (minnorm_solve_host)
   void *d_Ah = nullptr;
   zd *d_bh = nullptr, *d_xo = nullptr;
@@ -328,6 +336,15 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   ALLOC(plan->d_R, sizeof(zd) * (size_t)m * m);
   ALLOC(plan->d_Wp, sizeof(zd) * (size_t)m * m);
   ALLOC(plan->d_WpH, sizeof(zd) * (size_t)m * m);
+  {
+    const int G = (int)std::min<int64_t>(m, plan->sms);
+    const int per = (int)((m + G - 1) / G);
+    if (per <= 8 && qrp_smem_bytes((int)l, (int)m, plan->sms) <= kQrSmemLimit) {
+      ALLOC(plan->d_cand_val, sizeof(double) * 2 * G);
+      ALLOC(plan->d_cand_col, sizeof(int32_t) * 2 * G);
+      ALLOC(plan->d_cand_data, sizeof(zd) * 2 * (size_t)G * l);
+    }
+  }
   ALLOC(plan->d_bar, sizeof(GridBarrier));
   ALLOC(plan->d_err, sizeof(int));
   if (plan->fp32 && dtype == MINNORM_C128) ALLOC(plan->d_A32, sizeof(zf) * (size_t)m * n);
@@ -340,7 +357,6 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   pb = std::max(pb, gemv_fwd_partial_elems(plan->g_cg) * rc);
   pb = std::max(pb, gemv_adj_partial_elems(plan->g_hp) * sizeof(zd));
   pb = std::max(pb, gemv_fwd_partial_elems(plan->g_hp) * sizeof(zd));
-  pb = std::max(pb, 2 * fwd_dd_partial_elems(plan->g_hp) * sizeof(zd));
   plan->part_bytes = pb;
   ALLOC(plan->d_part, pb);
   plan->nqq = (int)std::min<int64_t>(1024, (n + 255) / 256);
@@ -356,6 +372,18 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   ALLOC(plan->d_xh, sizeof(zd) * n);
   ALLOC(plan->d_xl, sizeof(zd) * n);
   ALLOC(plan->d_d, sizeof(zd) * n);
+  ALLOC(plan->d_afix, sizeof(int64_t) * 2 * (size_t)m * n);
+  ALLOC(plan->d_E, sizeof(int32_t) * m);
+  ALLOC(plan->d_yfix, 32 * (size_t)m);
+  ALLOC(plan->d_F, sizeof(int) * 2);
+  {
+    const int64_t row_blocks = (m + 7) / 8;
+    int64_t nchunk = 1;
+    while (row_blocks * nchunk < 3 * plan->sms && n / (nchunk * 2) >= 1024) nchunk *= 2;
+    plan->x_nchunk = (int)nchunk;
+    plan->x_chunk = (n + nchunk - 1) / nchunk;
+    ALLOC(plan->d_xpart, xprod_partial_bytes(m, plan->x_nchunk));
+  }
   if (cudaMallocHost(&plan->h_norms, sizeof(double) * 4) != cudaSuccess) return MINNORM_ENOMEM;
   if (cudaMallocHost(&plan->h_cg, sizeof(CgScalars)) != cudaSuccess) return MINNORM_ENOMEM;
   draw_srft_params(seed, n, l, plan->P);
@@ -376,8 +404,9 @@ minnorm_status sketch_impl(minnorm_plan_t plan, const void *A, int64_t lda) {
   const void *src = A;
   int64_t lds = lda;
   bool src_c64 = plan->dtype == MINNORM_C64;
+  // fixed-point copy of A for the exact residuals (and the complex64 copy in mixed mode)
+  CK(launch_fix_prep(A, lda, src_c64, m, n, plan->d_afix, plan->d_E, plan->d_A32, st));
   if (plan->fp32 && plan->dtype == MINNORM_C128) {
-    CK(launch_to_c64(A, lda, plan->d_A32, n, m, n, st));
     src = plan->d_A32;
     lds = n;
     src_c64 = true;
@@ -401,7 +430,7 @@ minnorm_status sketch_impl(minnorm_plan_t plan, const void *A, int64_t lda) {
     CK(cudaMemsetAsync(plan->d_bar, 0, sizeof(GridBarrier), st));
     CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
     QrArgs q{plan->d_Y, (int)l, (int)m, plan->d_vn1, plan->d_vn2, plan->d_beta, plan->d_piv, plan->d_R,
-             plan->d_bar, plan->d_err, kBarrierLimitNs};
+             plan->d_bar, plan->d_err, kBarrierLimitNs, plan->d_cand_val, plan->d_cand_col, plan->d_cand_data};
     CK(launch_qrp(q, st));
     CK(launch_prinv(plan->d_R, plan->d_piv, (int)m, plan->d_Wp, plan->d_WpH, st));
   }
@@ -475,6 +504,27 @@ minnorm_status norms(minnorm_plan_t plan, bool with_x, double *gnorm, double *xn
   return MINNORM_OK;
 }
 
+XprodArgs xargs(minnorm_plan_t plan, const void *b) {
+  XprodArgs a{};
+  a.afix = plan->d_afix;
+  a.E = plan->d_E;
+  a.rows = plan->m;
+  a.cols = plan->n;
+  a.yh = plan->d_yh;
+  a.yl = plan->d_yl;
+  a.yfix = plan->d_yfix;
+  a.Fy = plan->d_F;
+  a.Fx = plan->d_F + 1;
+  a.xh = plan->d_xh;
+  a.xl = plan->d_xl;
+  a.b = b;
+  a.r = plan->d_r;
+  a.partial = plan->d_xpart;
+  a.nchunk = plan->x_nchunk;
+  a.chunk = plan->x_chunk;
+  return a;
+}
+
 minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const void *b, double eps, void *x,
                           minnorm_info *info) {
   cudaStream_t st = plan->st;
@@ -490,11 +540,11 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
   CK(cudaMemsetAsync(plan->d_xh, 0, sizeof(zd) * n, st));
   CK(cudaMemsetAsync(plan->d_xl, 0, sizeof(zd) * n, st));
   CK(cudaMemcpyAsync(plan->d_r, b, sizeof(zd) * m, cudaMemcpyDeviceToDevice, st));
-  const double kappa = plan->rdiag_max / std::max(plan->rdiag_min, 1e-300);
   const double tol_inner = plan->fp32 ? 1e-3 : 1e-11;
   const int maxit = plan->fp32 ? 40 : 300;
   double err = INFINITY, best = INFINITY, prev = INFINITY;
-  int cg_total = 0, dd_passes = 0, fp_passes = 0, outer = 0, stagnant = 0;
+  int cg_total = 0, dd_passes = 0, outer = 0, stagnant = 0;
+  (void)A;
   minnorm_status status = MINNORM_ENOCONV;
   for (outer = 0; outer < kMaxOuter; ++outer) {
     // g = Wp^* r (the preconditioned residual), and the bound ||x - p|| <= ||g||
@@ -519,21 +569,10 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
     if (s != MINNORM_OK) return s;
     cg_total += it;
     CK(launch_dd_accumulate(m, plan->d_yh, plan->d_yl, plan->d_dy, st));
-    // correction relative size ~ err (the bound before this step); FP64 suffices
-    // for the update when its cancellation error kappa * 2^-53 * err stays well below eps
-    const bool use_dd = (outer == 0) || (8.0 * kappa * 0x1.0p-53 * err > 0.25 * eps);
-    if (use_dd) {
+    {
       Timed tm(plan, 2);
-      CK(launch_adj_dd(plan->g_hp, A, plan->d_yh, plan->d_yl, plan->d_xh, plan->d_xl, st));
-      CK(launch_fwd_dd(plan->g_hp, A, plan->d_xh, plan->d_xl, plan->d_vh, plan->d_vl, plan->d_part, st));
-      CK(launch_resid_finish(m, b, plan->d_vh, plan->d_vl, plan->d_r, st));
+      CK(launch_xresidual(xargs(plan, b), st));
       dd_passes += 2;
-    } else {
-      CK(launch_gemv_adj(plan->g_hp, A, plan->d_dy, plan->d_d, plan->d_part, nullptr, nullptr, st));
-      CK(launch_dd_accumulate(n, plan->d_xh, plan->d_xl, plan->d_d, st));
-      CK(launch_gemv_fwd(plan->g_hp, A, plan->d_d, plan->d_t, plan->d_part, nullptr, st));
-      CK(launch_sub(m, plan->d_r, plan->d_t, st));
-      fp_passes += 2;
     }
   }
   if (status == MINNORM_ENOCONV && outer == kMaxOuter) {
@@ -560,8 +599,8 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
   if (info) {
     info->outer_steps = outer;
     info->cg_iters = cg_total;
-    info->dd_passes = dd_passes;
-    info->fp64_passes = fp_passes;
+    info->exact_passes = dd_passes;
+    info->reserved0 = 0;
     info->err_bound = err;
     const double bn = std::sqrt(plan->h_norms[3]);
     info->resid_rel = bn > 0 ? std::sqrt(plan->h_norms[2]) / bn : 0.0;
@@ -767,11 +806,15 @@ minnorm_status minnorm_residual_dd(minnorm_plan_t plan, const void *A, int64_t l
                                    const void *y_lo, const void *b, void *r, void *x_hi, void *x_lo) {
   if (!plan || !A || !y_hi || !b || !r || !x_hi || !x_lo) return MINNORM_EINVAL;
   if (lda < plan->n) return MINNORM_EINVAL;
-  plan->g_hp.ld = lda;
   cudaStream_t st = plan->st;
-  CK(launch_adj_dd(plan->g_hp, A, y_hi, y_lo, x_hi, x_lo, st));
-  CK(launch_fwd_dd(plan->g_hp, A, x_hi, x_lo, plan->d_vh, plan->d_vl, plan->d_part, st));
-  CK(launch_resid_finish(plan->m, b, plan->d_vh, plan->d_vl, r, st));
+  CK(launch_fix_prep(A, lda, plan->dtype == MINNORM_C64, plan->m, plan->n, plan->d_afix, plan->d_E, nullptr, st));
+  XprodArgs a = xargs(plan, b);
+  a.yh = y_hi;
+  a.yl = y_lo;
+  a.xh = x_hi;
+  a.xl = x_lo;
+  a.r = r;
+  CK(launch_xresidual(a, st));
   return MINNORM_OK;
 }
 

@@ -46,13 +46,34 @@ class System:
 
 
 def make_system(m, n, exponent, seed, dtype="c128", rhs="gaussian", nrhs=1,
-                device=None, keep_factors=False):
+                device=None, keep_factors=False, cache_dir=None):
     """A (m x n, row-major, complex128 or complex64 storage) and b (m, or m x nrhs).
 
     rhs: "gaussian" (the workloads) or "paper" (b = A p, p = sum eps_j v_j / sqrt(m)).
     device: None/"cpu" builds with numpy; "cuda"/"cuda:0" builds the factors
     with torch on that device and returns torch tensors there.
+    cache_dir: if given, A and b are stored there as .npy files after the first
+    build and loaded on later calls with the same arguments.
     """
+    if cache_dir is not None and not keep_factors:
+        import os
+        key = "sys_%d_%d_%g_%d_%s_%s_%d" % (m, n, exponent, seed, dtype, rhs, nrhs)
+        fa, fb = os.path.join(cache_dir, key + "_A.npy"), os.path.join(cache_dir, key + "_b.npy")
+        if os.path.exists(fa) and os.path.exists(fb):
+            A, b = np.load(fa), np.load(fb)
+            if device is not None and device != "cpu":
+                import torch
+                return System(torch.from_numpy(A).to(device), torch.from_numpy(b).to(device))
+            return System(A, b)
+        sysm = make_system(m, n, exponent, seed, dtype, rhs, nrhs, device)
+        os.makedirs(cache_dir, exist_ok=True)
+        A = sysm.A if isinstance(sysm.A, np.ndarray) else sysm.A.cpu().numpy()
+        b = sysm.b if isinstance(sysm.b, np.ndarray) else sysm.b.cpu().numpy()
+        np.save(fa + ".tmp.npy", A)
+        np.save(fb + ".tmp.npy", b)
+        os.replace(fa + ".tmp.npy", fa)
+        os.replace(fb + ".tmp.npy", fb)
+        return sysm
     rng = np.random.default_rng(seed)
     Gu = _gauss(rng, (m, m))
     Gv = _gauss(rng, (n, m))
