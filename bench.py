@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error check and CPU baseline")
+    ap.add_argument("--m", type=int, default=W["m"], help="rows (profiling runs of a smaller case)")
+    ap.add_argument("--n", type=int, default=W["n"], help="columns (profiling runs of a smaller case)")
     return ap.parse_args()
 
 
@@ -206,7 +208,7 @@ def main():
     from paper_0905_4745_gb300 import minnorm as mn
     import synth
 
-    m, n, eps = W["m"], W["n"], W["eps"]
+    m, n, eps = args.m, args.n, W["eps"]
     cache = os.environ.get("MINNORM_INPUT_CACHE", os.path.join(tempfile.gettempdir(), "minnorm_inputs"))
     s = synth.make_system(m, n, W["exponent"], W["seed"] + 100 * rank, device=str(device), cache_dir=cache)
     A, b = s.A, s.b
@@ -343,7 +345,9 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 products + f64 QR/R + dd residual" if mixed else "f64 + dd residual",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "m": m, "n": n, "l": l, "eps": eps,
+        "config": {"workload": WORKLOAD_NAME if (m, n) == (W["m"], W["n"]) else
+                   "%dx%d complex128 (profiling case, not the benchmark workload)" % (m, n),
+                   "m": m, "n": n, "l": l, "eps": eps,
                    "precision": "mixed" if mixed else "fp64", "storage": "complex128",
                    "l2": "no flush: A (512 MiB) exceeds L2 (129 MB)", "replicas": world},
         "rel_err_vs_oracle": err_main, "err_bound": last_info["err_bound"], "status": mn.STATUS_NAMES[last_st],

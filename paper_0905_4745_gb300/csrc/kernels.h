@@ -61,14 +61,7 @@ struct QrArgs {
   GridBarrier *bar;
   int *err;
   uint64_t limit_ns;
-  // candidate slots of the shared-memory variant (nullptr: use the L2 variant)
-  double *cand_val;       // 2 x G
-  int32_t *cand_col;      // 2 x G
-  void *cand_data;        // 2 x G x l complex128
 };
-// shared memory the shared-memory variant needs; it is used when this is at most kQrSmemLimit
-constexpr size_t kQrSmemLimit = 200 * 1024;
-size_t qrp_smem_bytes(int l, int m, int sms);
 cudaError_t launch_qrp(const QrArgs &a, cudaStream_t st);
 
 // Wp = P R^{-1} (row-major m x m) and WpH = Wp^* (row-major)

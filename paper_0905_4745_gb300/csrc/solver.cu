@@ -80,9 +80,6 @@ struct minnorm_plan_s {
   zd *d_R = nullptr, *d_Wp = nullptr, *d_WpH = nullptr;
   GridBarrier *d_bar = nullptr;
   int *d_err = nullptr;
-  double *d_cand_val = nullptr;
-  int32_t *d_cand_col = nullptr;
-  zd *d_cand_data = nullptr;
   double rdiag_max = 0, rdiag_min = 0;
   // products
   zf *d_A32 = nullptr;
@@ -336,15 +333,6 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   ALLOC(plan->d_R, sizeof(zd) * (size_t)m * m);
   ALLOC(plan->d_Wp, sizeof(zd) * (size_t)m * m);
   ALLOC(plan->d_WpH, sizeof(zd) * (size_t)m * m);
-  {
-    const int G = (int)std::min<int64_t>(m, plan->sms);
-    const int per = (int)((m + G - 1) / G);
-    if (per <= 8 && qrp_smem_bytes((int)l, (int)m, plan->sms) <= kQrSmemLimit) {
-      ALLOC(plan->d_cand_val, sizeof(double) * 2 * G);
-      ALLOC(plan->d_cand_col, sizeof(int32_t) * 2 * G);
-      ALLOC(plan->d_cand_data, sizeof(zd) * 2 * (size_t)G * l);
-    }
-  }
   ALLOC(plan->d_bar, sizeof(GridBarrier));
   ALLOC(plan->d_err, sizeof(int));
   if (plan->fp32 && dtype == MINNORM_C128) ALLOC(plan->d_A32, sizeof(zf) * (size_t)m * n);
@@ -430,7 +418,7 @@ minnorm_status sketch_impl(minnorm_plan_t plan, const void *A, int64_t lda) {
     CK(cudaMemsetAsync(plan->d_bar, 0, sizeof(GridBarrier), st));
     CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
     QrArgs q{plan->d_Y, (int)l, (int)m, plan->d_vn1, plan->d_vn2, plan->d_beta, plan->d_piv, plan->d_R,
-             plan->d_bar, plan->d_err, kBarrierLimitNs, plan->d_cand_val, plan->d_cand_col, plan->d_cand_data};
+             plan->d_bar, plan->d_err, kBarrierLimitNs};
     CK(launch_qrp(q, st));
     CK(launch_prinv(plan->d_R, plan->d_piv, (int)m, plan->d_Wp, plan->d_WpH, st));
   }
