@@ -207,8 +207,9 @@ int64_t minnorm_launch_count(void);
 
 /* Kernel timing since the last minnorm_sketch when the plan has
  * MINNORM_FLAG_TIMING: for kernel class k (0: CG product A^* w, 1: CG product
- * A q, 2: a double-double residual (both passes), 3: QR and P R^{-1},
- * 4: sketch (both chains and the FFT)) the number of timed regions and their
+ * A q, 2: an exact residual (x = A^* y and b - A x), 3: QR and P R^{-1},
+ * 4: sketch (both chains and the FFT), 5: fused CG solves) the number of
+ * timed regions (for k = 5: the CG iterations run inside them) and their
  * summed milliseconds (CUDA events on the plan's stream). Errors: EINVAL. */
 minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *launches, double *ms);
 

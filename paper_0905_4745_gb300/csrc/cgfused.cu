@@ -1,0 +1,391 @@
+// cgfused.cu -- Step 4 (Eq. overdet) as one persistent cooperative kernel for
+// the mixed-precision path: conjugate gradients on
+//     (Wp^* A A^* Wp) du = g,   Wp = P R^{-1},
+// with every iteration reading A (complex64) from HBM exactly once.
+//
+// Each CTA owns a contiguous range of 16-column sub-panels of A (m <= 512
+// rows). A sub-panel (m x 16 complex64, 128 bytes per row) is brought into
+// shared memory by 2-D TMA loads (cp.async.bulk.tensor, 128-byte swizzle)
+// through a two-stage mbarrier pipeline, and used twice while resident:
+//     q_j  = sum_i conj(A_ij) w_i      for the sub-panel's 16 columns
+//     t_i += sum_j A_ij q_j            for all m rows (per-thread accumulators)
+// so A^* w and A (A^* w) cost one pass. The FP64 parts (w = Wp p,
+// Np = Wp^* t, the CG scalars) are spread over the CTAs by rows, between four
+// grid barriers per iteration (bounded waits, see common.cuh). The search
+// direction p is kept, identically, in every CTA's shared memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "vec.h"
+
+namespace mn {
+
+constexpr int kCgThreads = 512;
+constexpr int kPanel = 16;      // columns per sub-panel: 16 complex64 = 128 bytes
+constexpr int kBoxRows = 256;   // rows per TMA box
+constexpr int kMaxFusedRows = 512;
+
+struct CgFusedParams {
+  int m, n, nbox;
+  const zd *Wp, *WpH;
+  const zd *g;
+  zd *u, *s, *w, *t, *dy;
+  zf *tpart;        // G x m
+  double *qq_part;  // G
+  double *gg_part;  // G
+  CgScalars *sc;
+  double tol2;
+  int maxit;
+  GridBarrier *bar;
+  int *err;
+  uint64_t limit_ns;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// wait for the phase with the given parity, at most limit_ns
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// out[i] = sum_k M[i][k] v[k] for i in [r0, r1): one warp per row (FP64)
+__device__ __forceinline__ void rows_dot(const zd *__restrict__ M, const zd *v, int m, int r0, int r1,
+                                         zd *out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = r0 + wid; i < r1; i += nw) {
+    const zd *row = M + (int64_t)i * m;
+    double re = 0.0, im = 0.0;
+    for (int k = lane; k < m; k += 32) {
+      const zd a = row[k], x = v[k];
+      re = fma(a.re, x.re, fma(-a.im, x.im, re));
+      im = fma(a.re, x.im, fma(a.im, x.re, im));
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) out[i] = {re, im};
+  }
+}
+
+__global__ void __launch_bounds__(kCgThreads, 1)
+cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int m = P.m, nbox = P.nbox;
+  const int rows_pad = nbox * kBoxRows;
+  const int stage_bytes = rows_pad * 128;
+  unsigned char *stage[2] = {base, base + stage_bytes};
+  zd *p_s = reinterpret_cast<zd *>(base + 2 * stage_bytes);     // m: search direction
+  zd *v_s = p_s + m;                                            // m: t, then u
+  zf *w_s = reinterpret_cast<zf *>(v_s + m);                    // rows_pad: w in FP32
+  zf *qpart = w_s + rows_pad;                                   // 32 x 16
+  zf *q_s = qpart + 32 * kPanel;                                // 16
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(q_s + kPanel);  // 2
+  __shared__ double red[32];
+  __shared__ double s_scal[4];
+
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int r0 = (int)((long long)m * b / G), r1 = (int)((long long)m * (b + 1) / G);
+  const int NP = (P.n + kPanel - 1) / kPanel;
+  const int sp0 = (int)((long long)NP * b / G), sp1 = (int)((long long)NP * (b + 1) / G);
+  const uint32_t stage_tx = (uint32_t)stage_bytes;
+
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // start: u = 0, s = p = g
+  double loc = 0.0;
+  for (int i = tid; i < m; i += blockDim.x) {
+    const zd gi = P.g[i];
+    p_s[i] = gi;
+    loc = fma(gi.re, gi.re, fma(gi.im, gi.im, loc));
+  }
+  for (int i = r0 + tid; i < r1; i += blockDim.x) {
+    P.s[i] = P.g[i];
+    P.u[i] = {0.0, 0.0};
+  }
+  for (int i = m + tid; i < rows_pad; i += blockDim.x) w_s[i] = {0.f, 0.f};
+  double gamma = block_sum(loc, red);
+  const double gamma0 = gamma;
+  bool done = !(gamma > 0.0);
+  uint32_t parity[2] = {0u, 0u};
+  int it = 0;
+  bool ok = true;
+
+  while (!done && it < P.maxit) {
+    // P1: w = Wp p (own rows)
+    rows_dot(P.Wp, p_s, m, r0, r1, P.w);
+    if (!grid_sync(P.bar, G, P.limit_ns)) { ok = false; break; }
+
+    // P2: q = A^* w and t = A q over the own sub-panels, A read once
+    for (int i = tid; i < m; i += blockDim.x) {
+      const zd wi = P.w[i];
+      w_s[i] = {(float)wi.re, (float)wi.im};
+    }
+    __syncthreads();
+    zf tacc = {0.f, 0.f};
+    double qq_loc = 0.0;
+    if (tid == 0) {
+      for (int q = 0; q < 2 && sp0 + q < sp1; ++q) {
+        mbar_expect_tx(&mbar[q], stage_tx);
+        for (int bx = 0; bx < nbox; ++bx)
+          tma_load_2d(stage[q] + bx * kBoxRows * 128, &amap, (sp0 + q) * 2 * kPanel, bx * kBoxRows, &mbar[q]);
+      }
+    }
+    for (int sp = sp0; sp < sp1; ++sp) {
+      const int st = (sp - sp0) & 1;
+      bool w_ok = mbar_wait(&mbar[st], parity[st], P.limit_ns);
+      if (!w_ok) w_ok = mbar_wait(&mbar[st], parity[st], P.limit_ns);  // a second bounded wait
+      parity[st] ^= 1u;
+      if (__syncthreads_or(!w_ok)) {
+        // give up uniformly; the other stage may still hold an issued copy: wait for it (bounded)
+        ok = false;
+        if (sp + 1 < sp1) mbar_wait(&mbar[st ^ 1], parity[st ^ 1], P.limit_ns);
+        break;
+      }
+      const unsigned char *S = stage[st];
+      // (a) partial q_j over row group grp
+      {
+        const int j = tid & (kPanel - 1), grp = tid >> 4;   // 32 groups
+        const int rg = rows_pad / 32;
+        zf acc = {0.f, 0.f};
+        for (int r = grp * rg; r < (grp + 1) * rg; ++r) {
+          const zf a = *reinterpret_cast<const zf *>(S + r * 128 + (((j >> 1) ^ (r & 7)) << 4) + ((j & 1) << 3));
+          macc(acc, a, w_s[r]);
+        }
+        qpart[grp * kPanel + j] = acc;
+      }
+      __syncthreads();
+      if (tid < kPanel) {
+        zf q = {0.f, 0.f};
+        for (int g2 = 0; g2 < 32; ++g2) {
+          const zf v = qpart[g2 * kPanel + tid];
+          q.re += v.re;
+          q.im += v.im;
+        }
+        q_s[tid] = q;
+        if (sp * kPanel + tid < P.n) qq_loc = fma((double)q.re, (double)q.re, fma((double)q.im, (double)q.im, qq_loc));
+      }
+      __syncthreads();
+      // (b) t_i += sum_j A_ij q_j, one row per thread
+      if (tid < m) {
+        const int i = tid;
+        const unsigned char *row = S + i * 128;
+#pragma unroll
+        for (int kc = 0; kc < 8; ++kc) {
+          const float4 v = *reinterpret_cast<const float4 *>(row + ((kc ^ (i & 7)) << 4));
+          const zf a0 = {v.x, v.y}, a1 = {v.z, v.w};
+          mac(tacc, a0, q_s[2 * kc]);
+          mac(tacc, a1, q_s[2 * kc + 1]);
+        }
+      }
+      __syncthreads();  // stage st is free
+      if (tid == 0 && sp + 2 < sp1) {
+        mbar_expect_tx(&mbar[st], stage_tx);
+        for (int bx = 0; bx < nbox; ++bx)
+          tma_load_2d(stage[st] + bx * kBoxRows * 128, &amap, (sp + 2) * 2 * kPanel, bx * kBoxRows, &mbar[st]);
+      }
+    }
+    if (!ok) break;
+    if (tid < m) P.tpart[(int64_t)b * m + tid] = tacc;
+    if (wid == 0) {
+      const double qsum = warp_sum(qq_loc);
+      if (lane == 0) P.qq_part[b] = qsum;
+    }
+    if (!grid_sync(P.bar, G, P.limit_ns)) { ok = false; break; }
+
+    // P3a: t (own rows) = sum of the partials; qq = sum of the per-CTA |q|^2
+    for (int i = r0 + wid; i < r1; i += blockDim.x >> 5) {
+      double re = 0.0, im = 0.0;
+      for (int c = lane; c < G; c += 32) {
+        const zf v = P.tpart[(int64_t)c * m + i];
+        re += (double)v.re;
+        im += (double)v.im;
+      }
+      re = warp_sum(re);
+      im = warp_sum(im);
+      if (lane == 0) P.t[i] = {re, im};
+    }
+    if (wid == 0) {
+      double qs = 0.0;
+      for (int c = lane; c < G; c += 32) qs += P.qq_part[c];
+      qs = warp_sum(qs);
+      if (lane == 0) s_scal[0] = qs;
+    }
+    if (!grid_sync(P.bar, G, P.limit_ns)) { ok = false; break; }
+    const double qq = s_scal[0];
+    const double alpha = qq > 0.0 ? gamma / qq : 0.0;
+
+    // P3b: Np = Wp^* t (own rows); s -= alpha Np; u += alpha p; partial ||s||^2
+    for (int i = tid; i < m; i += blockDim.x) v_s[i] = P.t[i];
+    __syncthreads();
+    rows_dot(P.WpH, v_s, m, r0, r1, P.dy);   // dy holds Np for the own rows here
+    __syncthreads();
+    double gl = 0.0;
+    for (int i = r0 + tid; i < r1; i += blockDim.x) {
+      const zd np = P.dy[i], pi = p_s[i];
+      zd si = P.s[i], ui = P.u[i];
+      si.re = fma(-alpha, np.re, si.re);
+      si.im = fma(-alpha, np.im, si.im);
+      ui.re = fma(alpha, pi.re, ui.re);
+      ui.im = fma(alpha, pi.im, ui.im);
+      P.s[i] = si;
+      P.u[i] = ui;
+      gl = fma(si.re, si.re, fma(si.im, si.im, gl));
+    }
+    if (wid == 0) {
+      const double gs = warp_sum(gl);
+      if (lane == 0) P.gg_part[b] = gs;
+    }
+    if (!grid_sync(P.bar, G, P.limit_ns)) { ok = false; break; }
+
+    // P4: gamma' and the new direction, identically in every CTA
+    if (wid == 0) {
+      double gs = 0.0;
+      for (int c = lane; c < G; c += 32) gs += P.gg_part[c];
+      gs = warp_sum(gs);
+      if (lane == 0) s_scal[1] = gs;
+    }
+    __syncthreads();
+    const double gnew = s_scal[1];
+    const double beta = gamma > 0.0 ? gnew / gamma : 0.0;
+    for (int i = tid; i < m; i += blockDim.x) {
+      const zd si = P.s[i];
+      zd pi = p_s[i];
+      pi.re = fma(beta, pi.re, si.re);
+      pi.im = fma(beta, pi.im, si.im);
+      p_s[i] = pi;
+    }
+    gamma = gnew;
+    ++it;
+    if (gnew <= P.tol2 * gamma0 || !(qq > 0.0)) done = true;
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(P.err, 1);
+    // no TMA load is left in flight: every issued stage was waited for above
+    return;
+  }
+  // dy = Wp u (own rows)
+  if (!grid_sync(P.bar, G, P.limit_ns)) {
+    if (tid == 0) atomicExch(P.err, 1);
+    return;
+  }
+  for (int i = tid; i < m; i += blockDim.x) v_s[i] = P.u[i];
+  __syncthreads();
+  rows_dot(P.Wp, v_s, m, r0, r1, P.dy);
+  if (b == 0 && tid == 0) {
+    P.sc->iters = it;
+    P.sc->gamma = gamma;
+    P.sc->gamma0 = gamma0;
+    P.sc->done = done ? 1 : 0;
+  }
+}
+
+// ---- host -------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool cg_fused_supported(int64_t m, int64_t n, int64_t lda, const void *A) {
+  return m >= 1 && m <= kMaxFusedRows && n >= kPanel && (lda % 2) == 0 && (((uintptr_t)A) & 15) == 0 &&
+         get_encode() != nullptr;
+}
+
+size_t cg_fused_smem(int64_t m) {
+  const int nbox = (int)((m + kBoxRows - 1) / kBoxRows);
+  const size_t rows_pad = (size_t)nbox * kBoxRows;
+  return 1024 + 2 * rows_pad * 128 + 2 * (size_t)m * sizeof(zd) + rows_pad * sizeof(zf) +
+         (32 * kPanel + kPanel) * sizeof(zf) + 2 * sizeof(uint64_t);
+}
+
+cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap map;
+  // A as a 2-D array of floats: dim0 = 2n (re, im interleaved), dim1 = m rows
+  const cuuint64_t gdim[2] = {(cuuint64_t)(2 * a.n), (cuuint64_t)a.m};
+  const cuuint64_t gstride[1] = {(cuuint64_t)(a.lda * sizeof(zf))};
+  const cuuint32_t box[2] = {2 * kPanel, kBoxRows};
+  const cuuint32_t estride[2] = {1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(a.A), gdim, gstride, box,
+                   estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  CgFusedParams P;
+  P.m = (int)a.m;
+  P.n = (int)a.n;
+  P.nbox = (int)((a.m + kBoxRows - 1) / kBoxRows);
+  P.Wp = (const zd *)a.Wp;
+  P.WpH = (const zd *)a.WpH;
+  P.g = (const zd *)a.g;
+  P.u = (zd *)a.u;
+  P.s = (zd *)a.s;
+  P.w = (zd *)a.w;
+  P.t = (zd *)a.t;
+  P.dy = (zd *)a.dy;
+  P.tpart = (zf *)a.tpart;
+  P.qq_part = a.qq_part;
+  P.gg_part = a.gg_part;
+  P.sc = a.sc;
+  P.tol2 = a.tol2;
+  P.maxit = a.maxit;
+  P.bar = a.bar;
+  P.err = a.err;
+  P.limit_ns = a.limit_ns;
+  const size_t smem = cg_fused_smem(a.m);
+  cudaError_t e = cudaFuncSetAttribute(cg_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int NP = (int)((a.n + kPanel - 1) / kPanel);
+  const int G = a.grid < NP ? a.grid : NP;
+  void *args[] = {(void *)&map, (void *)&P};
+  note_launch();
+  return cudaLaunchCooperativeKernel((const void *)cg_fused_kernel, dim3(G), dim3(kCgThreads), args, smem, st);
+}
+
+}  // namespace mn

@@ -117,6 +117,26 @@ cudaError_t launch_fix_prep(const void *A, int64_t lda, bool c64, int64_t rows, 
 cudaError_t launch_xresidual(const XprodArgs &a, cudaStream_t st);
 size_t xprod_partial_bytes(int64_t rows, int nchunk);
 
+// ---- cgfused.cu ---------------------------------------------------------------
+struct CgScalars;
+struct CgFusedArgs {
+  const void *A;           // complex64, row-major, lda even, 16-byte aligned
+  int64_t m, n, lda;
+  const void *Wp, *WpH, *g;
+  void *u, *s, *w, *t, *dy;
+  void *tpart;             // grid x m complex64
+  double *qq_part, *gg_part;  // grid each
+  CgScalars *sc;
+  double tol2;
+  int maxit;
+  GridBarrier *bar;
+  int *err;
+  uint64_t limit_ns;
+  int grid;                // CTAs (one per SM)
+};
+bool cg_fused_supported(int64_t m, int64_t n, int64_t lda, const void *A);
+cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st);
+
 // small dense m x m FP64 products: out = M v (M row-major), optionally also an FP32 copy
 cudaError_t launch_small_gemv(const void *M, int m, const void *v, void *out, void *out32, const int *skip,
                               cudaStream_t st);

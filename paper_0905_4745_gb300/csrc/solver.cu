@@ -105,6 +105,10 @@ struct minnorm_plan_s {
   int *d_F = nullptr;   // [0] = Fy, [1] = Fx
   int x_nchunk = 1;
   int64_t x_chunk = 1;
+  // fused CG (mixed precision, m <= 512)
+  bool fused_ok = false;
+  zf *d_tpart = nullptr;
+  double *d_qqp = nullptr, *d_ggp = nullptr;
   // host staging (minnorm_solve_host)
   void *d_Ah = nullptr;
   zd *d_bh = nullptr, *d_xo = nullptr;
@@ -115,9 +119,10 @@ struct minnorm_plan_s {
   std::vector<KernelTimer> timers;
   std::vector<cudaEvent_t> event_pool;
   size_t event_next = 0;
-  int stat_launches[5] = {0, 0, 0, 0, 0};
-  double stat_ms[5] = {0, 0, 0, 0, 0};
+  int stat_launches[6] = {0, 0, 0, 0, 0, 0};
+  double stat_ms[6] = {0, 0, 0, 0, 0, 0};
   float ms_sketch = 0, ms_qr = 0, ms_solve = 0;
+  int fused_iters = 0;
   std::vector<void *> allocs;
 };
 
@@ -186,7 +191,8 @@ struct Timed {
 };
 
 void reset_stats(minnorm_plan_t plan) {
-  for (int k = 0; k < 5; ++k) { plan->stat_launches[k] = 0; plan->stat_ms[k] = 0; }
+  for (int k = 0; k < 6; ++k) { plan->stat_launches[k] = 0; plan->stat_ms[k] = 0; }
+  plan->fused_iters = 0;
 }
 
 void collect_timers(minnorm_plan_t plan) {
@@ -372,6 +378,12 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
     plan->x_chunk = (n + nchunk - 1) / nchunk;
     ALLOC(plan->d_xpart, xprod_partial_bytes(m, plan->x_nchunk));
   }
+  if (plan->fp32 && m <= 512) {
+    plan->fused_ok = true;
+    ALLOC(plan->d_tpart, sizeof(zf) * (size_t)plan->sms * m);
+    ALLOC(plan->d_qqp, sizeof(double) * plan->sms);
+    ALLOC(plan->d_ggp, sizeof(double) * plan->sms);
+  }
   if (cudaMallocHost(&plan->h_norms, sizeof(double) * 4) != cudaSuccess) return MINNORM_ENOMEM;
   if (cudaMallocHost(&plan->h_cg, sizeof(CgScalars)) != cudaSuccess) return MINNORM_ENOMEM;
   draw_srft_params(seed, n, l, plan->P);
@@ -450,6 +462,49 @@ minnorm_status sketch_impl(minnorm_plan_t plan, const void *A, int64_t lda) {
 minnorm_status inner_cg(minnorm_plan_t plan, const void *Acg, double tol, int maxit, int *iters) {
   cudaStream_t st = plan->st;
   const int m = (int)plan->m;
+  const int64_t lda_cg = plan->g_cg.ld;
+  if (plan->fused_ok && cg_fused_supported(plan->m, plan->n, lda_cg, Acg)) {
+    CK(cudaMemsetAsync(plan->d_bar, 0, sizeof(GridBarrier), st));
+    CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
+    CgFusedArgs a{};
+    a.A = Acg;
+    a.m = plan->m;
+    a.n = plan->n;
+    a.lda = lda_cg;
+    a.Wp = plan->d_Wp;
+    a.WpH = plan->d_WpH;
+    a.g = plan->d_g;
+    a.u = plan->d_u;
+    a.s = plan->d_s;
+    a.w = plan->d_w;
+    a.t = plan->d_t;
+    a.dy = plan->d_dy;
+    a.tpart = plan->d_tpart;
+    a.qq_part = plan->d_qqp;
+    a.gg_part = plan->d_ggp;
+    a.sc = plan->d_cg;
+    a.tol2 = tol * tol;
+    a.maxit = maxit;
+    a.bar = plan->d_bar;
+    a.err = plan->d_err;
+    a.limit_ns = kBarrierLimitNs;
+    a.grid = plan->sms;
+    {
+      Timed tm(plan, 5);
+      CK(launch_cg_fused(a, st));
+    }
+    int err = 0;
+    CK(cudaMemcpyAsync(plan->h_cg, plan->d_cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err) {
+      plan->failed = true;
+      return MINNORM_ETIMEOUT;
+    }
+    *iters = plan->h_cg->iters;
+    plan->fused_iters += *iters;
+    return MINNORM_OK;
+  }
   const int *done = &plan->d_cg->done;
   CK(launch_cg_init(m, plan->d_g, plan->d_u, plan->d_s, plan->d_p, plan->d_cg, st));
   const int chunk = plan->fp32 ? 4 : 8;
@@ -809,8 +864,8 @@ minnorm_status minnorm_residual_dd(minnorm_plan_t plan, const void *A, int64_t l
 int64_t minnorm_launch_count(void) { return (int64_t)launches_so_far(); }
 
 minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *launches, double *ms) {
-  if (!plan || k < 0 || k > 4 || !launches || !ms) return MINNORM_EINVAL;
-  *launches = plan->stat_launches[k];
+  if (!plan || k < 0 || k > 5 || !launches || !ms) return MINNORM_EINVAL;
+  *launches = k == 5 ? plan->fused_iters : plan->stat_launches[k];
   *ms = plan->stat_ms[k];
   return MINNORM_OK;
 }
