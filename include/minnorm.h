@@ -213,6 +213,31 @@ int64_t minnorm_launch_count(void);
  * summed milliseconds (CUDA events on the plan's stream). Errors: EINVAL. */
 minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *launches, double *ms);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free entry point. The paper has no counterpart: this is the
+ * pivoted QR of Step 2 offered to callers that cannot allocate device memory
+ * (their memory belongs to another allocator, e.g. a framework's caching
+ * allocator or a pool fixed at start-up, or they run on a latency-critical
+ * path where cudaMalloc/cudaFree may synchronize the device).
+ *
+ * Y P = Q R for Y (device, l x m complex128, column-major, ldy == l, l >= m),
+ * computed by the same kernel as minnorm_sketch's Step 2. Y is overwritten
+ * (used as workspace). Writes R (device, m x m complex128, column-major, upper
+ * triangular, real diagonal) and the pivots (device, m int64: column k of R
+ * belongs to column piv[k] of Y). The kernel's scratch lives in one fixed
+ * device array of 160 KiB inside the library, held by every GPU that loads
+ * the library until the process exits; m may be at most 4096, larger m
+ * returns MINNORM_ENOTSUP. Nothing is allocated: no cudaMalloc or cudaFree is
+ * called. The first call on a device looks up that array's device address
+ * (once per device), so make it before any stream capture. All calls share
+ * the array: calls whose work may overlap on the GPU (other streams, other
+ * host threads) race and must be serialized by the caller. Work is enqueued
+ * on `stream` (cudaStream_t as void*); the call synchronizes it to read the
+ * barrier's status. Errors: EINVAL (null pointers, sizes), ENOTSUP (m > 4096),
+ * ETIMEOUT (a bounded grid-barrier wait expired), ECUDA. */
+minnorm_status minnorm_qr_noalloc(void *Y, int64_t ldy, int64_t l, int64_t m, void *R_out, void *piv_out,
+                                  void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ FLAG_TIMING, FLAG_KEEP_SKETCH = 1, 2
 EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_sketch", "minnorm_solve",
            "minnorm_solve_host", "minnorm_plan_destroy", "minnorm_status_string", "minnorm_get_sketch",
            "minnorm_get_factor", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats",
-           "minnorm_launch_count"]
+           "minnorm_launch_count", "minnorm_qr_noalloc"]
 
 
 class MinnormError(RuntimeError):
@@ -66,6 +66,7 @@ def lib():
         L.minnorm_cg_products.argtypes = [p, p, i64, p, p, p]
         L.minnorm_residual_dd.argtypes = [p, p, i64, p, p, p, p, p, p]
         L.minnorm_kernel_stats.argtypes = [p, i32, C.POINTER(i32), C.POINTER(d)]
+        L.minnorm_qr_noalloc.argtypes = [p, i64, i64, i64, p, p, p]
         L.minnorm_launch_count.argtypes = []
         L.minnorm_launch_count.restype = C.c_int64
         for name in EXPORTS:
@@ -181,3 +182,9 @@ def minnorm_kernel_stats(plan, k):
 
 def minnorm_launch_count():
     return int(lib().minnorm_launch_count())
+
+
+def minnorm_qr_noalloc(Y, l, m, R_out, piv_out, stream=None):
+    """Pivoted QR of Y (l x m, column-major, overwritten) with the library's fixed scratch."""
+    return _check(lib().minnorm_qr_noalloc(_ptr(Y), int(l), int(l), int(m), _ptr(R_out), _ptr(piv_out),
+                                           _stream(stream)), "minnorm_qr_noalloc")
