@@ -6,7 +6,7 @@
 // Each CTA owns a contiguous range of 16-column sub-panels of A (m <= 512
 // rows). A sub-panel (m x 16 complex64, 128 bytes per row) is brought into
 // shared memory by 2-D TMA loads (cp.async.bulk.tensor, 128-byte swizzle)
-// through a two-stage mbarrier pipeline, and used twice while resident:
+// through a three-stage mbarrier pipeline, and used twice while resident:
 //     q_j  = sum_i conj(A_ij) w_i      for the sub-panel's 16 columns
 //     t_i += sum_j A_ij q_j            for all m rows (per-thread accumulators)
 // so A^* w and A (A^* w) cost one pass. The FP64 parts (w = Wp p,
@@ -26,6 +26,7 @@ constexpr int kCgThreads = 512;
 constexpr int kPanel = 16;      // columns per sub-panel: 16 complex64 = 128 bytes
 constexpr int kBoxRows = 256;   // rows per TMA box
 constexpr int kMaxFusedRows = 512;
+constexpr int kStages = 3;      // TMA ring depth
 
 struct CgFusedParams {
   int m, n, nbox;
@@ -108,15 +109,17 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
   const int m = P.m, nbox = P.nbox;
   const int rows_pad = nbox * kBoxRows;
   const int stage_bytes = rows_pad * 128;
-  unsigned char *stage[2] = {base, base + stage_bytes};
-  zd *p_s = reinterpret_cast<zd *>(base + 2 * stage_bytes);     // m: search direction
-  zd *v_s = p_s + m;                                            // m: t, then u
-  zf *w_s = reinterpret_cast<zf *>(v_s + m);                    // rows_pad: w in FP32
-  zf *qpart = w_s + rows_pad;                                   // 32 x 16
-  zf *q_s = qpart + 32 * kPanel;                                // 16
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(q_s + kPanel);  // 2
+  unsigned char *stage[kStages];
+#pragma unroll
+  for (int q = 0; q < kStages; ++q) stage[q] = base + q * stage_bytes;
+  zd *p_s = reinterpret_cast<zd *>(base + kStages * stage_bytes);  // m: search direction
+  zd *v_s = p_s + m;                                               // m: t, then u
+  zf *w_s = reinterpret_cast<zf *>(v_s + m);                       // rows_pad: w in FP32
+  zf *q_s = w_s + rows_pad;                                        // 16
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(q_s + kPanel);     // kStages
   __shared__ double red[32];
   __shared__ double s_scal[4];
+  __shared__ double s_qq[kCgThreads / 32];
 
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
@@ -126,8 +129,7 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
   const uint32_t stage_tx = (uint32_t)stage_bytes;
 
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int q = 0; q < kStages; ++q) mbar_init(&mbar[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // start: u = 0, s = p = g
@@ -145,7 +147,7 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
   double gamma = block_sum(loc, red);
   const double gamma0 = gamma;
   bool done = !(gamma > 0.0);
-  uint32_t parity[2] = {0u, 0u};
+  uint32_t parity[kStages] = {};
   int it = 0;
   bool ok = true;
 
@@ -163,45 +165,42 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
     zf tacc = {0.f, 0.f};
     double qq_loc = 0.0;
     if (tid == 0) {
-      for (int q = 0; q < 2 && sp0 + q < sp1; ++q) {
+      for (int q = 0; q < kStages && sp0 + q < sp1; ++q) {
         mbar_expect_tx(&mbar[q], stage_tx);
         for (int bx = 0; bx < nbox; ++bx)
           tma_load_2d(stage[q] + bx * kBoxRows * 128, &amap, (sp0 + q) * 2 * kPanel, bx * kBoxRows, &mbar[q]);
       }
     }
+    int st = 0;
     for (int sp = sp0; sp < sp1; ++sp) {
-      const int st = (sp - sp0) & 1;
       bool w_ok = mbar_wait(&mbar[st], parity[st], P.limit_ns);
       if (!w_ok) w_ok = mbar_wait(&mbar[st], parity[st], P.limit_ns);  // a second bounded wait
       parity[st] ^= 1u;
       if (__syncthreads_or(!w_ok)) {
-        // give up uniformly; the other stage may still hold an issued copy: wait for it (bounded)
+        // give up uniformly; later stages may still hold issued copies: wait for them (bounded)
         ok = false;
-        if (sp + 1 < sp1) mbar_wait(&mbar[st ^ 1], parity[st ^ 1], P.limit_ns);
+        for (int q = 1; q < kStages && sp + q < sp1; ++q) {
+          const int s2 = (st + q) % kStages;
+          mbar_wait(&mbar[s2], parity[s2], P.limit_ns);
+        }
         break;
       }
       const unsigned char *S = stage[st];
-      // (a) partial q_j over row group grp
+      // (a) q_j = sum_i conj(A_ij) w_i: warp j takes column j, lanes stride over the rows
       {
-        const int j = tid & (kPanel - 1), grp = tid >> 4;   // 32 groups
-        const int rg = rows_pad / 32;
+        const int j = wid;   // 16 warps, 16 columns
         zf acc = {0.f, 0.f};
-        for (int r = grp * rg; r < (grp + 1) * rg; ++r) {
+        for (int r = lane; r < rows_pad; r += 32) {
           const zf a = *reinterpret_cast<const zf *>(S + r * 128 + (((j >> 1) ^ (r & 7)) << 4) + ((j & 1) << 3));
           macc(acc, a, w_s[r]);
         }
-        qpart[grp * kPanel + j] = acc;
-      }
-      __syncthreads();
-      if (tid < kPanel) {
-        zf q = {0.f, 0.f};
-        for (int g2 = 0; g2 < 32; ++g2) {
-          const zf v = qpart[g2 * kPanel + tid];
-          q.re += v.re;
-          q.im += v.im;
+        acc.re = warp_sum(acc.re);
+        acc.im = warp_sum(acc.im);
+        if (lane == 0) {
+          q_s[j] = acc;
+          if (sp * kPanel + j < P.n)
+            qq_loc = fma((double)acc.re, (double)acc.re, fma((double)acc.im, (double)acc.im, qq_loc));
         }
-        q_s[tid] = q;
-        if (sp * kPanel + tid < P.n) qq_loc = fma((double)q.re, (double)q.re, fma((double)q.im, (double)q.im, qq_loc));
       }
       __syncthreads();
       // (b) t_i += sum_j A_ij q_j, one row per thread
@@ -217,17 +216,22 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
         }
       }
       __syncthreads();  // stage st is free
-      if (tid == 0 && sp + 2 < sp1) {
+      if (tid == 0 && sp + kStages < sp1) {
         mbar_expect_tx(&mbar[st], stage_tx);
         for (int bx = 0; bx < nbox; ++bx)
-          tma_load_2d(stage[st] + bx * kBoxRows * 128, &amap, (sp + 2) * 2 * kPanel, bx * kBoxRows, &mbar[st]);
+          tma_load_2d(stage[st] + bx * kBoxRows * 128, &amap, (sp + kStages) * 2 * kPanel, bx * kBoxRows,
+                      &mbar[st]);
       }
+      st = (st + 1 == kStages) ? 0 : st + 1;
     }
     if (!ok) break;
     if (tid < m) P.tpart[(int64_t)b * m + tid] = tacc;
-    if (wid == 0) {
-      const double qsum = warp_sum(qq_loc);
-      if (lane == 0) P.qq_part[b] = qsum;
+    if (lane == 0) s_qq[wid] = qq_loc;
+    __syncthreads();
+    if (tid == 0) {
+      double qsum = 0.0;
+      for (int w2 = 0; w2 < kCgThreads / 32; ++w2) qsum += s_qq[w2];
+      P.qq_part[b] = qsum;
     }
     if (!grid_sync(P.bar, G, P.limit_ns)) { ok = false; break; }
 
@@ -340,8 +344,8 @@ bool cg_fused_supported(int64_t m, int64_t n, int64_t lda, const void *A) {
 size_t cg_fused_smem(int64_t m) {
   const int nbox = (int)((m + kBoxRows - 1) / kBoxRows);
   const size_t rows_pad = (size_t)nbox * kBoxRows;
-  return 1024 + 2 * rows_pad * 128 + 2 * (size_t)m * sizeof(zd) + rows_pad * sizeof(zf) +
-         (32 * kPanel + kPanel) * sizeof(zf) + 2 * sizeof(uint64_t);
+  return 1024 + kStages * rows_pad * 128 + 2 * (size_t)m * sizeof(zd) + rows_pad * sizeof(zf) +
+         kPanel * sizeof(zf) + kStages * sizeof(uint64_t);
 }
 
 cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st) {

@@ -169,7 +169,6 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned int nblocks, 
       while (ld_acquire_u32(&b->gen) == g) {
         if (ld_volatile_i32(&b->err)) { ok = 0; break; }
         if (global_ns() - t0 > limit_ns) { atomicExch(&b->err, 1); ok = 0; break; }
-        __nanosleep(100);
       }
     }
     __threadfence();

@@ -55,12 +55,37 @@ constexpr int kQrCtasPerSm = 2;
 template <int NC, int K>
 __device__ __forceinline__ void qr_dots(const zd *__restrict__ yp, const zd *__restrict__ Y, const int *cols,
                                         int k, int l, double (&part)[K]) {
-  for (int r = k + 1 + threadIdx.x; r < l; r += blockDim.x) {
+  const zd *cp[NC > 0 ? NC : 1];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) cp[c] = Y + (int64_t)cols[c] * l;
+  int r = k + 1 + threadIdx.x;
+  const int stride = blockDim.x;
+  // several rows per thread in flight (the columns live in L2), fewer for many columns
+  constexpr int U = NC <= 2 ? 4 : (NC <= 4 ? 2 : 1);
+  for (; r + (U - 1) * stride < l; r += U * stride) {
+    zd a[U], y[U][NC > 0 ? NC : 1];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      a[u] = yp[r + u * stride];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) y[u][c] = cp[c][r + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      part[0] = fma(a[u].re, a[u].re, fma(a[u].im, a[u].im, part[0]));
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        part[1 + 2 * c] = fma(a[u].re, y[u][c].re, fma(a[u].im, y[u][c].im, part[1 + 2 * c]));
+        part[2 + 2 * c] = fma(a[u].re, y[u][c].im, fma(-a[u].im, y[u][c].re, part[2 + 2 * c]));
+      }
+    }
+  }
+  for (; r < l; r += stride) {
     const zd a = yp[r];
     part[0] = fma(a.re, a.re, fma(a.im, a.im, part[0]));
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      const zd y = Y[r + (int64_t)cols[c] * l];
+      const zd y = cp[c][r];
       part[1 + 2 * c] = fma(a.re, y.re, fma(a.im, y.im, part[1 + 2 * c]));
       part[2 + 2 * c] = fma(a.re, y.im, fma(-a.im, y.re, part[2 + 2 * c]));
     }
@@ -71,17 +96,42 @@ template <int NC>
 __device__ __forceinline__ void qr_update(const zd *__restrict__ yp, zd *__restrict__ Y, const int *cols,
                                           const zd *g, int k, int l) {
   zd gg[NC > 0 ? NC : 1];
+  zd *cp[NC > 0 ? NC : 1];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) gg[c] = g[c];
-  for (int r = k + 1 + threadIdx.x; r < l; r += blockDim.x) {
+  for (int c = 0; c < NC; ++c) {
+    gg[c] = g[c];
+    cp[c] = Y + (int64_t)cols[c] * l;
+  }
+  int r = k + 1 + threadIdx.x;
+  const int stride = blockDim.x;
+  constexpr int U = NC <= 2 ? 4 : (NC <= 4 ? 2 : 1);
+  for (; r + (U - 1) * stride < l; r += U * stride) {
+    zd a[U], v[U][NC > 0 ? NC : 1];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      a[u] = yp[r + u * stride];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) v[u][c] = cp[c][r + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        zd t = v[u][c];
+        t.re = fma(-gg[c].re, a[u].re, fma(gg[c].im, a[u].im, t.re));
+        t.im = fma(-gg[c].re, a[u].im, fma(-gg[c].im, a[u].re, t.im));
+        cp[c][r + u * stride] = t;
+      }
+    }
+  }
+  for (; r < l; r += stride) {
     const zd a = yp[r];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      zd *y = Y + r + (int64_t)cols[c] * l;
-      zd v = *y;
+      zd v = cp[c][r];
       v.re = fma(-gg[c].re, a.re, fma(gg[c].im, a.im, v.re));
       v.im = fma(-gg[c].re, a.im, fma(-gg[c].im, a.re, v.im));
-      *y = v;
+      cp[c][r] = v;
     }
   }
 }
@@ -116,7 +166,6 @@ qrp_bal_kernel(zd *__restrict__ Y, int l, int m, double *__restrict__ vnA, doubl
   __shared__ zd s_g[MAXC];
   __shared__ int s_rec[MAXC];
   __shared__ int s_nact, s_nrec;
-  __shared__ zd s_tau, s_scale;
 
   const int G = gridDim.x, b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -186,8 +235,11 @@ qrp_bal_kernel(zd *__restrict__ Y, int l, int m, double *__restrict__ vnA, doubl
 #undef MN_DOTS
     block_sum_k<double, K>(part, red_scratch, red_out);
 
-    // 3. reflector H = I - tau v v^*, identical in every CTA (LAPACK zlarfg convention)
-    if (tid == 0) {
+    // 3. reflector H = I - tau v v^*, identical in every CTA (LAPACK zlarfg convention),
+    //    computed by each lane that owns a column (and lane 0 of CTA 0 for beta), then that
+    //    column's factor and partial-norm downdate
+    if (tid == 0) s_nrec = 0;
+    if (tid < (nact > 0 ? nact : 1)) {
       const zd alpha = yp[k];
       const double xn2 = red_out[0];
       zd tau = {0.0, 0.0}, scale = {0.0, 0.0};
@@ -203,38 +255,32 @@ qrp_bal_kernel(zd *__restrict__ Y, int l, int m, double *__restrict__ vnA, doubl
         const double iden = 1.0 / (dr * dr + di * di);
         scale = {dr * iden, -di * iden};
       }
-      if (b == 0) beta[k] = bt;
-      s_tau = tau;
-      s_scale = scale;
-      s_nrec = 0;
-    }
-    __syncthreads();
-    // factors and norm downdates of the own columns, one lane per column
-    if (tid < nact) {
-      const int c = tid;
-      const int j = s_col[c];
-      zd *yj = Y + (int64_t)j * l;
-      const zd tau = s_tau, scale = s_scale;
-      const zd d = {red_out[1 + 2 * c], red_out[2 + 2 * c]};
-      zd w = yj[k];
-      macc(w, scale, d);                      // w = y_k + conj(scale) d
-      const zd f = conjg(tau) * w;            // H^* = I - conj(tau) v v^*
-      s_g[c] = f * scale;
-      const zd rk = yj[k] - f;
-      yj[k] = rk;
-      // LAPACK zlaqp2 downdate: vn1 *= sqrt(1 - (|r_k|/vn1)^2) unless that loses half the digits
-      const double v1 = vn_cur[j];
-      double nv = v1;
-      if (v1 != 0.0) {
-        const double iv = 1.0 / v1;
-        const double t = sqrt(abs2(rk)) * iv;
-        double temp = 1.0 - t * t;
-        temp = temp < 0.0 ? 0.0 : temp;
-        const double ratio = v1 / vn2[j];
-        if (temp * ratio * ratio <= tol3z) s_rec[atomicAdd(&s_nrec, 1)] = c;
-        else nv = v1 * sqrt(temp);
+      if (b == 0 && tid == 0) beta[k] = bt;
+      if (tid < nact) {
+        const int c = tid;
+        const int j = s_col[c];
+        zd *yj = Y + (int64_t)j * l;
+        const zd d = {red_out[1 + 2 * c], red_out[2 + 2 * c]};
+        zd w = yj[k];
+        macc(w, scale, d);                      // w = y_k + conj(scale) d
+        const zd f = conjg(tau) * w;            // H^* = I - conj(tau) v v^*
+        s_g[c] = f * scale;
+        const zd rk = yj[k] - f;
+        yj[k] = rk;
+        // LAPACK zlaqp2 downdate: vn1 *= sqrt(1 - (|r_k|/vn1)^2) unless that loses half the digits
+        const double v1 = vn_cur[j];
+        double nv = v1;
+        if (v1 != 0.0) {
+          const double iv = 1.0 / v1;
+          const double t = sqrt(abs2(rk)) * iv;
+          double temp = 1.0 - t * t;
+          temp = temp < 0.0 ? 0.0 : temp;
+          const double ratio = v1 / vn2[j];
+          if (temp * ratio * ratio <= tol3z) s_rec[atomicAdd(&s_nrec, 1)] = c;
+          else nv = v1 * sqrt(temp);
+        }
+        vn_nxt[j] = nv;
       }
-      vn_nxt[j] = nv;
     }
     __syncthreads();
 

@@ -12,12 +12,12 @@
 //          their row's largest are rounded at 2^(E_i - 62), a relative
 //          perturbation of A below 2^-63.
 //   y      y' = y 2^(E_i) as one 128-bit fixed-point vector, |y'| < 2^Wy,
-//          Wy = 126 - ceil(log2 m); built from the double-double y exactly up
+//          Wy = 124 - ceil(log2 m); built from the double-double y exactly up
 //          to one unit.
 //   x      accumulated exactly in __int128 (products taken as
 //          floor(a y' / 2^64), error < 1 unit each), returned as a
 //          double-double vector, then re-scaled into 128-bit fixed point,
-//          |x'| < 2^Wx, Wx = 126 - ceil(log2 n), for the forward product.
+//          |x'| < 2^Wx, Wx = 124 - ceil(log2 n), for the forward product.
 //   r      sum_j a_ij x'_j exact per CTA and across CTAs, converted to
 //          double-double, r = b - t rounded to FP64.
 // The bounds on |a|, |y'|, |x'| keep every partial and total sum below 2^127.
@@ -151,27 +151,51 @@ fix_y_kernel(int m, const zd *__restrict__ yh, const zd *__restrict__ yl, const 
 
 // ---- x = A^* y' exactly; output as double-double, max exponent to Fx -------------
 constexpr int kXadjThreads = 128;
+constexpr int kXadjUnroll = 8;
 
+// Complex products use Gauss's three multiplications, exact in integers up to
+// the floor of each product:  conj(a) y = (t1 + t2) + i (t3 - t1 + t2) with
+// t1 = a_r y_r, t2 = a_i y_i, t3 = (a_r - a_i)(y_r + y_i).
 __global__ void __launch_bounds__(kXadjThreads)
 xadj_kernel(const fixc *__restrict__ afix, int64_t rows, int64_t cols, const i128c *__restrict__ yfix,
             const int *__restrict__ Fy, int Wy, zd *__restrict__ xh, zd *__restrict__ xl, int *__restrict__ Fx) {
   __shared__ i128c sy[kXadjThreads];
+  __shared__ i128 ss[kXadjThreads];
   __shared__ int red[kXadjThreads / 32];
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   i128 are = 0, aim = 0;
   for (int64_t i0 = 0; i0 < rows; i0 += kXadjThreads) {
     __syncthreads();
-    if (i0 + threadIdx.x < rows) sy[threadIdx.x] = yfix[i0 + threadIdx.x];
+    if (i0 + threadIdx.x < rows) {
+      const i128c y = yfix[i0 + threadIdx.x];
+      sy[threadIdx.x] = y;
+      ss[threadIdx.x] = y.re + y.im;
+    }
     __syncthreads();
     if (j < cols) {
-      const int64_t ie = (i0 + kXadjThreads < rows ? i0 + kXadjThreads : rows) - i0;
+      const int ie = (int)((i0 + kXadjThreads < rows ? i0 + kXadjThreads : rows) - i0);
       const fixc *a = afix + i0 * cols + j;
-      for (int64_t u = 0; u < ie; ++u) {
-        const fixc av = a[u * cols];
+      int u = 0;
+      for (; u + kXadjUnroll <= ie; u += kXadjUnroll) {
+        fixc av[kXadjUnroll];
+#pragma unroll
+        for (int q = 0; q < kXadjUnroll; ++q) av[q] = a[(int64_t)(u + q) * cols];
+#pragma unroll
+        for (int q = 0; q < kXadjUnroll; ++q) {
+          const i128c y = sy[u + q];
+          const i128 t1 = mulP(av[q].re, y.re), t2 = mulP(av[q].im, y.im);
+          const i128 t3 = mulP(av[q].re - av[q].im, ss[u + q]);
+          are += t1 + t2;
+          aim += t3 - t1 + t2;
+        }
+      }
+      for (; u < ie; ++u) {
+        const fixc av = a[(int64_t)u * cols];
         const i128c y = sy[u];
-        // conj(a) y = (ar yr + ai yi) + i (ar yi - ai yr)
-        are += mulP(av.re, y.re) + mulP(av.im, y.im);
-        aim += mulP(av.re, y.im) - mulP(av.im, y.re);
+        const i128 t1 = mulP(av.re, y.re), t2 = mulP(av.im, y.im);
+        const i128 t3 = mulP(av.re - av.im, ss[u]);
+        are += t1 + t2;
+        aim += t3 - t1 + t2;
       }
     }
   }
@@ -219,18 +243,22 @@ xfwd_kernel(const fixc *__restrict__ afix, int64_t rows, int64_t cols, const zd 
   i128 acc_re[kXfwdRows], acc_im[kXfwdRows];
 #pragma unroll
   for (int r = 0; r < kXfwdRows; ++r) { acc_re[r] = 0; acc_im[r] = 0; }
+  const int nr = rows - i0 < kXfwdRows ? (int)(rows - i0) : kXfwdRows;
   for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
     const zd h = xh[c], l = xl[c];
+    fixc av[kXfwdRows];
+#pragma unroll
+    for (int r = 0; r < kXfwdRows; ++r) av[r] = r < nr ? afix[(i0 + r) * cols + c] : fixc{0, 0};
     const i128 xr = d2fix(h.re, k) + d2fix(l.re, k);
     const i128 xi = d2fix(h.im, k) + d2fix(l.im, k);
+    const i128 xs = xr + xi;
 #pragma unroll
     for (int r = 0; r < kXfwdRows; ++r) {
-      if (i0 + r < rows) {
-        const fixc av = afix[(i0 + r) * cols + c];
-        // a x = (ar xr - ai xi) + i (ar xi + ai xr)
-        acc_re[r] += mulP(av.re, xr) - mulP(av.im, xi);
-        acc_im[r] += mulP(av.re, xi) + mulP(av.im, xr);
-      }
+      // a x = (t1 - t2) + i (t3 - t1 - t2), t1 = ar xr, t2 = ai xi, t3 = (ar + ai)(xr + xi)
+      const i128 t1 = mulP(av[r].re, xr), t2 = mulP(av[r].im, xi);
+      const i128 t3 = mulP(av[r].re + av[r].im, xs);
+      acc_re[r] += t1 - t2;
+      acc_im[r] += t3 - t1 - t2;
     }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -292,8 +320,8 @@ static int ceil_log2(int64_t v) {
   return k;
 }
 
-int xprod_wy(int64_t m) { return 126 - ceil_log2(m) - 1; }
-int xprod_wx(int64_t n) { return 126 - ceil_log2(n) - 1; }
+int xprod_wy(int64_t m) { return 126 - ceil_log2(m) - 2; }
+int xprod_wx(int64_t n) { return 126 - ceil_log2(n) - 2; }
 
 cudaError_t launch_fix_prep(const void *A, int64_t lda, bool c64, int64_t rows, int64_t cols, void *afix,
                             int32_t *E, void *A32, cudaStream_t st) {
