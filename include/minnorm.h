@@ -225,7 +225,7 @@ minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *lau
  * (used as workspace). Writes R (device, m x m complex128, column-major, upper
  * triangular, real diagonal) and the pivots (device, m int64: column k of R
  * belongs to column piv[k] of Y). The kernel's scratch lives in one fixed
- * device array of 160 KiB inside the library, held by every GPU that loads
+ * device array of 192 KiB inside the library, held by every GPU that loads
  * the library until the process exits; m may be at most 4096, larger m
  * returns MINNORM_ENOTSUP. Nothing is allocated: no cudaMalloc or cudaFree is
  * called. The first call on a device looks up that array's device address
@@ -234,7 +234,7 @@ minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *lau
  * host threads) race and must be serialized by the caller. Work is enqueued
  * on `stream` (cudaStream_t as void*); the call synchronizes it to read the
  * barrier's status. Errors: EINVAL (null pointers, sizes), ENOTSUP (m > 4096),
- * ETIMEOUT (a bounded grid-barrier wait expired), ECUDA. */
+ * ETIMEOUT (a bounded wait between the kernel's steps expired), ECUDA. */
 minnorm_status minnorm_qr_noalloc(void *Y, int64_t ldy, int64_t l, int64_t m, void *R_out, void *piv_out,
                                   void *stream);
 

@@ -53,6 +53,18 @@ __device__ __forceinline__ void macc(cx<R> &acc, cx<R> a, cx<R> b) {
 template <typename D, typename S>
 __device__ __forceinline__ cx<D> cvt(cx<S> a) { return {(D)a.re, (D)a.im}; }
 
+// loads and stores through L2 only (ld/st.global.cg): for data other CTAs
+// rewrite while the kernel runs
+template <typename T>
+__device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+template <typename T>
+__device__ __forceinline__ void stcg(T *p, T v) { __stcg(p, v); }
+__device__ __forceinline__ zd ldcg(const zd *p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void stcg(zd *p, zd v) { __stcg(reinterpret_cast<double2 *>(p), make_double2(v.re, v.im)); }
+
 // ---- reductions ---------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

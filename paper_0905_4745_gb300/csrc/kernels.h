@@ -58,11 +58,12 @@ struct QrArgs {
   double *beta;           // m: real diagonal of R
   int32_t *piv;           // m
   void *R;                // m x m complex128 column-major (out)
-  GridBarrier *bar;
+  void *mail;             // qr_mail_bytes() of exchange words (cleared by launch_qrp)
   int *err;
   uint64_t limit_ns;
 };
 cudaError_t launch_qrp(const QrArgs &a, cudaStream_t st);
+size_t qr_mail_bytes();
 
 // Wp = P R^{-1} (row-major m x m) and WpH = Wp^* (row-major)
 cudaError_t launch_prinv(const void *R, const int32_t *piv, int m, void *Wp, void *WpH, cudaStream_t st);

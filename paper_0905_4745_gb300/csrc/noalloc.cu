@@ -6,8 +6,8 @@
 // start-up that must not shrink behind its back), or they run on a
 // latency-critical path where cudaMalloc/cudaFree may synchronize the device.
 // minnorm_qr_noalloc gives them the same pivoted QR kernel the plans use, with
-// its scratch (partial norms, the diagonal of R, the pivots, the grid-barrier
-// words) taken from one file-scope device array instead of a plan. The caller
+// its scratch (partial norms, the diagonal of R, the pivots, the words the
+// CTAs exchange between steps) taken from one file-scope device array instead of a plan. The caller
 // still passes the matrix and the output buffers.
 //
 // The array below is part of the library's module: every GPU that loads the
@@ -25,9 +25,11 @@ namespace mn {
 
 // Largest m the scratch covers; the scratch holds, for m columns:
 // 2m + m + m doubles (partial norms, reference norms, diagonal of R),
-// m int32 pivots, the grid barrier and the error word.
+// m int32 pivots, the exchange words of the QR grid and the error word.
 constexpr int64_t kNoAllocMaxM = 4096;
-constexpr size_t kNoAllocScratchBytes = 160 * 1024;
+constexpr size_t kNoAllocScratchBytes = 192 * 1024;
+// exchange words of the QR kernel (flags and the posted candidates of up to 320 CTAs)
+constexpr size_t kNoAllocMailBytes = 24 * 1024;
 
 static __device__ __align__(256) unsigned char g_qr_scratch[kNoAllocScratchBytes];
 
@@ -73,20 +75,20 @@ extern "C" minnorm_status minnorm_qr_noalloc(void *Y, int64_t ldy, int64_t l, in
   unsigned char *base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return MINNORM_ECUDA;
   cudaStream_t st = (cudaStream_t)stream;
-  // carve the scratch: [vn1: 2m][vn2: m][beta: m] doubles, then pivots, barrier, error word
+  // carve the scratch: [vn1: 2m][vn2: m][beta: m] doubles, then pivots, the exchange words, the error word
   double *vn1 = reinterpret_cast<double *>(base);
   double *vn2 = vn1 + 2 * kNoAllocMaxM;
   double *beta = vn2 + kNoAllocMaxM;
   int32_t *piv = reinterpret_cast<int32_t *>(beta + kNoAllocMaxM);
-  GridBarrier *bar = reinterpret_cast<GridBarrier *>(base + 4 * kNoAllocMaxM * sizeof(double) +
-                                                     kNoAllocMaxM * sizeof(int32_t));
-  int *err = reinterpret_cast<int *>(bar + 1);
-  static_assert(4 * kNoAllocMaxM * sizeof(double) + kNoAllocMaxM * sizeof(int32_t) + sizeof(GridBarrier) +
+  unsigned char *mail = base + 4 * kNoAllocMaxM * sizeof(double) + kNoAllocMaxM * sizeof(int32_t);
+  int *err = reinterpret_cast<int *>(mail + kNoAllocMailBytes);
+  static_assert(4 * kNoAllocMaxM * sizeof(double) + kNoAllocMaxM * sizeof(int32_t) + kNoAllocMailBytes +
                         sizeof(int) <= kNoAllocScratchBytes,
                 "scratch too small");
-  // the barrier counters and the error word must start at zero; the previous
-  // call's values are still there
-  if (cudaMemsetAsync(bar, 0, sizeof(GridBarrier) + sizeof(int), st) != cudaSuccess) return MINNORM_ECUDA;
+  if (qr_mail_bytes() > kNoAllocMailBytes) return MINNORM_ENOTSUP;
+  // the error word must start at zero (launch_qrp clears the exchange flags itself);
+  // the previous call's value is still there
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return MINNORM_ECUDA;
   QrArgs q{};
   q.Y = Y;
   q.l = (int)l;
@@ -96,7 +98,7 @@ extern "C" minnorm_status minnorm_qr_noalloc(void *Y, int64_t ldy, int64_t l, in
   q.beta = beta;
   q.piv = piv;
   q.R = R_out;
-  q.bar = bar;
+  q.mail = mail;
   q.err = err;
   q.limit_ns = 2000000000ULL;
   if (launch_qrp(q, st) != cudaSuccess) return MINNORM_ECUDA;

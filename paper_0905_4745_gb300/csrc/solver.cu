@@ -79,6 +79,7 @@ struct minnorm_plan_s {
   int32_t *d_piv = nullptr;
   zd *d_R = nullptr, *d_Wp = nullptr, *d_WpH = nullptr;
   GridBarrier *d_bar = nullptr;
+  void *d_qrmail = nullptr;
   int *d_err = nullptr;
   double rdiag_max = 0, rdiag_min = 0;
   // products
@@ -340,6 +341,7 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   ALLOC(plan->d_Wp, sizeof(zd) * (size_t)m * m);
   ALLOC(plan->d_WpH, sizeof(zd) * (size_t)m * m);
   ALLOC(plan->d_bar, sizeof(GridBarrier));
+  ALLOC(plan->d_qrmail, qr_mail_bytes());
   ALLOC(plan->d_err, sizeof(int));
   if (plan->fp32 && dtype == MINNORM_C128) ALLOC(plan->d_A32, sizeof(zf) * (size_t)m * n);
   // products: g_cg for the CG passes, g_hp for FP64 / double-double passes on the stored A
@@ -427,10 +429,9 @@ minnorm_status sketch_impl(minnorm_plan_t plan, const void *A, int64_t lda) {
   if (timing) CK(cudaEventRecord(e1, st));
   {
     Timed tm(plan, 3);
-    CK(cudaMemsetAsync(plan->d_bar, 0, sizeof(GridBarrier), st));
     CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
     QrArgs q{plan->d_Y, (int)l, (int)m, plan->d_vn1, plan->d_vn2, plan->d_beta, plan->d_piv, plan->d_R,
-             plan->d_bar, plan->d_err, kBarrierLimitNs};
+             plan->d_qrmail, plan->d_err, kBarrierLimitNs};
     CK(launch_qrp(q, st));
     CK(launch_prinv(plan->d_R, plan->d_piv, (int)m, plan->d_Wp, plan->d_WpH, st));
   }
