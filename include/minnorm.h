@@ -148,6 +148,22 @@ minnorm_status minnorm_solve(minnorm_plan_t plan, const void *A, int64_t lda, co
                              double eps, void *x, minnorm_info *info);
 
 /*
+ * Steps 3-5 for nrhs right-hand sides sharing the A, T and R of the last
+ * minnorm_sketch (the block right-hand-side case: the sketch and the pivoted
+ * QR, the costly part of a solve, are paid once for all columns).
+ *   B:    device, m x nrhs complex128, column-major: column j at B + j*ldb.
+ *   X:    device, n x nrhs complex128, column-major: column j at X + j*ldx.
+ *   ldb >= m, ldx >= n, nrhs >= 1; eps as for minnorm_solve.
+ *   infos: host array of nrhs minnorm_info, or NULL.
+ * Every column gets the guarantee of minnorm_solve. Returns MINNORM_OK when
+ * every column did; otherwise the status of the first column that did not
+ * (ENOCONV / EFLOOR columns are still written and the later columns still
+ * solved; EINVAL, ESTATE and ECUDA stop at once).
+ */
+minnorm_status minnorm_solve_many(minnorm_plan_t plan, const void *A, int64_t lda, const void *B, int64_t ldb,
+                                  int64_t nrhs, double eps, void *X, int64_t ldx, minnorm_info *infos);
+
+/*
  * minnorm_sketch + minnorm_solve on HOST buffers: copies A (m x n, lda) and b
  * to the device, solves, and copies x (n complex128) back. The device copy of
  * A and b is plan-owned and allocated on the first call (and again only if

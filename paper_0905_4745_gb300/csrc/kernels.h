@@ -30,11 +30,12 @@ struct ChainArgs {
 cudaError_t launch_chain(const ChainArgs &a, cudaStream_t st);
 
 struct FftArgs {
-  const void *src;        // rows x n (compute precision), rows of ld
+  const void *src;        // rows of the input (compute precision), row stride ld
   int64_t ld;
-  void *work;             // rows x n scratch for the four-step path
-  const void *tw;         // n twiddles e^{-2 pi i k/n}
-  int logn, logN1;        // logN1 = 0: single-pass row FFT
+  void *work;             // rows x L scratch for the four-step path, row stride ldw
+  int64_t ldw;
+  const void *tw;         // L twiddles e^{-2 pi i k/L}
+  int logn, logN1;        // L = 2^logn; logN1 = 0: single-pass row FFT
   int tj, tk;             // tile widths of pass A / B
   const int32_t *samp_off, *samp_t, *samp_loc;
   int l, rows;
@@ -42,6 +43,13 @@ struct FftArgs {
   int64_t ldy;
   int row_offset;
   bool real_fp32;
+  // Bluestein stages (n not a power of two; see params.h):
+  const void *chirp;      // if set: the input is x_j chirp_j for j < nin and 0 for nin <= j < L
+  int nin;
+  void *full;             // if set: store conj(X_k bh_k) for all k < L (row stride ldf), no sampling
+  const void *bh;
+  int64_t ldf;
+  const double *fac;      // if set: sampled outputs are conj(X) * fac[t] (complex128) instead of X / sqrt(L)
 };
 cudaError_t launch_fft(const FftArgs &a, cudaStream_t st);
 cudaError_t launch_to_c64(const void *A, int64_t lda, void *B, int64_t ldb, int64_t rows, int64_t cols,

@@ -157,4 +157,46 @@ std::vector<int32_t> chain_halos(const std::vector<double> &theta, int64_t n, in
   return h;
 }
 
+// in-place radix-2 FFT, forward (e^{-2 pi i jk/L}), natural order in and out
+static void host_fft_pow2(std::vector<std::complex<double>> &a) {
+  const int64_t L = (int64_t)a.size();
+  for (int64_t i = 1, j = 0; i < L; ++i) {
+    int64_t bit = L >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int64_t h = 1; h < L; h <<= 1) {
+    for (int64_t k = 0; k < h; ++k) {
+      const double ang = -two_pi * (double)k / (double)(2 * h);
+      const std::complex<double> w(std::cos(ang), std::sin(ang));
+      for (int64_t s0 = 0; s0 < L; s0 += 2 * h) {
+        const std::complex<double> u = a[s0 + k], v = a[s0 + k + h] * w;
+        a[s0 + k] = u + v;
+        a[s0 + k + h] = u - v;
+      }
+    }
+  }
+}
+
+void bluestein_tables(int64_t n, int64_t L, std::vector<std::complex<double>> &chirp,
+                      std::vector<std::complex<double>> &bh) {
+  const double pi = 3.14159265358979323846264338327950;
+  chirp.resize(n);
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t q = (int64_t)(((uint64_t)j * (uint64_t)j) % (uint64_t)(2 * n));  // j < 2^31
+    const double ang = -pi * (double)q / (double)n;
+    chirp[j] = std::complex<double>(std::cos(ang), std::sin(ang));
+  }
+  std::vector<std::complex<double>> b(L, std::complex<double>(0.0, 0.0));
+  for (int64_t t = 0; t < n; ++t) {
+    b[t] = std::conj(chirp[t]);
+    if (t > 0) b[L - t] = std::conj(chirp[t]);
+  }
+  host_fft_pow2(b);
+  bh.resize(L);
+  for (int64_t k = 0; k < L; ++k) bh[k] = b[k] / (double)L;
+}
+
 }  // namespace mn

@@ -31,4 +31,13 @@ bool validate_srft_params(const SrftParams &P);
 std::vector<int32_t> chain_halos(const std::vector<double> &theta, int64_t n, int seg, double tol,
                                  int *hmax);
 
+// Tables of the DFT of a length n that is not a power of two, computed by
+// Bluestein's identity j k = (j^2 + k^2 - (k - j)^2) / 2 as a circular
+// convolution of power-of-two length L >= 2n - 1:
+//   X_k = c_k sum_j (x_j c_j) conj(c_{k-j}),   c_j = exp(-pi i j^2 / n).
+// chirp: c_j for j < n; bh: FFT_L(b) / L with b_t = conj(c_t) for |t| < n
+// (indices mod L) and 0 elsewhere. Both in FP64 (the angle uses j^2 mod 2n).
+void bluestein_tables(int64_t n, int64_t L, std::vector<std::complex<double>> &chirp,
+                      std::vector<std::complex<double>> &bh);
+
 }  // namespace mn

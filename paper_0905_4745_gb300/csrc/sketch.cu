@@ -9,7 +9,12 @@
 //   fft kernels           the unitary DFT F of Eq. (DFT) by radix-2 FFTs in
 //                         shared memory (one pass for n <= 4096/8192, otherwise
 //                         the four-step factorisation n = N1 N2), with the row
-//                         sample S applied while storing into Y
+//                         sample S applied while storing into Y. A length n
+//                         that is not a power of two takes Bluestein's chirp
+//                         convolution: two FFTs of length L >= 2n - 1, the
+//                         first with the chirp applied on load and conj(X bh)
+//                         stored in full, the second sampled with the chirp and
+//                         1/sqrt(n) folded into a per-row factor
 //
 // The chain Theta = G_0 G_1 ... G_{n-2} (G_{n-2} acting first) is the reverse
 // affine recurrence
@@ -171,24 +176,49 @@ __device__ __forceinline__ void smem_fft(cx<R> *data, int B, int logL, const cx<
   }
 }
 
-// Whole-row FFT (n <= smem capacity) + sample: Y[t, row] = X[s_t] / sqrt(n).
+// input element j of a row: plain, or (Bluestein) x_j c_j zero-padded past nin
+template <typename R>
+__device__ __forceinline__ cx<R> fft_in(const cx<R> *__restrict__ s, int64_t j, const cx<R> *__restrict__ chirp,
+                                        int nin) {
+  if (!chirp) return s[j];
+  return j < nin ? s[j] * chirp[j] : cx<R>{R(0), R(0)};
+}
+
+// sampled output t: X / sqrt(L), or (Bluestein) conj(X) * fac[t]
+template <typename R>
+__device__ __forceinline__ zd fft_out(cx<R> v, int t, const double *__restrict__ fac, double scale) {
+  if (!fac) return {double(v.re) * scale, double(v.im) * scale};
+  const double fr = fac[2 * t], fi = fac[2 * t + 1];
+  const double vr = double(v.re), vi = -double(v.im);
+  return {vr * fr - vi * fi, vr * fi + vi * fr};
+}
+
+// Whole-row FFT (L <= smem capacity) + sample: Y[t, row] = X[s_t] / sqrt(L),
+// or the Bluestein stages (see FftArgs).
 template <typename R>
 __global__ void __launch_bounds__(256)
 fft_row_kernel(const cx<R> *__restrict__ src, int64_t ld_src, int logn, const cx<R> *__restrict__ tw,
                const int32_t *__restrict__ samp_t, const int32_t *__restrict__ samp_loc, int l,
-               zd *__restrict__ Y, int64_t ldy, int row_offset, double scale) {
+               zd *__restrict__ Y, int64_t ldy, int row_offset, double scale, const cx<R> *__restrict__ chirp,
+               int nin, cx<R> *__restrict__ full, const cx<R> *__restrict__ bh, int64_t ldf,
+               const double *__restrict__ fac) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R> *data = reinterpret_cast<cx<R> *>(smem_raw);
   const int n = 1 << logn;
   const int64_t row = blockIdx.y;
   const cx<R> *s = src + row * ld_src;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) data[bitrev(j, logn)] = s[j];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) data[bitrev(j, logn)] = fft_in(s, j, chirp, nin);
   __syncthreads();
   smem_fft<R>(data, 1, logn, tw, logn);
+  if (full) {
+    cx<R> *f = full + row * ldf;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) f[k] = conjg(data[k] * bh[k]);
+    return;
+  }
   zd *y = Y + (row + row_offset) * ldy;
   for (int e = threadIdx.x; e < l; e += blockDim.x) {
-    const cx<R> v = data[samp_loc[e]];
-    y[samp_t[e]] = {double(v.re) * scale, double(v.im) * scale};
+    const int t = samp_t[e];
+    y[t] = fft_out(data[samp_loc[e]], t, fac, scale);
   }
 }
 
@@ -196,8 +226,8 @@ fft_row_kernel(const cx<R> *__restrict__ src, int64_t ld_src, int logn, const cx
 // v[j1 + N1 j2], times e^{-2 pi i j1 k2 / n}, stored at W[k2 N1 + j1].
 template <typename R>
 __global__ void __launch_bounds__(256)
-fft_pass_a_kernel(const cx<R> *__restrict__ src, int64_t ld, cx<R> *__restrict__ W, int logn, int logN1,
-                  int tj, const cx<R> *__restrict__ tw) {
+fft_pass_a_kernel(const cx<R> *__restrict__ src, int64_t ld, cx<R> *__restrict__ W, int64_t ldw, int logn,
+                  int logN1, int tj, const cx<R> *__restrict__ tw, const cx<R> *__restrict__ chirp, int nin) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R> *data = reinterpret_cast<cx<R> *>(smem_raw);
   const int n = 1 << logn, N1 = 1 << logN1, logN2 = logn - logN1, N2 = 1 << logN2;
@@ -207,11 +237,11 @@ fft_pass_a_kernel(const cx<R> *__restrict__ src, int64_t ld, cx<R> *__restrict__
   const int total = tj * N2;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int jj = e % tj, j2 = e / tj;
-    data[jj * N2 + bitrev(j2, logN2)] = s[(j1_0 + jj) + (int64_t)N1 * j2];
+    data[jj * N2 + bitrev(j2, logN2)] = fft_in(s, (j1_0 + jj) + (int64_t)N1 * j2, chirp, nin);
   }
   __syncthreads();
   smem_fft<R>(data, tj, logN2, tw, logn);
-  cx<R> *w = W + row * ld;
+  cx<R> *w = W + row * ldw;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int jj = e % tj, k2 = e / tj;
     const int j1 = j1_0 + jj;
@@ -224,16 +254,17 @@ fft_pass_a_kernel(const cx<R> *__restrict__ src, int64_t ld, cx<R> *__restrict__
 // W[k2 N1 + j1] gives X[N2 k1 + k2]; the sampled ones go to Y.
 template <typename R>
 __global__ void __launch_bounds__(256)
-fft_pass_b_kernel(const cx<R> *__restrict__ W, int64_t ld, int logn, int logN1, int tk,
+fft_pass_b_kernel(const cx<R> *__restrict__ W, int64_t ldw, int logn, int logN1, int tk,
                   const cx<R> *__restrict__ tw, const int32_t *__restrict__ samp_off,
                   const int32_t *__restrict__ samp_t, const int32_t *__restrict__ samp_loc,
-                  zd *__restrict__ Y, int64_t ldy, int row_offset, double scale) {
+                  zd *__restrict__ Y, int64_t ldy, int row_offset, double scale, cx<R> *__restrict__ full,
+                  const cx<R> *__restrict__ bh, int64_t ldf, const double *__restrict__ fac) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R> *data = reinterpret_cast<cx<R> *>(smem_raw);
   const int N1 = 1 << logN1;
   const int k2_0 = blockIdx.x * tk;
   const int64_t row = blockIdx.y;
-  const cx<R> *w = W + row * ld + (int64_t)k2_0 * N1;
+  const cx<R> *w = W + row * ldw + (int64_t)k2_0 * N1;
   const int total = tk * N1;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int kk = e >> logN1, j1 = e & (N1 - 1);
@@ -241,11 +272,22 @@ fft_pass_b_kernel(const cx<R> *__restrict__ W, int64_t ld, int logn, int logN1, 
   }
   __syncthreads();
   smem_fft<R>(data, tk, logN1, tw, logn);
+  if (full) {
+    // X[N2 k1 + k2] for k2 = k2_0 + kk sits at data[kk N1 + k1]; runs of tk consecutive outputs
+    const int N2 = 1 << (logn - logN1);
+    cx<R> *f = full + row * ldf;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int k1 = e / tk, kk = e - k1 * tk;
+      const int64_t K = (int64_t)N2 * k1 + k2_0 + kk;
+      f[K] = conjg(data[kk * N1 + k1] * bh[K]);
+    }
+    return;
+  }
   zd *y = Y + (row + row_offset) * ldy;
   const int b0 = samp_off[blockIdx.x], b1 = samp_off[blockIdx.x + 1];
   for (int e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
-    const cx<R> v = data[samp_loc[e]];
-    y[samp_t[e]] = {double(v.re) * scale, double(v.im) * scale};
+    const int t = samp_t[e];
+    y[t] = fft_out(data[samp_loc[e]], t, fac, scale);
   }
 }
 
@@ -312,7 +354,8 @@ static cudaError_t launch_fft_t(const FftArgs &a, cudaStream_t st) {
     note_launch();
     fft_row_kernel<R><<<dim3(1, a.rows), 256, smem, st>>>(
         (const cx<R> *)a.src, a.ld, a.logn, (const cx<R> *)a.tw, a.samp_t, a.samp_loc, a.l, (zd *)a.Y,
-        a.ldy, a.row_offset, scale);
+        a.ldy, a.row_offset, scale, (const cx<R> *)a.chirp, a.nin, (cx<R> *)a.full, (const cx<R> *)a.bh, a.ldf,
+        a.fac);
     return cudaGetLastError();
   }
   const int N1 = 1 << a.logN1, N2 = 1 << (a.logn - a.logN1);
@@ -324,13 +367,14 @@ static cudaError_t launch_fft_t(const FftArgs &a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   note_launch();
   fft_pass_a_kernel<R><<<dim3(N1 / a.tj, a.rows), 256, smemA, st>>>(
-      (const cx<R> *)a.src, a.ld, (cx<R> *)a.work, a.logn, a.logN1, a.tj, (const cx<R> *)a.tw);
+      (const cx<R> *)a.src, a.ld, (cx<R> *)a.work, a.ldw, a.logn, a.logN1, a.tj, (const cx<R> *)a.tw,
+      (const cx<R> *)a.chirp, a.nin);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   note_launch();
   fft_pass_b_kernel<R><<<dim3(N2 / a.tk, a.rows), 256, smemB, st>>>(
-      (const cx<R> *)a.work, a.ld, a.logn, a.logN1, a.tk, (const cx<R> *)a.tw, a.samp_off, a.samp_t,
-      a.samp_loc, (zd *)a.Y, a.ldy, a.row_offset, scale);
+      (const cx<R> *)a.work, a.ldw, a.logn, a.logN1, a.tk, (const cx<R> *)a.tw, a.samp_off, a.samp_t,
+      a.samp_loc, (zd *)a.Y, a.ldy, a.row_offset, scale, (cx<R> *)a.full, (const cx<R> *)a.bh, a.ldf, a.fac);
   return cudaGetLastError();
 }
 

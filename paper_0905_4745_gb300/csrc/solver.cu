@@ -67,7 +67,10 @@ struct minnorm_plan_s {
   SrftParams P;
 
   // sketch tables
-  int logn = 0, logN1 = 0, tj = 0, tk = 0;
+  int logn = 0, logN1 = 0, tj = 0, tk = 0;  // FFT geometry of length L = 2^logn
+  bool bluestein = false;                    // n not a power of two: L >= 2n - 1
+  void *d_chirp = nullptr, *d_bhat = nullptr;  // Bluestein tables (compute precision)
+  double *d_fac = nullptr;                   // l complex128: c_{s_t} / sqrt(n)
   int cap1 = 0, cap2 = 0;
   int32_t *d_idx1 = nullptr, *d_idx2 = nullptr, *d_halo1 = nullptr, *d_halo2 = nullptr;
   void *d_ph1 = nullptr, *d_ph2 = nullptr, *d_cs1 = nullptr, *d_cs2 = nullptr, *d_post = nullptr, *d_tw = nullptr;
@@ -278,13 +281,28 @@ minnorm_status upload_params(minnorm_plan_t plan) {
   CK(cudaMemcpy(plan->d_samp_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(plan->d_samp_t, st_t.data(), sizeof(int32_t) * l, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(plan->d_samp_loc, st_loc.data(), sizeof(int32_t) * l, cudaMemcpyHostToDevice));
-  // twiddles e^{-2 pi i k / n}
+  // twiddles e^{-2 pi i k / L}
+  const int64_t L = int64_t(1) << logn;
   const double two_pi = 6.283185307179586476925286766559;
-  for (int64_t k = 0; k < n; ++k) {
-    const double a = two_pi * (double)k / (double)n;
+  tmp.resize(L);
+  for (int64_t k = 0; k < L; ++k) {
+    const double a = two_pi * (double)k / (double)L;
     tmp[k] = std::complex<double>(cos(a), -sin(a));
   }
   CK(put_complex(plan->d_tw, tmp));
+  if (plan->bluestein) {
+    std::vector<std::complex<double>> chirp, bh;
+    bluestein_tables(n, L, chirp, bh);
+    CK(put_complex(plan->d_chirp, chirp));
+    CK(put_complex(plan->d_bhat, bh));
+    std::vector<double> fac(2 * l);
+    const double sc = 1.0 / std::sqrt((double)n);
+    for (int64_t t = 0; t < l; ++t) {
+      fac[2 * t] = chirp[P.s[t]].real() * sc;
+      fac[2 * t + 1] = chirp[P.s[t]].imag() * sc;
+    }
+    CK(cudaMemcpy(plan->d_fac, fac.data(), sizeof(double) * 2 * l, cudaMemcpyHostToDevice));
+  }
   plan->sketched = false;
   return MINNORM_OK;
 }
@@ -301,14 +319,20 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   plan->fp32 = (prec == MINNORM_MIXED);
   CK(cudaGetDevice(&plan->device));
   CK(cudaDeviceGetAttribute(&plan->sms, cudaDevAttrMultiProcessorCount, plan->device));
-  // FFT geometry (powers of two)
-  plan->logn = ilog2(n);
+  // FFT geometry: length L = n for a power of two, else the Bluestein length 2^ceil(log2(2n - 1))
+  plan->bluestein = (n & (n - 1)) != 0;
+  int64_t L = n;
+  if (plan->bluestein) {
+    L = 1;
+    while (L < 2 * n - 1) L <<= 1;
+  }
+  plan->logn = ilog2(L);
   const int cap = plan->fp32 ? 8192 : 4096;
-  if (n <= cap) {
+  if (L <= cap) {
     plan->logN1 = 0;
   } else {
     plan->logN1 = plan->logn / 2;
-    const int64_t N1 = int64_t(1) << plan->logN1, N2 = n / N1;
+    const int64_t N1 = int64_t(1) << plan->logN1, N2 = L / N1;
     if (N2 > cap) return MINNORM_ENOTSUP;
     plan->tj = (int)std::min<int64_t>(N1, cap / N2);
     plan->tk = (int)std::min<int64_t>(N2, cap / N1);
@@ -324,13 +348,18 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   ALLOC(plan->d_cs1, rc * n);
   ALLOC(plan->d_cs2, rc * n);
   ALLOC(plan->d_post, rc * n);
-  ALLOC(plan->d_tw, rc * n);
-  const int64_t nbB = plan->logN1 ? ((n >> plan->logN1) / plan->tk) : 1;
+  ALLOC(plan->d_tw, rc * L);
+  if (plan->bluestein) {
+    ALLOC(plan->d_chirp, rc * n);
+    ALLOC(plan->d_bhat, rc * L);
+    ALLOC(plan->d_fac, 2 * sizeof(double) * l);
+  }
+  const int64_t nbB = plan->logN1 ? ((L >> plan->logN1) / plan->tk) : 1;
   ALLOC(plan->d_samp_off, sizeof(int32_t) * (nbB + 1));
   ALLOC(plan->d_samp_t, sizeof(int32_t) * l);
   ALLOC(plan->d_samp_loc, sizeof(int32_t) * l);
-  ALLOC(plan->d_S1, rc * (size_t)m * n);
-  ALLOC(plan->d_S2, rc * (size_t)m * n);
+  ALLOC(plan->d_S1, rc * (size_t)m * L);
+  ALLOC(plan->d_S2, rc * (size_t)m * L);
   ALLOC(plan->d_Y, sizeof(zd) * (size_t)l * m);
   if (flags & MINNORM_FLAG_KEEP_SKETCH) ALLOC(plan->d_Ykeep, sizeof(zd) * (size_t)l * m);
   ALLOC(plan->d_vn1, sizeof(double) * 2 * m);
@@ -421,9 +450,49 @@ minnorm_status sketch_impl(minnorm_plan_t plan, const void *A, int64_t lda) {
     ChainArgs c2{plan->d_S1, n, plan->d_S2, n, plan->d_idx2, plan->d_ph2, plan->d_cs2, plan->d_post,
                  plan->d_halo2, (int)n, kSeg, plan->cap2, (int)m, plan->fp32, false, plan->fp32};
     CK(launch_chain(c2, st));
-    FftArgs f{plan->d_S2, n, plan->d_S1, plan->d_tw, plan->logn, plan->logN1, plan->tj, plan->tk,
-              plan->d_samp_off, plan->d_samp_t, plan->d_samp_loc, (int)l, (int)m, plan->d_Y, l, 0, plan->fp32};
-    CK(launch_fft(f, st));
+    const int64_t L = int64_t(1) << plan->logn;
+    FftArgs f{};
+    f.tw = plan->d_tw;
+    f.logn = plan->logn;
+    f.logN1 = plan->logN1;
+    f.tj = plan->tj;
+    f.tk = plan->tk;
+    f.samp_off = plan->d_samp_off;
+    f.samp_t = plan->d_samp_t;
+    f.samp_loc = plan->d_samp_loc;
+    f.l = (int)l;
+    f.rows = (int)m;
+    f.Y = plan->d_Y;
+    f.ldy = l;
+    f.real_fp32 = plan->fp32;
+    if (!plan->bluestein) {
+      f.src = plan->d_S2;
+      f.ld = n;
+      f.work = plan->d_S1;
+      f.ldw = n;
+      CK(launch_fft(f, st));
+    } else {
+      // stage 1: conj(FFT_L(x c) bh) in full; stage 2: FFT_L of that, sampled with c_k / sqrt(n)
+      // (single pass: S2 -> S1 -> Y; four-step: S2 -> S1 -> S2, then S2 -> S1 -> Y)
+      FftArgs f1 = f;
+      f1.src = plan->d_S2;
+      f1.ld = n;
+      f1.work = plan->d_S1;
+      f1.ldw = L;
+      f1.chirp = plan->d_chirp;
+      f1.nin = (int)n;
+      f1.full = plan->logN1 ? plan->d_S2 : plan->d_S1;
+      f1.bh = plan->d_bhat;
+      f1.ldf = L;
+      CK(launch_fft(f1, st));
+      FftArgs f2 = f;
+      f2.src = f1.full;
+      f2.ld = L;
+      f2.work = plan->d_S1;
+      f2.ldw = L;
+      f2.fac = plan->d_fac;
+      CK(launch_fft(f2, st));
+    }
   }
   if (plan->d_Ykeep) CK(cudaMemcpyAsync(plan->d_Ykeep, plan->d_Y, sizeof(zd) * l * m, cudaMemcpyDeviceToDevice, st));
   if (timing) CK(cudaEventRecord(e1, st));
@@ -693,7 +762,6 @@ minnorm_status minnorm_plan_create(minnorm_plan_t *out, int64_t m, int64_t n, in
   if (dtype != MINNORM_C128 && dtype != MINNORM_C64) return MINNORM_EINVAL;
   if (prec != MINNORM_FP64 && prec != MINNORM_MIXED) return MINNORM_EINVAL;
   if ((flags & ~(MINNORM_FLAG_TIMING | MINNORM_FLAG_KEEP_SKETCH)) != 0) return MINNORM_EINVAL;
-  if ((n & (n - 1)) != 0) return MINNORM_ENOTSUP;        // the FFT handles powers of two
   if (n > (int64_t(1) << 30) || m > 4864) return MINNORM_ENOTSUP;
   minnorm_plan_t plan = new (std::nothrow) minnorm_plan_s();
   if (!plan) return MINNORM_ENOMEM;
@@ -759,6 +827,24 @@ minnorm_status minnorm_solve(minnorm_plan_t plan, const void *A, int64_t lda, co
   plan->g_hp.ld = lda;
   plan->g_cg.ld = plan->d_A32 ? plan->n : lda;
   return solve_impl(plan, A, lda, b, eps, x, info);
+}
+
+minnorm_status minnorm_solve_many(minnorm_plan_t plan, const void *A, int64_t lda, const void *B, int64_t ldb,
+                                  int64_t nrhs, double eps, void *X, int64_t ldx, minnorm_info *infos) {
+  if (!plan || !A || !B || !X) return MINNORM_EINVAL;
+  if (plan->failed || !plan->sketched) return MINNORM_ESTATE;
+  if (lda < plan->n || ldb < plan->m || ldx < plan->n || nrhs < 1) return MINNORM_EINVAL;
+  if (!(eps > 0.0 && eps < 1.0)) return MINNORM_EINVAL;
+  plan->g_hp.ld = lda;
+  plan->g_cg.ld = plan->d_A32 ? plan->n : lda;
+  minnorm_status first = MINNORM_OK;
+  for (int64_t j = 0; j < nrhs; ++j) {
+    const minnorm_status s = solve_impl(plan, A, lda, static_cast<const zd *>(B) + j * ldb, eps,
+                                        static_cast<zd *>(X) + j * ldx, infos ? infos + j : nullptr);
+    if (s == MINNORM_EINVAL || s == MINNORM_ESTATE || s == MINNORM_ECUDA) return s;
+    if (s != MINNORM_OK && first == MINNORM_OK) first = s;
+  }
+  return first;
 }
 
 minnorm_status minnorm_solve_host(minnorm_plan_t plan, const void *A_host, int64_t lda, const void *b_host,

@@ -23,7 +23,7 @@ FLAG_TIMING, FLAG_KEEP_SKETCH = 1, 2
 EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_sketch", "minnorm_solve",
            "minnorm_solve_host", "minnorm_plan_destroy", "minnorm_status_string", "minnorm_get_sketch",
            "minnorm_get_factor", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats",
-           "minnorm_launch_count", "minnorm_qr_noalloc"]
+           "minnorm_launch_count", "minnorm_qr_noalloc", "minnorm_solve_many"]
 
 
 class MinnormError(RuntimeError):
@@ -58,6 +58,7 @@ def lib():
         L.minnorm_sketch.argtypes = [p, p, i64]
         L.minnorm_solve.argtypes = [p, p, i64, p, d, p, C.POINTER(Info)]
         L.minnorm_solve_host.argtypes = [p, p, i64, p, d, p, C.POINTER(Info)]
+        L.minnorm_solve_many.argtypes = [p, p, i64, p, i64, i64, d, p, i64, C.POINTER(Info)]
         L.minnorm_plan_destroy.argtypes = [p]
         L.minnorm_status_string.argtypes = [C.c_int]
         L.minnorm_status_string.restype = C.c_char_p
@@ -138,6 +139,21 @@ def minnorm_solve(plan, A, b, eps, x, lda=None, info=True, allow=(OK,)):
                              C.byref(inf) if inf is not None else None)
     _check(st, "minnorm_solve", allow)
     return st, (inf.as_dict() if inf is not None else None)
+
+
+def minnorm_solve_many(plan, A, B, eps, X, lda=None, info=True, allow=(OK,)):
+    """B: m x nrhs and X: n x nrhs complex128 device tensors, column-major (their .T contiguous),
+    i.e. column j at B + j*ldb; ldb/ldx are taken from the tensors' column strides."""
+    lda = A.shape[-1] if lda is None else lda
+    nrhs = B.shape[1]
+    ldb, ldx = B.stride(1), X.stride(1)
+    if B.stride(0) != 1 or X.stride(0) != 1 or X.shape[1] != nrhs:
+        raise ValueError("B and X must be column-major with matching column counts")
+    infos = (Info * nrhs)() if info else None
+    st = lib().minnorm_solve_many(plan, _ptr(A), int(lda), _ptr(B), int(ldb), int(nrhs), float(eps), _ptr(X),
+                                  int(ldx), infos)
+    _check(st, "minnorm_solve_many", allow)
+    return st, ([i.as_dict() for i in infos] if infos is not None else None)
 
 
 def minnorm_solve_host(plan, A, b, eps, x, lda=None, info=True, allow=(OK,)):
