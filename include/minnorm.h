@@ -45,6 +45,7 @@ extern "C" {
 #endif
 
 typedef struct minnorm_plan_s *minnorm_plan_t;
+typedef struct minnorm_batch_s *minnorm_batch_t;
 
 typedef enum {
   MINNORM_C128 = 0,          /* A stored as complex128 */
@@ -81,7 +82,8 @@ typedef struct {
   int32_t outer_steps;       /* refinement steps taken */
   int32_t cg_iters;          /* CG iterations summed over all steps */
   int32_t exact_passes;      /* passes over A in exact fixed-point arithmetic (x = A^* y, b - A x) */
-  int32_t reserved0;
+  int32_t status;            /* this solve's minnorm_status (per column / per system in the
+                                block and batch entry points) */
   double err_bound;          /* a-posteriori bound on ||x - p|| / ||x|| (uses sigma_min(A^* P R^{-1}) >= 1) */
   double resid_rel;          /* ||b - A x|| / ||b|| from the last residual */
   double rdiag_max;          /* |R_11| */
@@ -172,6 +174,38 @@ minnorm_status minnorm_solve_many(minnorm_plan_t plan, const void *A, int64_t ld
  */
 minnorm_status minnorm_solve_host(minnorm_plan_t plan, const void *A_host, int64_t lda,
                                   const void *b_host, double eps, void *x_host, minnorm_info *info);
+
+/*
+ * Batches of independent systems of uneven sizes (system i: m[i] x n[i], any
+ * n[i] >= 2, m[i] < n[i], l[i] = min(4 m[i], n[i])), solved in turn on one
+ * stream. System i uses the SRFT realization a plan with seed (seed + i)
+ * would draw. Each system keeps its own parameter tables, sketch, R and
+ * P R^{-1}; the m x n-sized scratch (the sketch's transform buffers, the
+ * fixed-point and complex64 copies of A) is one pool sized for the largest
+ * system and shared, so a batch holds little more than its largest plan.
+ *   count: >= 1; m, n: host arrays of count sizes; dtype, precision, flags,
+ *   stream as for minnorm_plan_create.
+ * Errors: EINVAL (a size or enum), ENOMEM, ENOTSUP, ECUDA.
+ */
+minnorm_status minnorm_batch_create(minnorm_batch_t *batch, int32_t count, const int64_t *m, const int64_t *n,
+                                    minnorm_dtype dtype, minnorm_precision precision, uint64_t seed,
+                                    uint32_t flags, void *stream);
+
+/*
+ * Steps 1-5 for every system of the batch: A[i] (device, row-major m[i] x n[i],
+ * leading dimension lda[i], or n[i] when lda is NULL), b[i] (device, m[i]
+ * complex128) -> x[i] (device, n[i] complex128), each with the guarantee of
+ * minnorm_solve for eps. A, lda, b, x, infos are host arrays of count entries
+ * (infos may be NULL; infos[i].status is system i's status). Returns
+ * MINNORM_OK when every system did; otherwise the status of the first system
+ * that did not (a system ending in ERANK, ENOCONV or EFLOOR does not stop the
+ * others; EINVAL, ECUDA and ETIMEOUT stop at once). Synchronizes the stream.
+ */
+minnorm_status minnorm_batch_solve(minnorm_batch_t batch, const void *const *A, const int64_t *lda,
+                                   const void *const *b, double eps, void *const *x, minnorm_info *infos);
+
+/* Free the batch, its plans and the shared scratch. NULL is accepted. */
+minnorm_status minnorm_batch_destroy(minnorm_batch_t batch);
 
 /* Free the plan and its workspace (synchronizes its stream). NULL is accepted. */
 minnorm_status minnorm_plan_destroy(minnorm_plan_t plan);

@@ -54,7 +54,14 @@ struct KernelTimer {
 
 }  // namespace
 
+// m x n-sized scratch a batch shares among its plans (solved in turn)
+struct ScratchPool {
+  void *S1 = nullptr, *S2 = nullptr, *afix = nullptr, *A32 = nullptr;
+  size_t s_bytes = 0, afix_bytes = 0, a32_bytes = 0;
+};
+
 struct minnorm_plan_s {
+  const ScratchPool *pool = nullptr;  // if set, S1, S2, afix and A32 point into it
   int64_t m = 0, n = 0, l = 0;
   minnorm_dtype dtype = MINNORM_C128;
   minnorm_precision prec = MINNORM_FP64;
@@ -159,6 +166,24 @@ minnorm_status dalloc(minnorm_plan_t plan, T **ptr, size_t bytes) {
     minnorm_status s_ = dalloc(plan, &(ptr), (bytes));  \
     if (s_ != MINNORM_OK) return s_;                    \
   } while (0)
+
+// transform length of the sketch: n, or Bluestein's power of two >= 2n - 1
+int64_t fft_length(int64_t n) {
+  if ((n & (n - 1)) == 0) return n;
+  int64_t L = 1;
+  while (L < 2 * n - 1) L <<= 1;
+  return L;
+}
+
+// bytes of the pooled scratch of one plan
+void scratch_sizes(int64_t m, int64_t n, minnorm_precision prec, minnorm_dtype dtype, size_t &s_bytes,
+                   size_t &afix_bytes, size_t &a32_bytes) {
+  const bool fp32 = prec == MINNORM_MIXED;
+  const size_t rc = fp32 ? sizeof(zf) : sizeof(zd);
+  s_bytes = rc * (size_t)m * (size_t)fft_length(n);
+  afix_bytes = sizeof(int64_t) * 2 * (size_t)m * (size_t)n;
+  a32_bytes = (fp32 && dtype == MINNORM_C128) ? sizeof(zf) * (size_t)m * (size_t)n : 0;
+}
 
 int ilog2(int64_t v) {
   int k = 0;
@@ -321,11 +346,7 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   CK(cudaDeviceGetAttribute(&plan->sms, cudaDevAttrMultiProcessorCount, plan->device));
   // FFT geometry: length L = n for a power of two, else the Bluestein length 2^ceil(log2(2n - 1))
   plan->bluestein = (n & (n - 1)) != 0;
-  int64_t L = n;
-  if (plan->bluestein) {
-    L = 1;
-    while (L < 2 * n - 1) L <<= 1;
-  }
+  const int64_t L = fft_length(n);
   plan->logn = ilog2(L);
   const int cap = plan->fp32 ? 8192 : 4096;
   if (L <= cap) {
@@ -358,8 +379,17 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   ALLOC(plan->d_samp_off, sizeof(int32_t) * (nbB + 1));
   ALLOC(plan->d_samp_t, sizeof(int32_t) * l);
   ALLOC(plan->d_samp_loc, sizeof(int32_t) * l);
-  ALLOC(plan->d_S1, rc * (size_t)m * L);
-  ALLOC(plan->d_S2, rc * (size_t)m * L);
+  if (plan->pool) {
+    size_t sb = 0, ab = 0, a32 = 0;
+    scratch_sizes(m, n, prec, dtype, sb, ab, a32);
+    if (sb > plan->pool->s_bytes || ab > plan->pool->afix_bytes || a32 > plan->pool->a32_bytes)
+      return MINNORM_EINVAL;
+    plan->d_S1 = plan->pool->S1;
+    plan->d_S2 = plan->pool->S2;
+  } else {
+    ALLOC(plan->d_S1, rc * (size_t)m * L);
+    ALLOC(plan->d_S2, rc * (size_t)m * L);
+  }
   ALLOC(plan->d_Y, sizeof(zd) * (size_t)l * m);
   if (flags & MINNORM_FLAG_KEEP_SKETCH) ALLOC(plan->d_Ykeep, sizeof(zd) * (size_t)l * m);
   ALLOC(plan->d_vn1, sizeof(double) * 2 * m);
@@ -372,7 +402,10 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   ALLOC(plan->d_bar, sizeof(GridBarrier));
   ALLOC(plan->d_qrmail, qr_mail_bytes());
   ALLOC(plan->d_err, sizeof(int));
-  if (plan->fp32 && dtype == MINNORM_C128) ALLOC(plan->d_A32, sizeof(zf) * (size_t)m * n);
+  if (plan->fp32 && dtype == MINNORM_C128) {
+    if (plan->pool) plan->d_A32 = static_cast<zf *>(plan->pool->A32);
+    else ALLOC(plan->d_A32, sizeof(zf) * (size_t)m * n);
+  }
   // products: g_cg for the CG passes, g_hp for FP64 / double-double passes on the stored A
   const int hp_mode = dtype == MINNORM_C128 ? 0 : 2;
   gemv_configure(plan->g_hp, m, n, n, hp_mode, plan->sms);
@@ -397,7 +430,8 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   ALLOC(plan->d_xh, sizeof(zd) * n);
   ALLOC(plan->d_xl, sizeof(zd) * n);
   ALLOC(plan->d_d, sizeof(zd) * n);
-  ALLOC(plan->d_afix, sizeof(int64_t) * 2 * (size_t)m * n);
+  if (plan->pool) plan->d_afix = plan->pool->afix;
+  else ALLOC(plan->d_afix, sizeof(int64_t) * 2 * (size_t)m * n);
   ALLOC(plan->d_E, sizeof(int32_t) * m);
   ALLOC(plan->d_yfix, 32 * (size_t)m);
   ALLOC(plan->d_F, sizeof(int) * 2);
@@ -713,7 +747,7 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
     info->outer_steps = outer;
     info->cg_iters = cg_total;
     info->exact_passes = dd_passes;
-    info->reserved0 = 0;
+    info->status = status;
     info->err_bound = err;
     const double bn = std::sqrt(plan->h_norms[3]);
     info->resid_rel = bn > 0 ? std::sqrt(plan->h_norms[2]) / bn : 0.0;
@@ -725,6 +759,38 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
     info->reserved = 0;
   }
   return status;
+}
+
+// argument checks of minnorm_plan_create (no device access)
+minnorm_status check_plan_args(int64_t m, int64_t n, int64_t &l, minnorm_dtype dtype, minnorm_precision prec,
+                               uint32_t flags) {
+  if (m < 1 || n < 2 || m >= n) return MINNORM_EINVAL;
+  if (l == 0) l = std::min<int64_t>(4 * m, n);
+  if (l <= m || l > n) return MINNORM_EINVAL;
+  if (dtype != MINNORM_C128 && dtype != MINNORM_C64) return MINNORM_EINVAL;
+  if (prec != MINNORM_FP64 && prec != MINNORM_MIXED) return MINNORM_EINVAL;
+  if ((flags & ~(MINNORM_FLAG_TIMING | MINNORM_FLAG_KEEP_SKETCH)) != 0) return MINNORM_EINVAL;
+  if (n > (int64_t(1) << 30) || m > 4864) return MINNORM_ENOTSUP;
+  return MINNORM_OK;
+}
+
+minnorm_status plan_create_pooled(minnorm_plan_t *out, int64_t m, int64_t n, int64_t l, minnorm_dtype dtype,
+                                  minnorm_precision prec, uint64_t seed, uint32_t flags, void *stream,
+                                  const ScratchPool *pool) {
+  if (!out) return MINNORM_EINVAL;
+  *out = nullptr;
+  minnorm_status c = check_plan_args(m, n, l, dtype, prec, flags);
+  if (c != MINNORM_OK) return c;
+  minnorm_plan_t plan = new (std::nothrow) minnorm_plan_s();
+  if (!plan) return MINNORM_ENOMEM;
+  plan->pool = pool;
+  minnorm_status s = create_impl(plan, m, n, l, dtype, prec, seed, flags, stream);
+  if (s != MINNORM_OK) {
+    minnorm_plan_destroy(plan);
+    return s;
+  }
+  *out = plan;
+  return MINNORM_OK;
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
@@ -754,24 +820,7 @@ const char *minnorm_status_string(minnorm_status s) {
 
 minnorm_status minnorm_plan_create(minnorm_plan_t *out, int64_t m, int64_t n, int64_t l, minnorm_dtype dtype,
                                    minnorm_precision prec, uint64_t seed, uint32_t flags, void *stream) {
-  if (!out) return MINNORM_EINVAL;
-  *out = nullptr;
-  if (m < 1 || n < 2 || m >= n) return MINNORM_EINVAL;
-  if (l == 0) l = std::min<int64_t>(4 * m, n);
-  if (l <= m || l > n) return MINNORM_EINVAL;
-  if (dtype != MINNORM_C128 && dtype != MINNORM_C64) return MINNORM_EINVAL;
-  if (prec != MINNORM_FP64 && prec != MINNORM_MIXED) return MINNORM_EINVAL;
-  if ((flags & ~(MINNORM_FLAG_TIMING | MINNORM_FLAG_KEEP_SKETCH)) != 0) return MINNORM_EINVAL;
-  if (n > (int64_t(1) << 30) || m > 4864) return MINNORM_ENOTSUP;
-  minnorm_plan_t plan = new (std::nothrow) minnorm_plan_s();
-  if (!plan) return MINNORM_ENOMEM;
-  minnorm_status s = create_impl(plan, m, n, l, dtype, prec, seed, flags, stream);
-  if (s != MINNORM_OK) {
-    minnorm_plan_destroy(plan);
-    return s;
-  }
-  *out = plan;
-  return MINNORM_OK;
+  return plan_create_pooled(out, m, n, l, dtype, prec, seed, flags, stream, nullptr);
 }
 
 minnorm_status minnorm_plan_set_params(minnorm_plan_t plan, const double *zeta_t, const int64_t *pi_t,
@@ -955,6 +1004,95 @@ minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *lau
   *launches = k == 5 ? plan->fused_iters : plan->stat_launches[k];
   *ms = plan->stat_ms[k];
   return MINNORM_OK;
+}
+
+
+// ---- batches ----------------------------------------------------------------
+struct minnorm_batch_s {
+  std::vector<minnorm_plan_t> plans;
+  ScratchPool pool;
+  std::vector<void *> allocs;
+};
+
+minnorm_status minnorm_batch_destroy(minnorm_batch_t batch) {
+  if (!batch) return MINNORM_OK;
+  for (minnorm_plan_t p : batch->plans) minnorm_plan_destroy(p);  // synchronizes the stream
+  for (void *p : batch->allocs) cudaFree(p);
+  delete batch;
+  return MINNORM_OK;
+}
+
+minnorm_status minnorm_batch_create(minnorm_batch_t *out, int32_t count, const int64_t *m, const int64_t *n,
+                                    minnorm_dtype dtype, minnorm_precision precision, uint64_t seed,
+                                    uint32_t flags, void *stream) {
+  if (!out) return MINNORM_EINVAL;
+  *out = nullptr;
+  if (count < 1 || !m || !n) return MINNORM_EINVAL;
+  size_t sb = 0, ab = 0, a32 = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    int64_t l = 0;
+    const minnorm_status c = check_plan_args(m[i], n[i], l, dtype, precision, flags);
+    if (c != MINNORM_OK) return c;
+    size_t s1 = 0, s2 = 0, s3 = 0;
+    scratch_sizes(m[i], n[i], precision, dtype, s1, s2, s3);
+    sb = std::max(sb, s1);
+    ab = std::max(ab, s2);
+    a32 = std::max(a32, s3);
+  }
+  minnorm_batch_t b = new (std::nothrow) minnorm_batch_s();
+  if (!b) return MINNORM_ENOMEM;
+  auto grab = [&](void **p, size_t bytes) -> bool {
+    if (bytes == 0) return true;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    b->allocs.push_back(*p);
+    return true;
+  };
+  if (!grab(&b->pool.S1, sb) || !grab(&b->pool.S2, sb) || !grab(&b->pool.afix, ab) || !grab(&b->pool.A32, a32)) {
+    minnorm_batch_destroy(b);
+    return MINNORM_ENOMEM;
+  }
+  b->pool.s_bytes = sb;
+  b->pool.afix_bytes = ab;
+  b->pool.a32_bytes = a32;
+  b->plans.reserve(count);
+  for (int32_t i = 0; i < count; ++i) {
+    minnorm_plan_t p = nullptr;
+    const minnorm_status s =
+        plan_create_pooled(&p, m[i], n[i], 0, dtype, precision, seed + (uint64_t)i, flags, stream, &b->pool);
+    if (s != MINNORM_OK) {
+      minnorm_batch_destroy(b);
+      return s;
+    }
+    b->plans.push_back(p);
+  }
+  *out = b;
+  return MINNORM_OK;
+}
+
+minnorm_status minnorm_batch_solve(minnorm_batch_t batch, const void *const *A, const int64_t *lda,
+                                   const void *const *b, double eps, void *const *x, minnorm_info *infos) {
+  if (!batch || !A || !b || !x) return MINNORM_EINVAL;
+  if (!(eps > 0.0 && eps < 1.0)) return MINNORM_EINVAL;
+  minnorm_status first = MINNORM_OK;
+  for (size_t i = 0; i < batch->plans.size(); ++i) {
+    minnorm_plan_t p = batch->plans[i];
+    const int64_t ld = lda ? lda[i] : p->n;
+    minnorm_status s = minnorm_sketch(p, A[i], ld);
+    if (s == MINNORM_OK) {
+      s = minnorm_solve(p, A[i], ld, b[i], eps, x[i], infos ? infos + i : nullptr);
+    } else if (infos) {
+      memset(infos + i, 0, sizeof(minnorm_info));
+      infos[i].status = s;
+    }
+    if (s == MINNORM_EINVAL || s == MINNORM_ECUDA || s == MINNORM_ETIMEOUT || s == MINNORM_ESTATE ||
+        s == MINNORM_ENOMEM)
+      return s;
+    if (s != MINNORM_OK && first == MINNORM_OK) first = s;
+  }
+  return first;
 }
 
 }  // extern "C"

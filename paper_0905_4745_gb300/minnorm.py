@@ -23,7 +23,8 @@ FLAG_TIMING, FLAG_KEEP_SKETCH = 1, 2
 EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_sketch", "minnorm_solve",
            "minnorm_solve_host", "minnorm_plan_destroy", "minnorm_status_string", "minnorm_get_sketch",
            "minnorm_get_factor", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats",
-           "minnorm_launch_count", "minnorm_qr_noalloc", "minnorm_solve_many"]
+           "minnorm_launch_count", "minnorm_qr_noalloc", "minnorm_solve_many", "minnorm_batch_create",
+           "minnorm_batch_solve", "minnorm_batch_destroy"]
 
 
 class MinnormError(RuntimeError):
@@ -34,7 +35,7 @@ class MinnormError(RuntimeError):
 
 class Info(C.Structure):
     _fields_ = [("outer_steps", C.c_int32), ("cg_iters", C.c_int32), ("exact_passes", C.c_int32),
-                ("reserved0", C.c_int32), ("err_bound", C.c_double), ("resid_rel", C.c_double),
+                ("status", C.c_int32), ("err_bound", C.c_double), ("resid_rel", C.c_double),
                 ("rdiag_max", C.c_double), ("rdiag_min", C.c_double), ("ms_sketch", C.c_float),
                 ("ms_qr", C.c_float), ("ms_solve", C.c_float), ("reserved", C.c_float)]
 
@@ -59,6 +60,11 @@ def lib():
         L.minnorm_solve.argtypes = [p, p, i64, p, d, p, C.POINTER(Info)]
         L.minnorm_solve_host.argtypes = [p, p, i64, p, d, p, C.POINTER(Info)]
         L.minnorm_solve_many.argtypes = [p, p, i64, p, i64, i64, d, p, i64, C.POINTER(Info)]
+        L.minnorm_batch_create.argtypes = [C.POINTER(p), i32, C.POINTER(i64), C.POINTER(i64), C.c_int, C.c_int,
+                                           u64, u32, p]
+        L.minnorm_batch_solve.argtypes = [p, C.POINTER(p), C.POINTER(i64), C.POINTER(p), d, C.POINTER(p),
+                                          C.POINTER(Info)]
+        L.minnorm_batch_destroy.argtypes = [p]
         L.minnorm_plan_destroy.argtypes = [p]
         L.minnorm_status_string.argtypes = [C.c_int]
         L.minnorm_status_string.restype = C.c_char_p
@@ -154,6 +160,37 @@ def minnorm_solve_many(plan, A, B, eps, X, lda=None, info=True, allow=(OK,)):
                                   int(ldx), infos)
     _check(st, "minnorm_solve_many", allow)
     return st, ([i.as_dict() for i in infos] if infos is not None else None)
+
+
+def minnorm_batch_create(ms, ns, dtype=C128, precision=FP64, seed=1, flags=0, stream=None):
+    """A batch of len(ms) systems, system i of size ms[i] x ns[i] (SRFT seed: seed + i)."""
+    count = len(ms)
+    if len(ns) != count:
+        raise ValueError("ms and ns differ in length")
+    am = (C.c_int64 * count)(*[int(v) for v in ms])
+    an = (C.c_int64 * count)(*[int(v) for v in ns])
+    h = C.c_void_p()
+    st = lib().minnorm_batch_create(C.byref(h), count, am, an, int(dtype), int(precision),
+                                    int(seed) & 0xFFFFFFFFFFFFFFFF, int(flags), _stream(stream))
+    _check(st, "minnorm_batch_create")
+    return h
+
+
+def minnorm_batch_solve(batch, As, bs, eps, xs, ldas=None, info=True, allow=(OK,)):
+    """As, bs, xs: sequences of device tensors (system i: m_i x n_i, m_i, n_i)."""
+    count = len(As)
+    pa = (C.c_void_p * count)(*[_ptr(a) for a in As])
+    pb = (C.c_void_p * count)(*[_ptr(v) for v in bs])
+    px = (C.c_void_p * count)(*[_ptr(v) for v in xs])
+    pl = (C.c_int64 * count)(*[int(v) for v in ldas]) if ldas is not None else None
+    infos = (Info * count)() if info else None
+    st = lib().minnorm_batch_solve(batch, pa, pl, pb, float(eps), px, infos)
+    _check(st, "minnorm_batch_solve", allow)
+    return st, ([i.as_dict() for i in infos] if infos is not None else None)
+
+
+def minnorm_batch_destroy(batch):
+    return _check(lib().minnorm_batch_destroy(batch), "minnorm_batch_destroy")
 
 
 def minnorm_solve_host(plan, A, b, eps, x, lda=None, info=True, allow=(OK,)):
