@@ -3,8 +3,7 @@
 //     (Wp^* A A^* Wp) du = g,   Wp = P R^{-1},
 // with every iteration reading A (complex64) from HBM exactly once.
 //
-// Each CTA owns a contiguous range of 16-column sub-panels of A (m <= 512
-// rows). A sub-panel (m x 16 complex64, 128 bytes per row) is brought into
+// Each CTA owns every G-th 16-column sub-panel of A (m <= 512 rows). A sub-panel (m x 16 complex64, 128 bytes per row) is brought into
 // shared memory by 2-D TMA loads (cp.async.bulk.tensor, 128-byte swizzle)
 // through a three-stage mbarrier pipeline, and used twice while resident:
 //     q_j  = sum_i conj(A_ij) w_i      for the sub-panel's 16 columns
@@ -124,8 +123,11 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   const int r0 = (int)((long long)m * b / G), r1 = (int)((long long)m * (b + 1) / G);
+  // sub-panels b, b + G, b + 2G, ...: at any moment the grid reads one contiguous
+  // stretch of every row (DRAM page locality), not G scattered 128-byte pieces
   const int NP = (P.n + kPanel - 1) / kPanel;
-  const int sp0 = (int)((long long)NP * b / G), sp1 = (int)((long long)NP * (b + 1) / G);
+  const int nsp = NP > b ? (NP - b + G - 1) / G : 0;
+  unsigned int epoch = 0;
   const uint32_t stage_tx = (uint32_t)stage_bytes;
 
   if (tid == 0) {
@@ -154,7 +156,7 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
   while (!done && it < P.maxit) {
     // P1: w = Wp p (own rows)
     rows_dot(P.Wp, p_s, m, r0, r1, P.w);
-    if (!grid_sync(P.bar, G, P.limit_ns)) { ok = false; break; }
+    if (!grid_sync(P.bar, G, epoch, P.limit_ns)) { ok = false; break; }
 
     // P2: q = A^* w and t = A q over the own sub-panels, A read once
     for (int i = tid; i < m; i += blockDim.x) {
@@ -163,23 +165,26 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
     }
     __syncthreads();
     zf tacc = {0.f, 0.f};
-    double qq_loc = 0.0;
+    // |q|^2 of this warp's columns in FP32 inside the loop (an FP64 instruction costs
+    // ~76 cycles of the SM sub-partition's FP64 pipe on GB300), widened once at the end
+    float qq_loc = 0.f;
     if (tid == 0) {
-      for (int q = 0; q < kStages && sp0 + q < sp1; ++q) {
+      for (int q = 0; q < kStages && q < nsp; ++q) {
         mbar_expect_tx(&mbar[q], stage_tx);
         for (int bx = 0; bx < nbox; ++bx)
-          tma_load_2d(stage[q] + bx * kBoxRows * 128, &amap, (sp0 + q) * 2 * kPanel, bx * kBoxRows, &mbar[q]);
+          tma_load_2d(stage[q] + bx * kBoxRows * 128, &amap, (b + q * G) * 2 * kPanel, bx * kBoxRows, &mbar[q]);
       }
     }
     int st = 0;
-    for (int sp = sp0; sp < sp1; ++sp) {
+    for (int ip = 0; ip < nsp; ++ip) {
+      const int sp = b + ip * G;
       bool w_ok = mbar_wait(&mbar[st], parity[st], P.limit_ns);
       if (!w_ok) w_ok = mbar_wait(&mbar[st], parity[st], P.limit_ns);  // a second bounded wait
       parity[st] ^= 1u;
       if (__syncthreads_or(!w_ok)) {
         // give up uniformly; later stages may still hold issued copies: wait for them (bounded)
         ok = false;
-        for (int q = 1; q < kStages && sp + q < sp1; ++q) {
+        for (int q = 1; q < kStages && ip + q < nsp; ++q) {
           const int s2 = (st + q) % kStages;
           mbar_wait(&mbar[s2], parity[s2], P.limit_ns);
         }
@@ -199,7 +204,7 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
         if (lane == 0) {
           q_s[j] = acc;
           if (sp * kPanel + j < P.n)
-            qq_loc = fma((double)acc.re, (double)acc.re, fma((double)acc.im, (double)acc.im, qq_loc));
+            qq_loc = fmaf(acc.re, acc.re, fmaf(acc.im, acc.im, qq_loc));
         }
       }
       __syncthreads();
@@ -216,24 +221,24 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
         }
       }
       __syncthreads();  // stage st is free
-      if (tid == 0 && sp + kStages < sp1) {
+      if (tid == 0 && ip + kStages < nsp) {
         mbar_expect_tx(&mbar[st], stage_tx);
         for (int bx = 0; bx < nbox; ++bx)
-          tma_load_2d(stage[st] + bx * kBoxRows * 128, &amap, (sp + kStages) * 2 * kPanel, bx * kBoxRows,
+          tma_load_2d(stage[st] + bx * kBoxRows * 128, &amap, (sp + kStages * G) * 2 * kPanel, bx * kBoxRows,
                       &mbar[st]);
       }
       st = (st + 1 == kStages) ? 0 : st + 1;
     }
     if (!ok) break;
     if (tid < m) P.tpart[(int64_t)b * m + tid] = tacc;
-    if (lane == 0) s_qq[wid] = qq_loc;
+    if (lane == 0) s_qq[wid] = (double)qq_loc;
     __syncthreads();
     if (tid == 0) {
       double qsum = 0.0;
       for (int w2 = 0; w2 < kCgThreads / 32; ++w2) qsum += s_qq[w2];
       P.qq_part[b] = qsum;
     }
-    if (!grid_sync(P.bar, G, P.limit_ns)) { ok = false; break; }
+    if (!grid_sync(P.bar, G, epoch, P.limit_ns)) { ok = false; break; }
 
     // P3a: t (own rows) = sum of the partials; qq = sum of the per-CTA |q|^2
     for (int i = r0 + wid; i < r1; i += blockDim.x >> 5) {
@@ -253,7 +258,7 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
       qs = warp_sum(qs);
       if (lane == 0) s_scal[0] = qs;
     }
-    if (!grid_sync(P.bar, G, P.limit_ns)) { ok = false; break; }
+    if (!grid_sync(P.bar, G, epoch, P.limit_ns)) { ok = false; break; }
     const double qq = s_scal[0];
     const double alpha = qq > 0.0 ? gamma / qq : 0.0;
 
@@ -278,7 +283,7 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
       const double gs = warp_sum(gl);
       if (lane == 0) P.gg_part[b] = gs;
     }
-    if (!grid_sync(P.bar, G, P.limit_ns)) { ok = false; break; }
+    if (!grid_sync(P.bar, G, epoch, P.limit_ns)) { ok = false; break; }
 
     // P4: gamma' and the new direction, identically in every CTA
     if (wid == 0) {
@@ -308,7 +313,7 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
     return;
   }
   // dy = Wp u (own rows)
-  if (!grid_sync(P.bar, G, P.limit_ns)) {
+  if (!grid_sync(P.bar, G, epoch, P.limit_ns)) {
     if (tid == 0) atomicExch(P.err, 1);
     return;
   }

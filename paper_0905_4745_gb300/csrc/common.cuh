@@ -140,8 +140,8 @@ __device__ __forceinline__ void dd_round(dd_acc a, double &hi, double &lo) { two
 
 // ---- grid barrier with a bounded wait ------------------------------------
 struct GridBarrier {
-  unsigned int count;
-  unsigned int gen;
+  unsigned int count;  // arrivals since launch
+  unsigned int gen;    // unused
   int err;  // set to 1 when a wait expired (or by a caller to stop the grid)
   int pad;
 };
@@ -162,23 +162,24 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // All blocks of a co-resident (cooperative) grid meet here. Returns false,
 // on every thread of the block, if the barrier gave up: after `limit_ns` of
-// waiting, or when another block already reported a failure. Every wait in the
-// library goes through this function.
-__device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned int nblocks, uint64_t limit_ns) {
+// waiting, or when another block already reported a failure. The arrival
+// counter only grows: the e-th barrier of a launch is complete once it reaches
+// e * nblocks, so one atomic per block and a poll of the same word suffice
+// (`epoch` counts this block's barriers; it starts at 0 and the counter must be
+// zero at launch).
+__device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned int nblocks, unsigned int &epoch,
+                                          uint64_t limit_ns) {
   __shared__ int s_ok;
+  epoch += 1u;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
+    const unsigned int target = epoch * nblocks;
     __threadfence();
-    const unsigned int g = ld_acquire_u32(&b->gen);
     const unsigned int arrived = atomicAdd(&b->count, 1u) + 1u;
-    if (arrived == nblocks) {
-      atomicExch(&b->count, 0u);
-      __threadfence();
-      atomicAdd(&b->gen, 1u);
-    } else {
+    if ((int)(target - arrived) > 0) {
       const uint64_t t0 = global_ns();
-      while (ld_acquire_u32(&b->gen) == g) {
+      while ((int)(target - ld_acquire_u32(&b->count)) > 0) {
         if (ld_volatile_i32(&b->err)) { ok = 0; break; }
         if (global_ns() - t0 > limit_ns) { atomicExch(&b->err, 1); ok = 0; break; }
       }

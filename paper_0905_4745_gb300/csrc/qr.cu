@@ -1003,30 +1003,56 @@ cudaError_t launch_qrp(const QrArgs &a, cudaStream_t st) {
 // (after w_j is final, subtract w_j R[0:j, j] from the entries above). Writes
 // Wp = P R^{-1} (row piv[i] of Wp is row i of R^{-1}) and WpH = Wp^*, both
 // row-major; the caller zeroes them first.
+//
+// The chain of k steps is latency-bound, so each step is kept short: the
+// reciprocals of R's (real) diagonal are formed once per CTA, the thread that
+// finishes w_{j-1} scales it at once (no FP64 division inside the chain, one
+// FP64 instruction per step instead of one per thread), and with STAGE the next
+// column of R is copied into shared memory by cp.async while the current one is
+// applied (each thread copies and reads only its own rows).
+template <bool STAGE>
 __global__ void __launch_bounds__(128)
 prinv_kernel(const zd *__restrict__ R, const int32_t *__restrict__ piv, int m, zd *__restrict__ Wp,
              zd *__restrict__ WpH) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   zd *w = reinterpret_cast<zd *>(smem_raw);
   zd *wout = w + m;
+  zd *rcol = wout + m;                                      // STAGE: 2 x m
+  double *rinv = reinterpret_cast<double *>(rcol + (STAGE ? 2 * m : 0));
+  __shared__ zd s_wj[2];
+  const int tid = threadIdx.x;
   const int k = m - 1 - blockIdx.x;  // longest columns first: they bound the kernel's duration
-  for (int i = threadIdx.x; i <= k; i += blockDim.x) w[i] = {i == k ? 1.0 : 0.0, 0.0};
+  for (int i = tid; i <= k; i += blockDim.x) {
+    w[i] = {i == k ? 1.0 : 0.0, 0.0};
+    rinv[i] = 1.0 / R[i + (int64_t)i * m].re;
+  }
+  if (STAGE) {
+    for (int i = tid; i < k; i += blockDim.x)
+      cp_async16(rcol + (k & 1) * m + i, R + i + (int64_t)k * m, 16);
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  if (tid == 0) s_wj[k & 1] = {rinv[k], 0.0};
   for (int j = k; j >= 0; --j) {
-    __syncthreads();
-    const double rjj = R[j + (int64_t)j * m].re;  // real diagonal
-    const zd wj = {w[j].re / rjj, w[j].im / rjj};
-    if (threadIdx.x == 0) wout[j] = wj;
-    const zd *rj = R + (int64_t)j * m;
-    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    __syncthreads();  // s_wj[j & 1] = w_j / r_jj
+    const zd wj = s_wj[j & 1];
+    if (tid == 0) wout[j] = wj;
+    if (STAGE && j > 0)  // column j-1 for the next step
+      for (int i = tid; i < j - 1; i += blockDim.x)
+        cp_async16(rcol + ((j - 1) & 1) * m + i, R + i + (int64_t)(j - 1) * m, 16);
+    const zd *rj = STAGE ? rcol + (j & 1) * m : R + (int64_t)j * m;
+    for (int i = tid; i < j; i += blockDim.x) {
       zd v = w[i];
       const zd a = rj[i];
       v.re = fma(-a.re, wj.re, fma(a.im, wj.im, v.re));
       v.im = fma(-a.re, wj.im, fma(-a.im, wj.re, v.im));
       w[i] = v;
+      if (i == j - 1) s_wj[i & 1] = {v.re * rinv[i], v.im * rinv[i]};
     }
+    if (STAGE) cp_async_wait_all();
   }
   __syncthreads();
-  for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+  for (int i = tid; i <= k; i += blockDim.x) {
     const zd v = wout[i];
     const int pi = piv[i];
     Wp[(int64_t)pi * m + k] = v;
@@ -1039,11 +1065,14 @@ cudaError_t launch_prinv(const void *R, const int32_t *piv, int m, void *Wp, voi
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(WpH, 0, sizeof(zd) * (size_t)m * m, st);
   if (e != cudaSuccess) return e;
-  const size_t smem = sizeof(zd) * 2 * (size_t)m;
-  e = cudaFuncSetAttribute(prinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t staged = (sizeof(zd) * 4 + sizeof(double)) * (size_t)m;
+  const bool stage = staged <= 96 * 1024;
+  const size_t smem = stage ? staged : (sizeof(zd) * 2 + sizeof(double)) * (size_t)m;
+  auto kern = stage ? prinv_kernel<true> : prinv_kernel<false>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   note_launch();
-  prinv_kernel<<<m, 128, smem, st>>>((const zd *)R, piv, m, (zd *)Wp, (zd *)WpH);
+  kern<<<m, 128, smem, st>>>((const zd *)R, piv, m, (zd *)Wp, (zd *)WpH);
   return cudaGetLastError();
 }
 
