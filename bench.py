@@ -138,6 +138,16 @@ def dist_setup(n_gpus):
     return rank, world, local, pg
 
 
+def replica_seed(rank):
+    """Seed of the system rank `rank` solves: every replica gets its own A and b."""
+    return W["seed"] + 100 * rank
+
+
+def aggregate_value(world, steps, ms_max):
+    """Whole-job solves/s: every rank solved `steps` systems; the job took the slowest rank's time."""
+    return world * steps / (ms_max / 1000.0)
+
+
 def reduce_max(pg, value, device):
     if pg is None:
         return value
@@ -210,7 +220,7 @@ def main():
 
     m, n, eps = args.m, args.n, W["eps"]
     cache = os.environ.get("MINNORM_INPUT_CACHE", os.path.join(tempfile.gettempdir(), "minnorm_inputs"))
-    s = synth.make_system(m, n, W["exponent"], W["seed"] + 100 * rank, device=str(device), cache_dir=cache)
+    s = synth.make_system(m, n, W["exponent"], replica_seed(rank), device=str(device), cache_dir=cache)
     A, b = s.A, s.b
     stream = torch.cuda.current_stream()
     prec_main = mn.MIXED if args.precision == "mixed" else mn.FP64
@@ -254,12 +264,12 @@ def main():
 
     ms_main, stats, infos, launches, clk = timed(plans["main"], args.steps, args.warmup, clocks=True)
     ms_max = reduce_max(pg, ms_main, device)
-    value = world * args.steps / (ms_max / 1000.0)
+    value = aggregate_value(world, args.steps, ms_max)
     x_main = x.clone()
     last_st, last_info = infos[-1]
     ms_other, stats_other, infos_other, _, _ = timed(plans["other"], max(3, args.steps // 2), 2)
     ms_other = reduce_max(pg, ms_other, device)
-    other_value = world * max(3, args.steps // 2) / (ms_other / 1000.0)
+    other_value = aggregate_value(world, max(3, args.steps // 2), ms_other)
     x_other = x.clone()
 
     # end to end through the public API with host buffers (pinned): H2D of A and b, D2H of x
@@ -281,7 +291,7 @@ def main():
     wall = time.perf_counter() - t0
     e2e_ms = max(f0.elapsed_time(f1), 1000 * wall)
     e2e_ms = reduce_max(pg, e2e_ms, device)
-    e2e_value = world * e2e_steps / (e2e_ms / 1000.0)
+    e2e_value = aggregate_value(world, e2e_steps, e2e_ms)
 
     for p in plans.values():
         mn.minnorm_plan_destroy(p)
