@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error check and CPU baseline")
     ap.add_argument("--m", type=int, default=W["m"], help="rows (profiling runs of a smaller case)")
     ap.add_argument("--n", type=int, default=W["n"], help="columns (profiling runs of a smaller case)")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "block"],
+                    help="plain: the benchmark line; batch / block: the batching and block right-hand-side "
+                         "workloads, measured on their own (one line each, not the benchmark line)")
     return ap.parse_args()
 
 
@@ -202,10 +205,76 @@ def reference_arm(args):
     return 0
 
 
+def side_workload(args):
+    """The batching workload (256 systems, m uniform in [32, 512], n = m k, k uniform in [8, 64],
+    complex64, sigma 1..1e-4, eps 1e-10) or the block right-hand-side workload (4096 x 131072
+    complex64, sigma 1..1e-6, 64 complex Gaussian right-hand sides, eps 1e-10), built on the GPU.
+    A step is the whole workload: every system's Steps 1-5, or one sketch + all 64 solves."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_0905_4745_gb300 import minnorm as mn
+    import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    steps, warmup = max(1, args.steps), max(1, args.warmup)
+    if args.workload == "batch":
+        shapes = synth.batch_shapes(256, seed=4000)
+        systems = [synth.make_system(m, n, exponent=4, seed=4000 + i, dtype="c64", device="cuda:0")
+                   for i, (m, n) in enumerate(shapes)]
+        batch = mn.minnorm_batch_create([m for m, _ in shapes], [n for _, n in shapes], mn.C64, mn.MIXED,
+                                        seed=4000, stream=stream)
+        xs = [torch.empty(n, dtype=torch.complex128, device=dev) for _, n in shapes]
+        As, bs = [q.A for q in systems], [q.b for q in systems]
+
+        def step():
+            return mn.minnorm_batch_solve(batch, As, bs, 1e-10, xs)
+        units, name = len(shapes), ("batching: 256 systems, m in [32, 512], n = m k, k in [8, 64], complex64, "
+                                    "sigma 1..1e-4, eps 1e-10 (mixed)")
+        hbm = sum(m * n * 8 for m, n in shapes)
+    else:
+        w = synth.WORKLOADS["c5_blockrhs_4096x131072"]
+        m, n, k = w["m"], w["n"], w["nrhs"]
+        q = synth.make_system(m, n, w["exponent"], w["seed"], dtype="c64", nrhs=k, device="cuda:0")
+        plan = mn.minnorm_plan_create(m, n, 0, mn.C64, mn.MIXED, seed=5, stream=stream)
+        B = q.b.T.contiguous().T
+        X = torch.empty((k, n), dtype=torch.complex128, device=dev).T
+
+        def step():
+            mn.minnorm_sketch(plan, q.A)
+            return mn.minnorm_solve_many(plan, q.A, B, w["eps"], X)
+        units, name = k, "block right-hand sides: 4096x131072 complex64, sigma 1..1e-6, 64 RHS, eps 1e-10 (mixed)"
+        hbm = m * n * 8
+    for _ in range(warmup):
+        step()
+    launches0 = mn.minnorm_launch_count()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    statuses = []
+    for _ in range(steps):
+        st, infos = step()
+        statuses.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    worst = max(i["err_bound"] for i in infos)
+    print(json.dumps({"metric": "solves/s (%s workload)" % args.workload, "value": units * steps / (ms / 1000.0),
+                      "unit": "solves/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
+                      "ms_per_step": ms / steps, "higher_is_better": True, "dtype": "c64 products + f64 QR/R + "
+                      "fixed-point residual", "data": "synthetic", "config": {"workload": name, "A_bytes": hbm},
+                      "status": mn.STATUS_NAMES[max(statuses)], "worst_err_bound": worst,
+                      "gpu_launches": mn.minnorm_launch_count() - launches0}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload != "plain":
+        return side_workload(args)
     import torch
     rank, world, local, pg = dist_setup(args.gpus)
     device = torch.device("cuda", local)
