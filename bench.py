@@ -32,7 +32,11 @@ METRIC = "solves/s at <=1e-10 rel. error (mixed vs plain FP64 GPU); CG matvec HB
 W = dict(m=512, n=65536, exponent=6, dtype="c128", eps=1e-12, seed=1002)
 WORKLOAD_NAME = ("512x65536 complex128, sigma 1..1e-6, complex Gaussian b, eps 1e-12, l = 4m "
                  "(plain-method workload)")
-FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor) peak, 152 SMs
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26 TFLOP/s
+# DRAM bytes (read + write) per launch of a kernel class, from one ncu capture of the current
+# kernels on this workload: class 3 = qrp_reg_kernel<16> (16.91 + 2.77 MB) + prinv_kernel<1>
+# (2.14 MB + 0.5 KB). Y (16 MiB) stays in L2 through the QR, so traffic is one read of Y.
+PROFILED_TRAFFIC = {3: 21.82e6}
 KERNEL_CLASSES = {0: "cg_adjoint_product", 1: "cg_forward_product", 2: "exact_residual", 3: "pivoted_qr",
                   4: "srft_sketch", 5: "cg_fused"}
 REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
@@ -394,9 +398,10 @@ def main():
         achieved = bytes_per / (per_launch_ms / 1000.0) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = PROFILED_TRAFFIC.get(dom) if (m, n) == (W["m"], W["n"]) else None
     roof["kernel"] = KERNEL_CLASSES[dom]
-    roof["peak_source"] = pk_kind if roof["unit"] == "GB/s" else "nominal FP64 (1.25 TFLOP/s)"
+    roof["peak_source"] = (pk_kind if roof["unit"] == "GB/s" else
+                           "FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe 1.25)")
     # CG matvec bandwidth (the metric's second half)
     if stats[5][0] > 0:     # fused CG: one pass over A per iteration
         cg_ms = stats[5][1] / stats[5][0]
