@@ -63,7 +63,7 @@ struct QrMail {
   int pad;
 };
 
-size_t qr_mail_bytes() { return 4 * (size_t)kQrMaxGrid + 2 * (size_t)kQrMaxGrid * 24; }
+size_t qr_mail_bytes() { return 4 * (size_t)kQrMaxGrid + 2 * (size_t)kQrMaxGrid * 24 + 8 * (size_t)kQrMaxGrid; }
 
 __device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -464,6 +464,7 @@ constexpr int kQrNoPos = 0x3FFF;
 struct QrPosts {
   unsigned long long *wa, *wb;  // [2][kQrMaxGrid] tagged words
   double *xn2;                  // [2][kQrMaxGrid] the candidate's ||Y[k+2:, j]||^2
+  unsigned long long *smw;      // [kQrMaxGrid] 2^40 | SM id of each CTA, posted once at launch
 };
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
@@ -739,7 +740,8 @@ __device__ __forceinline__ void qr_reg_step(zd *Y, const int l, const int k, con
 template <int RPT>
 __global__ void __launch_bounds__(kQrRegThreads, 2)
 qrp_reg_kernel(zd *Y, int l, int m, double *vnA, double *vnB, double *vn2, double *__restrict__ beta,
-               int32_t *__restrict__ piv, zd *__restrict__ Rout, QrPosts P, int *err, uint64_t limit_ns) {
+               int32_t *__restrict__ piv, zd *__restrict__ Rout, QrPosts P, int *err, uint64_t limit_ns,
+               int npair) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   zd *spiv = reinterpret_cast<zd *>(smem_raw);                         // RPT x 128 pivot rows, then 2 own columns
   int *perm = reinterpret_cast<int *>(spiv + 3 * RPT * kQrRowThreads); // logical -> physical
@@ -749,6 +751,41 @@ qrp_reg_kernel(zd *Y, int l, int m, double *vnA, double *vnB, double *vn2, doubl
   constexpr int NW = kQrRegThreads / 32;
   const double tol3z = sqrt(0x1.0p-53);
   for (int j = tid; j < m; j += blockDim.x) perm[j] = j;
+
+  // with two CTAs on every SM (npair > 0), find this CTA's SM rank among the SMs and whether it
+  // is the SM's second CTA: every CTA posts its SM id, waits for all, and ranks its own
+  int sm_rank = 0, sm_half = 0;
+  if (npair > 0) {
+    unsigned int mysm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(mysm));
+    if (tid == 0) st_relaxed_u64(P.smw + b, (1ull << 40) | mysm);
+    int less = 0, before = 0, fail = 0;
+    for (int c = tid; c < G; c += blockDim.x) {
+      unsigned long long wv = ld_relaxed_u64(P.smw + c);
+      if ((wv >> 40) != 1ull) {
+        const uint64_t t0 = global_ns();
+        while (((wv = ld_relaxed_u64(P.smw + c)) >> 40) != 1ull) {
+          if (ld_volatile_i32(err)) { fail = 1; break; }
+          if (global_ns() - t0 > limit_ns) { atomicExch(err, 1); fail = 1; break; }
+        }
+      }
+      if (fail) break;
+      const unsigned int sm = (unsigned int)(wv & 0xFFFFFFFFull);
+      less += sm < mysm;
+      before += (sm == mysm && c < b);
+    }
+    less = __reduce_add_sync(0xffffffffu, less);
+    before = __reduce_add_sync(0xffffffffu, before);
+    fail = __reduce_or_sync(0xffffffffu, fail);
+    if (lane == 0) { S.pos[wid] = less; S.cta[wid] = before; S.fail[wid] = fail; }
+    __syncthreads();
+    int l_all = 0, b_all = 0, f_all = 0;
+    for (int w = 0; w < NW; ++w) { l_all += S.pos[w]; b_all += S.cta[w]; f_all |= S.fail[w]; }
+    if (f_all) return;
+    sm_rank = l_all / 2;
+    sm_half = b_all;
+    __syncthreads();
+  }
 
   // pivot of step 0 and its ||Y[1:, p]||^2 (every CTA)
   {
@@ -784,8 +821,19 @@ qrp_reg_kernel(zd *Y, int l, int m, double *vnA, double *vnB, double *vn2, doubl
     double *vn_nxt = (k & 1) ? vnA : vnB;
     const double xn2 = (k == 0) ? S.xn2_0 : ldcg(P.xn2 + ((k - 1) & 1) * kQrMaxGrid + win);
     const int T = m - k - 1;
-    const int q0 = k + 1 + (int)(((long long)T * b) / G), q1 = k + 1 + (int)(((long long)T * (b + 1)) / G);
-    const int nact = q1 - q0;
+    int q0, nact;
+    if (npair > 0) {
+      // shares per SM first, then halved between the SM's two CTAs: no SM holds more than
+      // ceil(T / npair) columns
+      const int sm = sm_rank, half = sm_half;
+      const int a0 = (int)(((long long)T * sm) / npair), a1 = (int)(((long long)T * (sm + 1)) / npair);
+      const int c0 = (a1 - a0 + 1) / 2;
+      q0 = k + 1 + a0 + (half ? c0 : 0);
+      nact = half ? (a1 - a0 - c0) : c0;
+    } else {
+      q0 = k + 1 + (int)(((long long)T * b) / G);
+      nact = k + 1 + (int)(((long long)T * (b + 1)) / G) - q0;
+    }
     const int slot = (k & 1) * kQrMaxGrid + b;
     if (nact == 0) {
       qr_reg_step<0, RPT>(Y, l, k, G, b, perm, q0, vn_cur, vn_nxt, vn2, beta, spiv, S, P, slot, xn2, tol3z);
@@ -903,7 +951,9 @@ static cudaError_t try_qrp_reg(const QrArgs &a, int sms, cudaStream_t st, bool &
   int G = 2 * sms;
   if (G > kQrMaxGrid) G = kQrMaxGrid;
   if (G > a.m) G = a.m;
-  if ((a.m - 1 + G - 1) / G > 2) return cudaSuccess;
+  // widest share: ceil(T / G) columns, or with SM pairing half of ceil(T / sms), rounded up
+  const int widest = (G == 2 * sms) ? ((a.m - 1 + sms - 1) / sms + 1) / 2 : (a.m - 1 + G - 1) / G;
+  if (widest > 2) return cudaSuccess;
   zd *Y = (zd *)a.Y;
   double *vnB = a.vn1 + a.m;
   int l = a.l, m = a.m;
@@ -913,9 +963,12 @@ static cudaError_t try_qrp_reg(const QrArgs &a, int sms, cudaStream_t st, bool &
   posts.wa = (unsigned long long *)pbase;
   posts.wb = posts.wa + 2 * kQrMaxGrid;
   posts.xn2 = (double *)(posts.wb + 2 * kQrMaxGrid);
+  posts.smw = (unsigned long long *)(posts.xn2 + 2 * kQrMaxGrid);
   uint64_t lim = a.limit_ns;
+  // two CTAs on every SM (G co-resident CTAs, at most two per SM): shares are balanced per SM
+  int npair = (G == 2 * sms) ? sms : 0;
   void *args[] = {&Y, &l, &m, (void *)&a.vn1, &vnB, (void *)&a.vn2, (void *)&a.beta, (void *)&a.piv,
-                  &R, &posts, (void *)&a.err, &lim};
+                  &R, &posts, (void *)&a.err, &lim, &npair};
   note_launch();
   launched = true;
   return cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(kQrRegThreads), args, smem, st);

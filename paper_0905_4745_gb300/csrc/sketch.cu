@@ -103,12 +103,29 @@ chain_kernel(const S *__restrict__ src, int64_t ld_src, cx<R> *__restrict__ dst,
   const int cnt = E - lo;
   const S *srow = src + row * ld_src;
 
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-    const int j = lo + t;
-    const S a = srow[idx[j]];
-    const cx<R> v = {R(a.re), CONJ ? -R(a.im) : R(a.im)};
-    V[t] = v * phase[j];
-    CS[t] = cs[j];
+  // the gather is latency-bound: issue the index loads, then the gathered loads, of several
+  // elements per thread before using any of them
+  constexpr int kG = 8;
+  for (int t0 = threadIdx.x; t0 < cnt; t0 += kG * blockDim.x) {
+    int ix[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+      const int t = t0 + g * blockDim.x;
+      ix[g] = t < cnt ? idx[lo + t] : 0;
+    }
+    S a[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) a[g] = srow[ix[g]];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+      const int t = t0 + g * blockDim.x;
+      if (t < cnt) {
+        const int j = lo + t;
+        const cx<R> v = {R(a[g].re), CONJ ? -R(a[g].im) : R(a[g].im)};
+        V[t] = v * phase[j];
+        CS[t] = cs[j];
+      }
+    }
   }
   __syncthreads();
 
@@ -152,7 +169,7 @@ __device__ __forceinline__ int bitrev(int j, int logL) {
 // sequences of length L = 2^logL stored in bit-reversed order; twiddles
 // e^{-2 pi i k / NT} from the table tw (L divides NT).
 template <typename R>
-__device__ __forceinline__ void smem_fft(cx<R> *data, int B, int logL, const cx<R> *__restrict__ tw,
+__device__ __forceinline__ void smem_fft(cx<R> *data, int B, int logL, int stride, const cx<R> *__restrict__ tw,
                                          int logNT) {
   const int L = 1 << logL;
   const int halfL = L >> 1;
@@ -165,7 +182,7 @@ __device__ __forceinline__ void smem_fft(cx<R> *data, int B, int logL, const cx<
       const int bb = b & (halfL - 1);
       const int k = bb & (h - 1);
       const int pos = ((bb >> lh) << (lh + 1)) + k;
-      cx<R> *d = data + seqi * L;
+      cx<R> *d = data + seqi * stride;
       const cx<R> w = tw[k << twshift];
       const cx<R> u = d[pos];
       const cx<R> v = d[pos + h] * w;
@@ -209,7 +226,7 @@ fft_row_kernel(const cx<R> *__restrict__ src, int64_t ld_src, int logn, const cx
   const cx<R> *s = src + row * ld_src;
   for (int j = threadIdx.x; j < n; j += blockDim.x) data[bitrev(j, logn)] = fft_in(s, j, chirp, nin);
   __syncthreads();
-  smem_fft<R>(data, 1, logn, tw, logn);
+  smem_fft<R>(data, 1, logn, n, tw, logn);
   if (full) {
     cx<R> *f = full + row * ldf;
     for (int k = threadIdx.x; k < n; k += blockDim.x) f[k] = conjg(data[k] * bh[k]);
@@ -237,16 +254,16 @@ fft_pass_a_kernel(const cx<R> *__restrict__ src, int64_t ld, cx<R> *__restrict__
   const int total = tj * N2;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int jj = e % tj, j2 = e / tj;
-    data[jj * N2 + bitrev(j2, logN2)] = fft_in(s, (j1_0 + jj) + (int64_t)N1 * j2, chirp, nin);
+    data[jj * (N2 + 1) + bitrev(j2, logN2)] = fft_in(s, (j1_0 + jj) + (int64_t)N1 * j2, chirp, nin);
   }
   __syncthreads();
-  smem_fft<R>(data, tj, logN2, tw, logn);
+  smem_fft<R>(data, tj, logN2, N2 + 1, tw, logn);
   cx<R> *w = W + row * ldw;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int jj = e % tj, k2 = e / tj;
     const int j1 = j1_0 + jj;
     const int64_t tix = ((int64_t)j1 * k2) & (n - 1);
-    w[(int64_t)k2 * N1 + j1] = data[jj * N2 + k2] * tw[tix];
+    w[(int64_t)k2 * N1 + j1] = data[jj * (N2 + 1) + k2] * tw[tix];
   }
 }
 
@@ -268,18 +285,18 @@ fft_pass_b_kernel(const cx<R> *__restrict__ W, int64_t ldw, int logn, int logN1,
   const int total = tk * N1;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int kk = e >> logN1, j1 = e & (N1 - 1);
-    data[kk * N1 + bitrev(j1, logN1)] = w[e];
+    data[kk * (N1 + 1) + bitrev(j1, logN1)] = w[e];
   }
   __syncthreads();
-  smem_fft<R>(data, tk, logN1, tw, logn);
+  smem_fft<R>(data, tk, logN1, N1 + 1, tw, logn);
   if (full) {
-    // X[N2 k1 + k2] for k2 = k2_0 + kk sits at data[kk N1 + k1]; runs of tk consecutive outputs
+    // X[N2 k1 + k2] for k2 = k2_0 + kk sits at data[kk (N1 + 1) + k1]; runs of tk consecutive outputs
     const int N2 = 1 << (logn - logN1);
     cx<R> *f = full + row * ldf;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int k1 = e / tk, kk = e - k1 * tk;
       const int64_t K = (int64_t)N2 * k1 + k2_0 + kk;
-      f[K] = conjg(data[kk * N1 + k1] * bh[K]);
+      f[K] = conjg(data[kk * (N1 + 1) + k1] * bh[K]);
     }
     return;
   }
@@ -359,8 +376,10 @@ static cudaError_t launch_fft_t(const FftArgs &a, cudaStream_t st) {
     return cudaGetLastError();
   }
   const int N1 = 1 << a.logN1, N2 = 1 << (a.logn - a.logN1);
-  const size_t smemA = sizeof(cx<R>) * (size_t)a.tj * N2;
-  const size_t smemB = sizeof(cx<R>) * (size_t)a.tk * N1;
+  // sequences padded by one element: the strided transposes into and out of shared memory
+  // then touch distinct banks
+  const size_t smemA = sizeof(cx<R>) * (size_t)a.tj * (N2 + 1);
+  const size_t smemB = sizeof(cx<R>) * (size_t)a.tk * (N1 + 1);
   e = cudaFuncSetAttribute(fft_pass_a_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemA);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(fft_pass_b_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemB);

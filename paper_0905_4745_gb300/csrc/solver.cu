@@ -300,7 +300,7 @@ minnorm_status upload_params(minnorm_plan_t plan) {
       const int64_t k = P.s[t], k2 = k % N2, k1 = k / N2, b = k2 / plan->tk, kk = k2 - b * plan->tk;
       const int32_t pos = fill[b]++;
       st_t[pos] = (int32_t)t;
-      st_loc[pos] = (int32_t)(kk * N1 + k1);
+      st_loc[pos] = (int32_t)(kk * (N1 + 1) + k1);  // pass B's sequences are padded by one element
     }
   }
   CK(cudaMemcpy(plan->d_samp_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice));
