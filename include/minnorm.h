@@ -204,6 +204,12 @@ minnorm_status minnorm_batch_create(minnorm_batch_t *batch, int32_t count, const
 minnorm_status minnorm_batch_solve(minnorm_batch_t batch, const void *const *A, const int64_t *lda,
                                    const void *const *b, double eps, void *const *x, minnorm_info *infos);
 
+/* minnorm_kernel_stats for system `system` of a batch created with
+ * MINNORM_FLAG_TIMING, or summed over all systems when system = -1 (each
+ * system's counts cover its last Steps 1-5). Errors: EINVAL. */
+minnorm_status minnorm_batch_kernel_stats(minnorm_batch_t batch, int32_t system, int32_t k, int32_t *launches,
+                                          double *ms);
+
 /* Free the batch, its plans and the shared scratch. NULL is accepted. */
 minnorm_status minnorm_batch_destroy(minnorm_batch_t batch);
 

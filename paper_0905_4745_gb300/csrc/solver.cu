@@ -78,6 +78,8 @@ struct minnorm_plan_s {
   bool bluestein = false;                    // n not a power of two: L >= 2n - 1
   void *d_chirp = nullptr, *d_bhat = nullptr;  // Bluestein tables (compute precision)
   double *d_fac = nullptr;                   // l complex128: c_{s_t} / sqrt(n)
+  cudaEvent_t ev_sk0 = nullptr, ev_sk1 = nullptr, ev_sk2 = nullptr;  // sketch / QR timing events
+  double *h_qr = nullptr;                    // pinned: QR error word, |R_11|, |R_mm| of the last sketch
   int cap1 = 0, cap2 = 0;
   int32_t *d_idx1 = nullptr, *d_idx2 = nullptr, *d_halo1 = nullptr, *d_halo2 = nullptr;
   void *d_ph1 = nullptr, *d_ph2 = nullptr, *d_cs1 = nullptr, *d_cs2 = nullptr, *d_post = nullptr, *d_tw = nullptr;
@@ -451,20 +453,22 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   }
   if (cudaMallocHost(&plan->h_norms, sizeof(double) * 4) != cudaSuccess) return MINNORM_ENOMEM;
   if (cudaMallocHost(&plan->h_cg, sizeof(CgScalars)) != cudaSuccess) return MINNORM_ENOMEM;
+  if (cudaMallocHost(&plan->h_qr, sizeof(double) * 3) != cudaSuccess) return MINNORM_ENOMEM;
   draw_srft_params(seed, n, l, plan->P);
   return upload_params(plan);
 }
 
-// ---- Step 1 + Step 2 --------------------------------------------------------
-minnorm_status sketch_impl(minnorm_plan_t plan, const void *A, int64_t lda) {
+// Step 1 on the plan's stream: the fixed-point (and complex64) copies of A, then Y = T A^*.
+minnorm_status sketch_transform(minnorm_plan_t plan, const void *A, int64_t lda) {
   cudaStream_t st = plan->st;
   const int64_t m = plan->m, n = plan->n, l = plan->l;
-  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   const bool timing = plan->flags & MINNORM_FLAG_TIMING;
   reset_stats(plan);
+  plan->sketched = false;
   if (timing) {
-    e0 = next_event(plan); e1 = next_event(plan); e2 = next_event(plan);
-    CK(cudaEventRecord(e0, st));
+    plan->ev_sk0 = next_event(plan);
+    plan->ev_sk1 = next_event(plan);
+    CK(cudaEventRecord(plan->ev_sk0, st));
   }
   const void *src = A;
   int64_t lds = lda;
@@ -529,7 +533,15 @@ minnorm_status sketch_impl(minnorm_plan_t plan, const void *A, int64_t lda) {
     }
   }
   if (plan->d_Ykeep) CK(cudaMemcpyAsync(plan->d_Ykeep, plan->d_Y, sizeof(zd) * l * m, cudaMemcpyDeviceToDevice, st));
-  if (timing) CK(cudaEventRecord(e1, st));
+  if (timing) CK(cudaEventRecord(plan->ev_sk1, st));
+  return MINNORM_OK;
+}
+
+// Step 2 on the plan's stream: pivoted QR of Y, then P R^{-1}; the status words are copied
+// to pinned host memory (read by sketch_finish after the stream has reached them).
+minnorm_status sketch_factor(minnorm_plan_t plan) {
+  cudaStream_t st = plan->st;
+  const int64_t m = plan->m, l = plan->l;
   {
     Timed tm(plan, 3);
     CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
@@ -538,18 +550,29 @@ minnorm_status sketch_impl(minnorm_plan_t plan, const void *A, int64_t lda) {
     CK(launch_qrp(q, st));
     CK(launch_prinv(plan->d_R, plan->d_piv, (int)m, plan->d_Wp, plan->d_WpH, st));
   }
-  if (timing) CK(cudaEventRecord(e2, st));
-  int err = 0;
-  double b0 = 0, bm = 0;
-  CK(cudaMemcpyAsync(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(&b0, plan->d_beta, sizeof(double), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(&bm, plan->d_beta + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  if (timing) {
-    cudaEventElapsedTime(&plan->ms_sketch, e0, e1);
-    cudaEventElapsedTime(&plan->ms_qr, e1, e2);
+  if (plan->flags & MINNORM_FLAG_TIMING) {
+    plan->ev_sk2 = next_event(plan);
+    CK(cudaEventRecord(plan->ev_sk2, st));
+  }
+  CK(cudaMemcpyAsync(&plan->h_qr[0], plan->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&plan->h_qr[1], plan->d_beta, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&plan->h_qr[2], plan->d_beta + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
+  return MINNORM_OK;
+}
+
+// After the stream has passed sketch_factor: timings, the QR's status and the rank test.
+minnorm_status sketch_finish(minnorm_plan_t plan) {
+  CK(cudaStreamSynchronize(plan->st));
+  if (plan->flags & MINNORM_FLAG_TIMING) {
+    cudaEventElapsedTime(&plan->ms_sketch, plan->ev_sk0, plan->ev_sk1);
+    cudaEventElapsedTime(&plan->ms_qr, plan->ev_sk1, plan->ev_sk2);
     collect_timers(plan);
   }
+  int err = 0;
+  double b0 = 0, bm = 0;
+  memcpy(&err, &plan->h_qr[0], sizeof(int));
+  memcpy(&b0, &plan->h_qr[1], sizeof(double));
+  memcpy(&bm, &plan->h_qr[2], sizeof(double));
   if (err) {
     plan->failed = true;
     return MINNORM_ETIMEOUT;
@@ -557,8 +580,17 @@ minnorm_status sketch_impl(minnorm_plan_t plan, const void *A, int64_t lda) {
   plan->rdiag_max = std::fabs(b0);
   plan->rdiag_min = std::fabs(bm);
   plan->sketched = true;
-  if (!(plan->rdiag_min > 64.0 * (double)m * 0x1.0p-53 * plan->rdiag_max)) return MINNORM_ERANK;
+  if (!(plan->rdiag_min > 64.0 * (double)plan->m * 0x1.0p-53 * plan->rdiag_max)) return MINNORM_ERANK;
   return MINNORM_OK;
+}
+
+// ---- Step 1 + Step 2 --------------------------------------------------------
+minnorm_status sketch_impl(minnorm_plan_t plan, const void *A, int64_t lda) {
+  minnorm_status s = sketch_transform(plan, A, lda);
+  if (s != MINNORM_OK) return s;
+  s = sketch_factor(plan);
+  if (s != MINNORM_OK) return s;
+  return sketch_finish(plan);
 }
 
 // ---- Steps 3-5 --------------------------------------------------------------
@@ -929,6 +961,7 @@ minnorm_status minnorm_plan_destroy(minnorm_plan_t plan) {
   for (cudaEvent_t e : plan->event_pool) cudaEventDestroy(e);
   if (plan->h_norms) cudaFreeHost(plan->h_norms);
   if (plan->h_cg) cudaFreeHost(plan->h_cg);
+  if (plan->h_qr) cudaFreeHost(plan->h_qr);
   delete plan;
   return MINNORM_OK;
 }
@@ -1012,11 +1045,21 @@ struct minnorm_batch_s {
   std::vector<minnorm_plan_t> plans;
   ScratchPool pool;
   std::vector<void *> allocs;
+  cudaStream_t st = nullptr;                // the batch's stream
+  std::vector<cudaStream_t> side;           // streams the systems' QRs are spread over
+  std::vector<cudaEvent_t> ev;              // one per side stream, plus one for the batch stream
 };
+
+static constexpr int kBatchSideStreams = 8;
 
 minnorm_status minnorm_batch_destroy(minnorm_batch_t batch) {
   if (!batch) return MINNORM_OK;
   for (minnorm_plan_t p : batch->plans) minnorm_plan_destroy(p);  // synchronizes the stream
+  for (cudaStream_t s : batch->side) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  for (cudaEvent_t e : batch->ev) cudaEventDestroy(e);
   for (void *p : batch->allocs) cudaFree(p);
   delete batch;
   return MINNORM_OK;
@@ -1057,6 +1100,22 @@ minnorm_status minnorm_batch_create(minnorm_batch_t *out, int32_t count, const i
   b->pool.s_bytes = sb;
   b->pool.afix_bytes = ab;
   b->pool.a32_bytes = a32;
+  b->st = (cudaStream_t)stream;
+  for (int i = 0; i < kBatchSideStreams + 1; ++i) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      minnorm_batch_destroy(b);
+      return MINNORM_ECUDA;
+    }
+    b->ev.push_back(e);
+    if (i == kBatchSideStreams) break;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      minnorm_batch_destroy(b);
+      return MINNORM_ECUDA;
+    }
+    b->side.push_back(s);
+  }
   b->plans.reserve(count);
   for (int32_t i = 0; i < count; ++i) {
     minnorm_plan_t p = nullptr;
@@ -1076,23 +1135,99 @@ minnorm_status minnorm_batch_solve(minnorm_batch_t batch, const void *const *A, 
                                    const void *const *b, double eps, void *const *x, minnorm_info *infos) {
   if (!batch || !A || !b || !x) return MINNORM_EINVAL;
   if (!(eps > 0.0 && eps < 1.0)) return MINNORM_EINVAL;
-  minnorm_status first = MINNORM_OK;
-  for (size_t i = 0; i < batch->plans.size(); ++i) {
+  const size_t N = batch->plans.size();
+  for (size_t i = 0; i < N; ++i) {
+    const minnorm_plan_t p = batch->plans[i];
+    const int64_t ld = lda ? lda[i] : p->n;
+    if (!A[i] || !b[i] || !x[i] || ld < p->n) return MINNORM_EINVAL;
+    if (!aligned16(A[i]) && p->dtype == MINNORM_C128) return MINNORM_EINVAL;
+    if (p->failed) return MINNORM_ESTATE;
+  }
+#define BCK(expr)                                                    \
+  do {                                                               \
+    if ((expr) != cudaSuccess) {                                     \
+      for (minnorm_plan_t q_ : batch->plans) {                       \
+        q_->st = batch->st;                                          \
+        q_->failed = true;                                           \
+      }                                                              \
+      return MINNORM_ECUDA;                                          \
+    }                                                                \
+  } while (0)
+  auto fatal = [](minnorm_status s) {
+    return s == MINNORM_EINVAL || s == MINNORM_ECUDA || s == MINNORM_ETIMEOUT || s == MINNORM_ESTATE ||
+           s == MINNORM_ENOMEM;
+  };
+  std::vector<minnorm_status> st(N, MINNORM_OK);
+  // 1. Step 1 of every system, in turn on the batch stream (the shared pool holds a system's
+  //    transform buffers only while its Step 1 runs; Y is the system's own)
+  for (size_t i = 0; i < N; ++i) {
     minnorm_plan_t p = batch->plans[i];
     const int64_t ld = lda ? lda[i] : p->n;
-    minnorm_status s = minnorm_sketch(p, A[i], ld);
+    p->g_hp.ld = ld;
+    p->g_cg.ld = p->d_A32 ? p->n : ld;
+    const minnorm_status s = sketch_transform(p, A[i], ld);
+    if (s != MINNORM_OK) return s;
+  }
+  // 2. Step 2 of every system, spread over the side streams: the QRs are latency-bound
+  //    cooperative grids on per-system buffers, so those of different systems overlap
+  BCK(cudaEventRecord(batch->ev.back(), batch->st));
+  for (cudaStream_t s : batch->side) BCK(cudaStreamWaitEvent(s, batch->ev.back(), 0));
+  for (size_t i = 0; i < N; ++i) {
+    minnorm_plan_t p = batch->plans[i];
+    p->st = batch->side[i % batch->side.size()];
+    const minnorm_status s = sketch_factor(p);
+    if (s != MINNORM_OK) {
+      for (minnorm_plan_t q : batch->plans) q->st = batch->st;
+      return s;
+    }
+  }
+  for (size_t k = 0; k < batch->side.size(); ++k) {
+    BCK(cudaEventRecord(batch->ev[k], batch->side[k]));
+    BCK(cudaStreamWaitEvent(batch->st, batch->ev[k], 0));
+  }
+  for (minnorm_plan_t p : batch->plans) p->st = batch->st;
+  for (size_t i = 0; i < N; ++i) {
+    st[i] = sketch_finish(batch->plans[i]);
+    if (fatal(st[i])) return st[i];
+  }
+  // 3. Steps 3-5 of every system, in turn; the pooled fixed-point (and complex64) copy of A is
+  //    rebuilt first, since later systems' Step 1 overwrote it
+  minnorm_status first = MINNORM_OK;
+  for (size_t i = 0; i < N; ++i) {
+    minnorm_plan_t p = batch->plans[i];
+    const int64_t ld = lda ? lda[i] : p->n;
+    minnorm_status s = st[i];
     if (s == MINNORM_OK) {
+      BCK(launch_fix_prep(A[i], ld, p->dtype == MINNORM_C64, p->m, p->n, p->d_afix, p->d_E, p->d_A32, p->st));
       s = minnorm_solve(p, A[i], ld, b[i], eps, x[i], infos ? infos + i : nullptr);
     } else if (infos) {
       memset(infos + i, 0, sizeof(minnorm_info));
       infos[i].status = s;
     }
-    if (s == MINNORM_EINVAL || s == MINNORM_ECUDA || s == MINNORM_ETIMEOUT || s == MINNORM_ESTATE ||
-        s == MINNORM_ENOMEM)
-      return s;
+    if (fatal(s)) return s;
     if (s != MINNORM_OK && first == MINNORM_OK) first = s;
   }
   return first;
+}
+#undef BCK
+
+minnorm_status minnorm_batch_kernel_stats(minnorm_batch_t batch, int32_t system, int32_t k, int32_t *launches,
+                                          double *ms) {
+  if (!batch || !launches || !ms || k < 0 || k > 5) return MINNORM_EINVAL;
+  if (system < -1 || system >= (int32_t)batch->plans.size()) return MINNORM_EINVAL;
+  int32_t nl = 0;
+  double t = 0.0;
+  for (int32_t i = 0; i < (int32_t)batch->plans.size(); ++i) {
+    if (system >= 0 && i != system) continue;
+    int32_t a = 0;
+    double b = 0.0;
+    minnorm_kernel_stats(batch->plans[i], k, &a, &b);
+    nl += a;
+    t += b;
+  }
+  *launches = nl;
+  *ms = t;
+  return MINNORM_OK;
 }
 
 }  // extern "C"

@@ -24,7 +24,7 @@ EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_sketch", "
            "minnorm_solve_host", "minnorm_plan_destroy", "minnorm_status_string", "minnorm_get_sketch",
            "minnorm_get_factor", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats",
            "minnorm_launch_count", "minnorm_qr_noalloc", "minnorm_solve_many", "minnorm_batch_create",
-           "minnorm_batch_solve", "minnorm_batch_destroy"]
+           "minnorm_batch_solve", "minnorm_batch_destroy", "minnorm_batch_kernel_stats"]
 
 
 class MinnormError(RuntimeError):
@@ -65,6 +65,7 @@ def lib():
         L.minnorm_batch_solve.argtypes = [p, C.POINTER(p), C.POINTER(i64), C.POINTER(p), d, C.POINTER(p),
                                           C.POINTER(Info)]
         L.minnorm_batch_destroy.argtypes = [p]
+        L.minnorm_batch_kernel_stats.argtypes = [p, i32, i32, C.POINTER(i32), C.POINTER(d)]
         L.minnorm_plan_destroy.argtypes = [p]
         L.minnorm_status_string.argtypes = [C.c_int]
         L.minnorm_status_string.restype = C.c_char_p
@@ -187,6 +188,14 @@ def minnorm_batch_solve(batch, As, bs, eps, xs, ldas=None, info=True, allow=(OK,
     st = lib().minnorm_batch_solve(batch, pa, pl, pb, float(eps), px, infos)
     _check(st, "minnorm_batch_solve", allow)
     return st, ([i.as_dict() for i in infos] if infos is not None else None)
+
+
+def minnorm_batch_kernel_stats(batch, system, k):
+    n = C.c_int32()
+    ms = C.c_double()
+    _check(lib().minnorm_batch_kernel_stats(batch, int(system), int(k), C.byref(n), C.byref(ms)),
+           "minnorm_batch_kernel_stats")
+    return n.value, ms.value
 
 
 def minnorm_batch_destroy(batch):
