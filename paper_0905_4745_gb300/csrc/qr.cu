@@ -455,9 +455,8 @@ qrp_mail_kernel(zd *Y, int l, int m, double *vnA, double *vnB, double *vn2, doub
 //   wb = tag | low 31 bits of the norm's bit pattern
 // (a non-negative double has a zero sign bit). The writer fences before the
 // tagged stores (release); a reader fences after seeing all tags (acquire).
-constexpr int kQrRowThreads = 128;
-constexpr int kQrRegThreads = kQrRowThreads + 32;
 constexpr int kQrNoPos = 0x3FFF;
+constexpr bool kQrWide = false;  // the one-CTA-per-SM tile (256 row threads): measured no faster
 
 // posts, one entry per CTA and step parity, in three dense arrays (a poll of
 // all CTAs reads few cache lines)
@@ -484,15 +483,29 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-// Warp sums of K = 2 or 4 values with a transposed butterfly: each level
+// Warp sums of K = 2, 4 or 8 values with a transposed butterfly: each level
 // sends half of the values still held and adds the other half, so a lane
 // issues K - 1 + 5 - log2(K) additions instead of 5 K. Afterwards lane
 // L holds the sum of v[L / (32 / K)] when L is a multiple of 32 / K.
 template <int K>
 __device__ __forceinline__ double warp_sum_t(const double (&v)[K], int lane) {
-  static_assert(K == 2 || K == 4, "K");
+  static_assert(K == 2 || K == 4 || K == 8, "K");
   double z;
-  if (K == 4) {
+  if (K == 8) {
+    // level 16: keep v[0..3] (lanes 0-15) or v[4..7]; level 8: keep two of them; level 4: one
+    const bool lo = !(lane & 16);
+    double w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double keep = lo ? v[q % K] : v[(q + 4) % K], send = lo ? v[(q + 4) % K] : v[q % K];
+      w[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    const bool lo2 = !(lane & 8);
+    const double u0 = (lo2 ? w[0] : w[2]) + __shfl_xor_sync(0xffffffffu, lo2 ? w[2] : w[0], 8);
+    const double u1 = (lo2 ? w[1] : w[3]) + __shfl_xor_sync(0xffffffffu, lo2 ? w[3] : w[1], 8);
+    const bool lo3 = !(lane & 4);
+    z = (lo3 ? u0 : u1) + __shfl_xor_sync(0xffffffffu, lo3 ? u1 : u0, 4);
+  } else if (K == 4) {
     const bool lo = !(lane & 16);
     const double s0 = lo ? v[2 % K] : v[0], s1 = lo ? v[3 % K] : v[1 % K];
     const double w0 = (lo ? v[0] : v[2 % K]) + __shfl_xor_sync(0xffffffffu, s0, 16);
@@ -512,53 +525,53 @@ __device__ __forceinline__ double warp_sum_t(const double (&v)[K], int lane) {
 }
 
 struct QrRegShared {
-  double red[4 * 4];     // row-warp partial sums
-  double nv[2];          // new partial norms of the own columns
-  double from[2];        // slow path: ||Y[k+2:, j]||^2 of the own columns
-  double scratch[8];
-  zd g[2];               // factors of the own columns
-  int fl[2];             // own column needs its norm recomputed
+  double red[8 * 8];     // row-warp partial sums (up to 8 row warps x 8 values)
+  double nv[4];          // new partial norms of the own columns
+  double from[4];        // slow path: ||Y[k+2:, j]||^2 of the own columns
+  double scratch[16];
+  zd g[4];               // factors of the own columns
+  int fl[4];             // own column needs its norm recomputed
   int cand;              // own column posted (-1: decided after the update)
-  long long key[5];
-  int pos[5], cta[5], fail[5];
+  long long key[9];
+  int pos[9], cta[9], fail[9];
   int win, abort_;
   double xn2_0;
 };
 
 // one step for a CTA that owns NC trailing columns (positions q0..q0+NC-1)
-template <int NC, int RPT>
+template <int NC, int RPT, int ROWT>
 __device__ __forceinline__ void qr_reg_step(zd *Y, const int l, const int k, const int G, const int b,
                                             const int *perm, const int q0, const double *vn_cur, double *vn_nxt,
                                             double *vn2, double *beta, zd *spiv, QrRegShared &S, QrPosts P,
                                             const int slot, const double xn2, const double tol3z) {
   constexpr int NCV = NC > 0 ? NC : 1;
-  constexpr int K = 2 * NCV;
+  constexpr int K = 2 * NCV <= 2 ? 2 : (2 * NCV <= 4 ? 4 : 8);  // partial sums, padded to a power of two
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const bool rowt = tid < kQrRowThreads;
+  const bool rowt = tid < ROWT;
   const int p = perm[k];
   const zd *yp = Y + (int64_t)p * l;
   zd *cp[NCV];
 #pragma unroll
   for (int c = 0; c < NC; ++c) cp[c] = Y + (int64_t)perm[q0 + c] * l;
-  zd *sy = spiv + RPT * kQrRowThreads;  // own columns: sy[c * RPT * 128 + i * 128 + tid]
-  constexpr int CS = RPT * kQrRowThreads;
+  zd *sy = spiv + RPT * ROWT;  // own columns: sy[c * RPT * 128 + i * 128 + tid]
+  constexpr int CS = RPT * ROWT;
   zd tau = {0.0, 0.0}, scale = {0.0, 0.0}, yk = {0.0, 0.0};
   double v1 = 0.0, v2 = 1.0;
 
   // rows of this thread: k + 1 + tid + i * 128 for i < ni (loops stop there: on
   // GB300 an FP64 instruction costs its pipe time even when predicated off)
   const int rem = l - (k + 1) - tid;
-  const int ni = rem > 0 ? (rem + kQrRowThreads - 1) / kQrRowThreads : 0;
+  const int ni = rem > 0 ? (rem + ROWT - 1) / ROWT : 0;
 
   // 1. dot products (row warps) while the scalar warp forms the reflector
   if (rowt) {
     if (NC > 0) {
 #pragma unroll 4
       for (int i = 0; i < ni; ++i) {
-        const int r = k + 1 + tid + i * kQrRowThreads;
-        cp_async16(spiv + i * kQrRowThreads + tid, yp + r, 16);
+        const int r = k + 1 + tid + i * ROWT;
+        cp_async16(spiv + i * ROWT + tid, yp + r, 16);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) cp_async16(sy + c * CS + i * kQrRowThreads + tid, cp[c] + r, 16);
+        for (int c = 0; c < NC; ++c) cp_async16(sy + c * CS + i * ROWT + tid, cp[c] + r, 16);
       }
       cp_async_wait_all();
       double part[K];
@@ -566,10 +579,10 @@ __device__ __forceinline__ void qr_reg_step(zd *Y, const int l, const int k, con
       for (int c = 0; c < K; ++c) part[c] = 0.0;
 #pragma unroll 4
       for (int i = 0; i < ni; ++i) {
-        const zd a = spiv[i * kQrRowThreads + tid];
+        const zd a = spiv[i * ROWT + tid];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          const zd yv = sy[c * CS + i * kQrRowThreads + tid];
+          const zd yv = sy[c * CS + i * ROWT + tid];
           part[2 * c] = fma(a.re, yv.re, fma(a.im, yv.im, part[2 * c]));
           part[2 * c + 1] = fma(a.re, yv.im, fma(-a.im, yv.re, part[2 * c + 1]));
         }
@@ -610,7 +623,7 @@ __device__ __forceinline__ void qr_reg_step(zd *Y, const int l, const int k, con
       const int c = lane;
       zd d = {0.0, 0.0};
 #pragma unroll
-      for (int w = 0; w < 4; ++w) {
+      for (int w = 0; w < ROWT / 32; ++w) {
         d.re += S.red[w * K + 2 * c];
         d.im += S.red[w * K + 2 * c + 1];
       }
@@ -665,15 +678,15 @@ __device__ __forceinline__ void qr_reg_step(zd *Y, const int l, const int k, con
     }
 #pragma unroll 4
     for (int i = i0; i < ni; ++i) {
-      const int r = k + 1 + tid + i * kQrRowThreads;
-      const zd a = spiv[i * kQrRowThreads + tid];
+      const int r = k + 1 + tid + i * ROWT;
+      const zd a = spiv[i * ROWT + tid];
       zd v = {0.0, 0.0};
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        zd t = sy[c * CS + i * kQrRowThreads + tid];
+        zd t = sy[c * CS + i * ROWT + tid];
         t.re = fma(-g[c].re, a.re, fma(g[c].im, a.im, t.re));
         t.im = fma(-g[c].re, a.im, fma(-g[c].im, a.re, t.im));
-        if (cand < 0) sy[c * CS + i * kQrRowThreads + tid] = t;
+        if (cand < 0) sy[c * CS + i * ROWT + tid] = t;
         stcg(cp[c] + r, t);
         v = (c == 0 || cand == c) ? t : v;
       }
@@ -692,14 +705,14 @@ __device__ __forceinline__ void qr_reg_step(zd *Y, const int l, const int k, con
       if (rowt) {
 #pragma unroll
         for (int i = 0; i < ni; ++i) {
-          const double q = abs2(sy[c * CS + i * kQrRowThreads + tid]);
+          const double q = abs2(sy[c * CS + i * ROWT + tid]);
           fs += q;
           if (tid + i > 0) fr += q;  // rows k+2..
         }
       }
       const double full = block_sum(fs, S.scratch);
       const double from = block_sum(fr, S.scratch);
-      if (tid == kQrRowThreads) {
+      if (tid == ROWT) {
         if (S.fl[c]) {
           const double v = (k < l - 1) ? sqrt(full) : 0.0;
           S.nv[c] = v;
@@ -719,7 +732,8 @@ __device__ __forceinline__ void qr_reg_step(zd *Y, const int l, const int k, con
       int c0 = cand;
       double xsum;
       if (c0 >= 0) {
-        xsum = S.red[0] + S.red[1] + S.red[2] + S.red[3];
+        xsum = 0.0;
+        for (int w = 0; w < ROWT / 32; ++w) xsum += S.red[w];
       } else {
         long long bk = -1;
         int bq = 0x7fffffff;
@@ -737,18 +751,18 @@ __device__ __forceinline__ void qr_reg_step(zd *Y, const int l, const int k, con
   }
 }
 
-template <int RPT>
-__global__ void __launch_bounds__(kQrRegThreads, 2)
+template <int RPT, int ROWT, int NCMAX>
+__global__ void __launch_bounds__((ROWT + 32), (ROWT <= 128 ? 2 : 1))
 qrp_reg_kernel(zd *Y, int l, int m, double *vnA, double *vnB, double *vn2, double *__restrict__ beta,
                int32_t *__restrict__ piv, zd *__restrict__ Rout, QrPosts P, int *err, uint64_t limit_ns,
                int npair) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   zd *spiv = reinterpret_cast<zd *>(smem_raw);                         // RPT x 128 pivot rows, then 2 own columns
-  int *perm = reinterpret_cast<int *>(spiv + 3 * RPT * kQrRowThreads); // logical -> physical
+  int *perm = reinterpret_cast<int *>(spiv + (1 + NCMAX) * RPT * ROWT);  // logical -> physical
   __shared__ QrRegShared S;
   const int G = gridDim.x, b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int NW = kQrRegThreads / 32;
+  constexpr int NW = (ROWT + 32) / 32;
   const double tol3z = sqrt(0x1.0p-53);
   for (int j = tid; j < m; j += blockDim.x) perm[j] = j;
 
@@ -836,23 +850,29 @@ qrp_reg_kernel(zd *Y, int l, int m, double *vnA, double *vnB, double *vn2, doubl
     }
     const int slot = (k & 1) * kQrMaxGrid + b;
     if (nact == 0) {
-      qr_reg_step<0, RPT>(Y, l, k, G, b, perm, q0, vn_cur, vn_nxt, vn2, beta, spiv, S, P, slot, xn2, tol3z);
+      qr_reg_step<0, RPT, ROWT>(Y, l, k, G, b, perm, q0, vn_cur, vn_nxt, vn2, beta, spiv, S, P, slot, xn2, tol3z);
       if (k == m - 1) break;
-      if (tid == kQrRowThreads) {
+      if (tid == ROWT) {
         const unsigned long long tag = (unsigned long long)((k + 1) & 0x3FFFF) << 46;
         st_relaxed_u64(P.wa + slot, tag | ((unsigned long long)kQrNoPos << 32));
         st_relaxed_u64(P.wb + slot, tag);
       }
     } else if (nact == 1) {
-      qr_reg_step<1, RPT>(Y, l, k, G, b, perm, q0, vn_cur, vn_nxt, vn2, beta, spiv, S, P, slot, xn2, tol3z);
+      qr_reg_step<1, RPT, ROWT>(Y, l, k, G, b, perm, q0, vn_cur, vn_nxt, vn2, beta, spiv, S, P, slot, xn2, tol3z);
+    } else if (NCMAX <= 2 || nact == 2) {
+      qr_reg_step<2, RPT, ROWT>(Y, l, k, G, b, perm, q0, vn_cur, vn_nxt, vn2, beta, spiv, S, P, slot, xn2, tol3z);
+    } else if (nact == 3) {
+      qr_reg_step<(NCMAX >= 3 ? 3 : 2), RPT, ROWT>(Y, l, k, G, b, perm, q0, vn_cur, vn_nxt, vn2, beta, spiv, S, P,
+                                                   slot, xn2, tol3z);
     } else {
-      qr_reg_step<2, RPT>(Y, l, k, G, b, perm, q0, vn_cur, vn_nxt, vn2, beta, spiv, S, P, slot, xn2, tol3z);
+      qr_reg_step<(NCMAX >= 4 ? 4 : 2), RPT, ROWT>(Y, l, k, G, b, perm, q0, vn_cur, vn_nxt, vn2, beta, spiv, S, P,
+                                                   slot, xn2, tol3z);
     }
 
     // exchange: the scalar warp waits for every CTA's post of step k (relaxed polls of
     // the posts not yet seen, then an acquire fence) and reduces the candidates; the
     // row warps wait at the barrier
-    if (tid >= kQrRowThreads) {
+    if (tid >= ROWT) {
       constexpr int NT = (kQrMaxGrid + 31) / 32;
       const unsigned long long tagk = (unsigned long long)((k + 1) & 0x3FFFF);
       const unsigned long long *WA = P.wa + (k & 1) * kQrMaxGrid, *WB = P.wb + (k & 1) * kQrMaxGrid;
@@ -937,23 +957,24 @@ qrp_reg_kernel(zd *Y, int l, int m, double *vnA, double *vnB, double *vn2, doubl
   }
 }
 
-template <int RPT>
+template <int RPT, int ROWT, int NCMAX>
 static cudaError_t try_qrp_reg(const QrArgs &a, int sms, cudaStream_t st, bool &launched) {
   launched = false;
-  auto kern = qrp_reg_kernel<RPT>;
-  const size_t smem = sizeof(zd) * 3 * RPT * kQrRowThreads + sizeof(int) * (size_t)a.m;
+  auto kern = qrp_reg_kernel<RPT, ROWT, NCMAX>;
+  constexpr int per_sm = ROWT <= 128 ? 2 : 1;
+  const size_t smem = sizeof(zd) * (1 + NCMAX) * RPT * ROWT + sizeof(int) * (size_t)a.m;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kQrRegThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (ROWT + 32), smem);
   if (e != cudaSuccess) return e;
-  if (occ < 2) return cudaSuccess;  // the tile assumes two CTAs per SM (at most two own columns)
-  int G = 2 * sms;
+  if (occ < per_sm) return cudaSuccess;  // the tile's column limit assumes per_sm CTAs on every SM
+  int G = per_sm * sms;
   if (G > kQrMaxGrid) G = kQrMaxGrid;
   if (G > a.m) G = a.m;
   // widest share: ceil(T / G) columns, or with SM pairing half of ceil(T / sms), rounded up
-  const int widest = (G == 2 * sms) ? ((a.m - 1 + sms - 1) / sms + 1) / 2 : (a.m - 1 + G - 1) / G;
-  if (widest > 2) return cudaSuccess;
+  const int widest = (per_sm == 2 && G == 2 * sms) ? ((a.m - 1 + sms - 1) / sms + 1) / 2 : (a.m - 1 + G - 1) / G;
+  if (widest > NCMAX) return cudaSuccess;
   zd *Y = (zd *)a.Y;
   double *vnB = a.vn1 + a.m;
   int l = a.l, m = a.m;
@@ -966,12 +987,12 @@ static cudaError_t try_qrp_reg(const QrArgs &a, int sms, cudaStream_t st, bool &
   posts.smw = (unsigned long long *)(posts.xn2 + 2 * kQrMaxGrid);
   uint64_t lim = a.limit_ns;
   // two CTAs on every SM (G co-resident CTAs, at most two per SM): shares are balanced per SM
-  int npair = (G == 2 * sms) ? sms : 0;
+  int npair = (per_sm == 2 && G == 2 * sms) ? sms : 0;
   void *args[] = {&Y, &l, &m, (void *)&a.vn1, &vnB, (void *)&a.vn2, (void *)&a.beta, (void *)&a.piv,
                   &R, &posts, (void *)&a.err, &lim, &npair};
   note_launch();
   launched = true;
-  return cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(kQrRegThreads), args, smem, st);
+  return cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3((ROWT + 32)), args, smem, st);
 }
 
 template <int MAXC>
@@ -1024,13 +1045,17 @@ cudaError_t launch_qrp(const QrArgs &a, cudaStream_t st) {
   qr_norms_kernel<<<a.m, kQrThreads, 0, st>>>((const zd *)a.Y, a.l, a.vn1, a.vn2);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // register-tiled form when the sketch has at most 2048 rows and two CTAs per SM
-  // leave at most two columns to each
-  if (a.m <= 16383 && a.l - 1 <= 16 * kQrRowThreads) {
+  // register/shared-tiled form when a column's trailing rows fit the tile
+  if (a.m <= 16383) {
     bool launched = false;
-    if (a.l - 1 <= 4 * kQrRowThreads) e = try_qrp_reg<4>(a, sms, st, launched);
-    else if (a.l - 1 <= 8 * kQrRowThreads) e = try_qrp_reg<8>(a, sms, st, launched);
-    else e = try_qrp_reg<16>(a, sms, st, launched);
+    if (kQrWide && a.l - 1 <= 8 * 256) {
+      // one CTA per SM, 256 row threads, up to 4 own columns
+      e = try_qrp_reg<8, 256, 4>(a, sms, st, launched);
+      if (e != cudaSuccess || launched) return e;
+    }
+    if (a.l - 1 <= 4 * 128) e = try_qrp_reg<4, 128, 2>(a, sms, st, launched);
+    else if (a.l - 1 <= 8 * 128) e = try_qrp_reg<8, 128, 2>(a, sms, st, launched);
+    else if (a.l - 1 <= 16 * 128) e = try_qrp_reg<16, 128, 2>(a, sms, st, launched);
     if (e != cudaSuccess || launched) return e;
   }
   // the widest own-column share is the one at step 0; choose the instantiation for it

@@ -114,7 +114,7 @@ struct minnorm_plan_s {
   // fixed-point A for the exact residual
   void *d_afix = nullptr;
   int32_t *d_E = nullptr;
-  void *d_yfix = nullptr, *d_xpart = nullptr;
+  void *d_yfix = nullptr, *d_xpart = nullptr, *d_xapart = nullptr, *d_xfix = nullptr;
   int *d_F = nullptr;   // [0] = Fy, [1] = Fx
   int x_nchunk = 1;
   int64_t x_chunk = 1;
@@ -444,6 +444,8 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
     plan->x_nchunk = (int)nchunk;
     plan->x_chunk = (n + nchunk - 1) / nchunk;
     ALLOC(plan->d_xpart, xprod_partial_bytes(m, plan->x_nchunk));
+    ALLOC(plan->d_xapart, xadj_partial_bytes(m, n));
+    ALLOC(plan->d_xfix, xfix_bytes(n));
   }
   if (plan->fp32 && m <= 512) {
     plan->fused_ok = true;
@@ -701,6 +703,8 @@ XprodArgs xargs(minnorm_plan_t plan, const void *b) {
   a.partial = plan->d_xpart;
   a.nchunk = plan->x_nchunk;
   a.chunk = plan->x_chunk;
+  a.xpart = plan->d_xapart;
+  a.xfix = plan->d_xfix;
   return a;
 }
 

@@ -156,24 +156,27 @@ constexpr int kXadjUnroll = 8;
 // Complex products use Gauss's three multiplications, exact in integers up to
 // the floor of each product:  conj(a) y = (t1 + t2) + i (t3 - t1 + t2) with
 // t1 = a_r y_r, t2 = a_i y_i, t3 = (a_r - a_i)(y_r + y_i).
+// The rows are split over gridDim.y CTAs (more resident warps to hide the
+// loads' latency); each writes its exact partial sums, added by xadj_finish.
 __global__ void __launch_bounds__(kXadjThreads)
 xadj_kernel(const fixc *__restrict__ afix, int64_t rows, int64_t cols, const i128c *__restrict__ yfix,
-            const int *__restrict__ Fy, int Wy, zd *__restrict__ xh, zd *__restrict__ xl, int *__restrict__ Fx) {
+            i128c *__restrict__ xpart) {
   __shared__ i128c sy[kXadjThreads];
   __shared__ i128 ss[kXadjThreads];
-  __shared__ int red[kXadjThreads / 32];
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = (rows + gridDim.y - 1) / gridDim.y;
+  const int64_t r0 = (int64_t)blockIdx.y * per, r1 = r0 + per < rows ? r0 + per : rows;
   i128 are = 0, aim = 0;
-  for (int64_t i0 = 0; i0 < rows; i0 += kXadjThreads) {
+  for (int64_t i0 = r0; i0 < r1; i0 += kXadjThreads) {
     __syncthreads();
-    if (i0 + threadIdx.x < rows) {
+    if (i0 + threadIdx.x < r1) {
       const i128c y = yfix[i0 + threadIdx.x];
       sy[threadIdx.x] = y;
       ss[threadIdx.x] = y.re + y.im;
     }
     __syncthreads();
     if (j < cols) {
-      const int ie = (int)((i0 + kXadjThreads < rows ? i0 + kXadjThreads : rows) - i0);
+      const int ie = (int)((i0 + kXadjThreads < r1 ? i0 + kXadjThreads : r1) - i0);
       const fixc *a = afix + i0 * cols + j;
       int u = 0;
       for (; u + kXadjUnroll <= ie; u += kXadjUnroll) {
@@ -199,9 +202,23 @@ xadj_kernel(const fixc *__restrict__ afix, int64_t rows, int64_t cols, const i12
       }
     }
   }
+  if (j < cols) xpart[(int64_t)blockIdx.y * cols + j] = {are, aim};
+}
+
+// x_j = sum of the row splits' partials, as double-double; max exponent to Fx
+__global__ void __launch_bounds__(256)
+xadj_finish_kernel(const i128c *__restrict__ xpart, int nsplit, int64_t cols, const int *__restrict__ Fy, int Wy,
+                   zd *__restrict__ xh, zd *__restrict__ xl, int *__restrict__ Fx) {
+  __shared__ int red[8];
   int mx = -100000;
-  if (j < cols) {
-    const int scale = 2 + *Fy - Wy;
+  const int scale = 2 + *Fy - Wy;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols; j += (int64_t)gridDim.x * blockDim.x) {
+    i128 are = 0, aim = 0;
+    for (int q = 0; q < nsplit; ++q) {
+      const i128c v = xpart[(int64_t)q * cols + j];
+      are += v.re;
+      aim += v.im;
+    }
     double h1, l1, h2, l2;
     fix2dd(are, scale, h1, l1);
     fix2dd(aim, scale, h2, l2);
@@ -216,8 +233,19 @@ xadj_kernel(const fixc *__restrict__ afix, int64_t rows, int64_t cols, const i12
   __syncthreads();
   if (threadIdx.x == 0) {
     int e = red[0];
-    for (int w = 1; w < kXadjThreads / 32; ++w) e = max(e, red[w]);
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) e = max(e, red[w]);
     if (e > -99999) atomicMax(Fx, e + 1);
+  }
+}
+
+// x' = (xh + xl) 2^(Wx - Fx) as 128-bit fixed point, once per column for the forward pass
+__global__ void __launch_bounds__(256)
+xfix_kernel(int64_t cols, const zd *__restrict__ xh, const zd *__restrict__ xl, const int *__restrict__ Fx, int Wx,
+            i128c *__restrict__ xfix) {
+  const int k = Wx - *Fx;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols; j += (int64_t)gridDim.x * blockDim.x) {
+    const zd h = xh[j], l = xl[j];
+    xfix[j] = {d2fix(h.re, k) + d2fix(l.re, k), d2fix(h.im, k) + d2fix(l.im, k)};
   }
 }
 
@@ -232,25 +260,22 @@ __device__ __forceinline__ i128 shfl_xor_i128(i128 v, int o) {
 }
 
 __global__ void __launch_bounds__(kXfwdThreads)
-xfwd_kernel(const fixc *__restrict__ afix, int64_t rows, int64_t cols, const zd *__restrict__ xh,
-            const zd *__restrict__ xl, const int *__restrict__ Fx, int Wx, int64_t chunk,
-            i128c *__restrict__ partial) {
+xfwd_kernel(const fixc *__restrict__ afix, int64_t rows, int64_t cols, const i128c *__restrict__ xfix,
+            int64_t chunk, i128c *__restrict__ partial) {
   __shared__ i128c sred[(kXfwdThreads / 32) * kXfwdRows];
   const int64_t i0 = (int64_t)blockIdx.y * kXfwdRows;
   const int64_t c0 = (int64_t)blockIdx.x * chunk;
   const int64_t c1 = c0 + chunk < cols ? c0 + chunk : cols;
-  const int k = Wx - *Fx;
   i128 acc_re[kXfwdRows], acc_im[kXfwdRows];
 #pragma unroll
   for (int r = 0; r < kXfwdRows; ++r) { acc_re[r] = 0; acc_im[r] = 0; }
   const int nr = rows - i0 < kXfwdRows ? (int)(rows - i0) : kXfwdRows;
   for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-    const zd h = xh[c], l = xl[c];
+    const i128c xv = xfix[c];
     fixc av[kXfwdRows];
 #pragma unroll
     for (int r = 0; r < kXfwdRows; ++r) av[r] = r < nr ? afix[(i0 + r) * cols + c] : fixc{0, 0};
-    const i128 xr = d2fix(h.re, k) + d2fix(l.re, k);
-    const i128 xi = d2fix(h.im, k) + d2fix(l.im, k);
+    const i128 xr = xv.re, xi = xv.im;
     const i128 xs = xr + xi;
 #pragma unroll
     for (int r = 0; r < kXfwdRows; ++r) {
@@ -335,6 +360,16 @@ cudaError_t launch_fix_prep(const void *A, int64_t lda, bool c64, int64_t rows, 
 
 size_t xprod_partial_bytes(int64_t rows, int nchunk) { return sizeof(i128c) * (size_t)rows * nchunk; }
 
+// row splits of x = A^* y: enough CTAs for several per SM while each split keeps >= 64 rows
+int xadj_splits(int64_t rows, int64_t cols) {
+  const int64_t nbx = (cols + kXadjThreads - 1) / kXadjThreads;
+  int s = 1;
+  while (s < 8 && nbx * s < 2048 && rows / (2 * s) >= 64) s *= 2;
+  return s;
+}
+size_t xadj_partial_bytes(int64_t rows, int64_t cols) { return sizeof(i128c) * (size_t)cols * xadj_splits(rows, cols); }
+size_t xfix_bytes(int64_t cols) { return sizeof(i128c) * (size_t)cols; }
+
 cudaError_t launch_xresidual(const XprodArgs &a, cudaStream_t st) {
   const int Wy = xprod_wy(a.rows), Wx = xprod_wx(a.cols);
   cudaError_t e = cudaMemsetAsync(a.Fx, 0x80, sizeof(int), st);  // very negative start for atomicMax
@@ -343,15 +378,33 @@ cudaError_t launch_xresidual(const XprodArgs &a, cudaStream_t st) {
   fix_y_kernel<<<1, 1024, 0, st>>>((int)a.rows, (const zd *)a.yh, (const zd *)a.yl, a.E, Wy, (i128c *)a.yfix,
                                    a.Fy);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  note_launch();
-  xadj_kernel<<<(unsigned)((a.cols + kXadjThreads - 1) / kXadjThreads), kXadjThreads, 0, st>>>(
-      (const fixc *)a.afix, a.rows, a.cols, (const i128c *)a.yfix, a.Fy, Wy, (zd *)a.xh, (zd *)a.xl, a.Fx);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  {
+    const int64_t nbx = (a.cols + kXadjThreads - 1) / kXadjThreads;
+    const int nsplit = xadj_splits(a.rows, a.cols);
+    note_launch();
+    xadj_kernel<<<dim3((unsigned)nbx, (unsigned)nsplit), kXadjThreads, 0, st>>>(
+        (const fixc *)a.afix, a.rows, a.cols, (const i128c *)a.yfix, (i128c *)a.xpart);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int64_t nb = (a.cols + 255) / 256;
+    if (nb > 2048) nb = 2048;
+    note_launch();
+    xadj_finish_kernel<<<(unsigned)nb, 256, 0, st>>>((const i128c *)a.xpart, nsplit, a.cols, a.Fy, Wy,
+                                                     (zd *)a.xh, (zd *)a.xl, a.Fx);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (!a.b) return cudaSuccess;  // x only
+  {
+    int64_t nb = (a.cols + 255) / 256;
+    if (nb > 2048) nb = 2048;
+    note_launch();
+    xfix_kernel<<<(unsigned)nb, 256, 0, st>>>(a.cols, (const zd *)a.xh, (const zd *)a.xl, a.Fx, Wx,
+                                              (i128c *)a.xfix);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   dim3 grid(a.nchunk, (unsigned)((a.rows + kXfwdRows - 1) / kXfwdRows));
   note_launch();
-  xfwd_kernel<<<grid, kXfwdThreads, 0, st>>>((const fixc *)a.afix, a.rows, a.cols, (const zd *)a.xh,
-                                             (const zd *)a.xl, a.Fx, Wx, a.chunk, (i128c *)a.partial);
+  xfwd_kernel<<<grid, kXfwdThreads, 0, st>>>((const fixc *)a.afix, a.rows, a.cols, (const i128c *)a.xfix, a.chunk,
+                                             (i128c *)a.partial);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int64_t nb = (a.rows + 255) / 256;
   if (nb > 1024) nb = 1024;
