@@ -440,7 +440,7 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   {
     const int64_t row_blocks = (m + 7) / 8;
     int64_t nchunk = 1;
-    while (row_blocks * nchunk < 3 * plan->sms && n / (nchunk * 2) >= 1024) nchunk *= 2;
+    while (row_blocks * nchunk < 8 * plan->sms && n / (nchunk * 2) >= 1024) nchunk *= 2;
     plan->x_nchunk = (int)nchunk;
     plan->x_chunk = (n + nchunk - 1) / nchunk;
     ALLOC(plan->d_xpart, xprod_partial_bytes(m, plan->x_nchunk));

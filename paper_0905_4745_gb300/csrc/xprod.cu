@@ -364,7 +364,7 @@ size_t xprod_partial_bytes(int64_t rows, int nchunk) { return sizeof(i128c) * (s
 int xadj_splits(int64_t rows, int64_t cols) {
   const int64_t nbx = (cols + kXadjThreads - 1) / kXadjThreads;
   int s = 1;
-  while (s < 8 && nbx * s < 2048 && rows / (2 * s) >= 64) s *= 2;
+  while (s < 8 && nbx * s < 4096 && rows / (2 * s) >= 64) s *= 2;
   return s;
 }
 size_t xadj_partial_bytes(int64_t rows, int64_t cols) { return sizeof(i128c) * (size_t)cols * xadj_splits(rows, cols); }
