@@ -83,6 +83,19 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
       : "memory");
 }
 
+// warp sums of 4 floats, transposed: lane 0 gets v[0], lane 8 v[1], lane 16 v[2], lane 24 v[3]
+__device__ __forceinline__ float warp_sum_t4(const float (&v)[4], int lane) {
+  const bool lo = !(lane & 16);
+  const float w0 = (lo ? v[0] : v[2]) + __shfl_xor_sync(0xffffffffu, lo ? v[2] : v[0], 16);
+  const float w1 = (lo ? v[1] : v[3]) + __shfl_xor_sync(0xffffffffu, lo ? v[3] : v[1], 16);
+  const bool lo2 = !(lane & 8);
+  float z = (lo2 ? w0 : w1) + __shfl_xor_sync(0xffffffffu, lo2 ? w1 : w0, 8);
+  z += __shfl_xor_sync(0xffffffffu, z, 4);
+  z += __shfl_xor_sync(0xffffffffu, z, 2);
+  z += __shfl_xor_sync(0xffffffffu, z, 1);
+  return z;
+}
+
 // out[i] = sum_k M[i][k] v[k] for i in [r0, r1): one warp per row (FP64)
 __device__ __forceinline__ void rows_dot(const zd *__restrict__ M, const zd *v, int m, int r0, int r1,
                                          zd *out) {
@@ -114,8 +127,8 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
   zd *p_s = reinterpret_cast<zd *>(base + kStages * stage_bytes);  // m: search direction
   zd *v_s = p_s + m;                                               // m: t, then u
   zf *w_s = reinterpret_cast<zf *>(v_s + m);                       // rows_pad: w in FP32
-  zf *q_s = w_s + rows_pad;                                        // 16
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(q_s + kPanel);     // kStages
+  zf *q_s = w_s + rows_pad;                                        // 2 x 16: row halves' sums
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(q_s + 2 * kPanel); // kStages
   __shared__ double red[32];
   __shared__ double s_scal[4];
   __shared__ double s_qq[kCgThreads / 32];
@@ -180,7 +193,25 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
       const int sp = b + ip * G;
       bool w_ok = mbar_wait(&mbar[st], parity[st], P.limit_ns);
       if (!w_ok) w_ok = mbar_wait(&mbar[st], parity[st], P.limit_ns);  // a second bounded wait
+      w_ok = __all_sync(0xffffffffu, w_ok);  // warp-uniform: the q step below uses full-warp shuffles
       parity[st] ^= 1u;
+      const unsigned char *S = stage[st];
+      // (a) q_j = sum_i conj(A_ij) w_i: warp w takes the column pair 2cp, 2cp+1 (cp = w / 2,
+      //     one 16-byte swizzled chunk per row) over half of the rows; 16-byte shared loads
+      //     need the fewest wavefronts. The two halves' sums go to q_s[half][16].
+      if (w_ok) {  // a thread whose wait expired skips the stage; the barrier below tells all
+        const int cp = wid >> 1, hf = wid & 1, half = rows_pad >> 1;
+        zf a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
+        for (int r = hf * half + lane; r < (hf + 1) * half; r += 32) {
+          const float4 v = *reinterpret_cast<const float4 *>(S + r * 128 + ((cp ^ (r & 7)) << 4));
+          const zf wr = w_s[r];
+          macc(a0, zf{v.x, v.y}, wr);
+          macc(a1, zf{v.z, v.w}, wr);
+        }
+        const float vals[4] = {a0.re, a0.im, a1.re, a1.im};
+        const float z = warp_sum_t4(vals, lane);
+        if ((lane & 7) == 0) reinterpret_cast<float *>(q_s)[hf * 2 * kPanel + 4 * cp + (lane >> 3)] = z;
+      }
       if (__syncthreads_or(!w_ok)) {
         // give up uniformly; later stages may still hold issued copies: wait for them (bounded)
         ok = false;
@@ -190,24 +221,6 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
         }
         break;
       }
-      const unsigned char *S = stage[st];
-      // (a) q_j = sum_i conj(A_ij) w_i: warp j takes column j, lanes stride over the rows
-      {
-        const int j = wid;   // 16 warps, 16 columns
-        zf acc = {0.f, 0.f};
-        for (int r = lane; r < rows_pad; r += 32) {
-          const zf a = *reinterpret_cast<const zf *>(S + r * 128 + (((j >> 1) ^ (r & 7)) << 4) + ((j & 1) << 3));
-          macc(acc, a, w_s[r]);
-        }
-        acc.re = warp_sum(acc.re);
-        acc.im = warp_sum(acc.im);
-        if (lane == 0) {
-          q_s[j] = acc;
-          if (sp * kPanel + j < P.n)
-            qq_loc = fmaf(acc.re, acc.re, fmaf(acc.im, acc.im, qq_loc));
-        }
-      }
-      __syncthreads();
       // (b) t_i += sum_j A_ij q_j, one row per thread
       if (tid < m) {
         const int i = tid;
@@ -216,8 +229,16 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
         for (int kc = 0; kc < 8; ++kc) {
           const float4 v = *reinterpret_cast<const float4 *>(row + ((kc ^ (i & 7)) << 4));
           const zf a0 = {v.x, v.y}, a1 = {v.z, v.w};
-          mac(tacc, a0, q_s[2 * kc]);
-          mac(tacc, a1, q_s[2 * kc + 1]);
+          const zf q0 = q_s[2 * kc] + q_s[kPanel + 2 * kc], q1 = q_s[2 * kc + 1] + q_s[kPanel + 2 * kc + 1];
+          mac(tacc, a0, q0);
+          mac(tacc, a1, q1);
+        }
+      }
+      if (tid == 0) {
+#pragma unroll
+        for (int j = 0; j < kPanel; ++j) {
+          const zf qj = q_s[j] + q_s[kPanel + j];
+          if (sp * kPanel + j < P.n) qq_loc = fmaf(qj.re, qj.re, fmaf(qj.im, qj.im, qq_loc));
         }
       }
       __syncthreads();  // stage st is free
@@ -350,7 +371,7 @@ size_t cg_fused_smem(int64_t m) {
   const int nbox = (int)((m + kBoxRows - 1) / kBoxRows);
   const size_t rows_pad = (size_t)nbox * kBoxRows;
   return 1024 + kStages * rows_pad * 128 + 2 * (size_t)m * sizeof(zd) + rows_pad * sizeof(zf) +
-         kPanel * sizeof(zf) + kStages * sizeof(uint64_t);
+         2 * kPanel * sizeof(zf) + kStages * sizeof(uint64_t);
 }
 
 cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st) {
