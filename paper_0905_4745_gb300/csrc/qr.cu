@@ -175,7 +175,15 @@ __device__ __forceinline__ void qr_update(const zd *yp, zd *Y, const int *cols, 
     case 5: CALLN((MAXC >= 5 ? 5 : 0)); break;                \
     case 6: CALLN((MAXC >= 6 ? 6 : 0)); break;                \
     case 7: CALLN((MAXC >= 7 ? 7 : 0)); break;                \
-    default: CALLN((MAXC >= 8 ? 8 : 0)); break;               \
+    case 8: CALLN((MAXC >= 8 ? 8 : 0)); break;                \
+    case 9: CALLN((MAXC >= 9 ? 9 : 0)); break;                \
+    case 10: CALLN((MAXC >= 10 ? 10 : 0)); break;             \
+    case 11: CALLN((MAXC >= 11 ? 11 : 0)); break;             \
+    case 12: CALLN((MAXC >= 12 ? 12 : 0)); break;             \
+    case 13: CALLN((MAXC >= 13 ? 13 : 0)); break;             \
+    case 14: CALLN((MAXC >= 14 ? 14 : 0)); break;             \
+    case 15: CALLN((MAXC >= 15 ? 15 : 0)); break;             \
+    default: CALLN((MAXC >= 16 ? 16 : 0)); break;             \
   }
 
 // best (key, pos) of the pair: larger key, then lower position
@@ -265,7 +273,7 @@ qrp_mail_kernel(zd *Y, int l, int m, double *vnA, double *vnB, double *vn2, doub
 #pragma unroll
     for (int c = 0; c < K; ++c) part[c] = 0.0;
 #define MN_DOTS(NC) qr_dots<NC, K>(yp, Y, s_col, k, l, spiv, part)
-    if (MAXC <= 8) {
+    if (MAXC <= 16) {
       MN_QR_SWITCH(nact, MN_DOTS(0), MN_DOTS)
     } else {
       for (int r = k + 1 + tid; r < l; r += blockDim.x) {
@@ -331,7 +339,7 @@ qrp_mail_kernel(zd *Y, int l, int m, double *vnA, double *vnB, double *vn2, doub
 
     // 3. apply H^* to the own columns, rows k+1..l-1
 #define MN_UPD(NC) qr_update<NC>(yp, Y, s_col, s_g, k, l, spiv)
-    if (MAXC <= 8) {
+    if (MAXC <= 16) {
       MN_QR_SWITCH(nact, (void)0, MN_UPD)
     } else {
       for (int r = k + 1 + tid; r < l; r += blockDim.x) {
