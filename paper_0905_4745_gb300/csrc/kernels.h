@@ -151,6 +151,41 @@ struct CgFusedArgs {
 bool cg_fused_supported(int64_t m, int64_t n, int64_t lda, const void *A);
 cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st);
 
+// ---- blockcg.cu -------------------------------------------------------------------
+// block CG over kBlockRhs right-hand sides (block vectors row-major m x kBlockRhs)
+constexpr int kBlockRhs = 32;
+struct BlockProductArgs {
+  const void *A;           // complex64, row-major m x n, leading dimension lda
+  int64_t m, n, lda;
+  const void *W32;         // m x KB complex64: Wp P
+  void *Q;                 // n x KB complex64: A^* W
+  float *qqp;              // block_adj_parts(n) x KB partial |Q|^2
+  const double *gam;       // KB
+  const int *active;       // KB
+  double *alpha;           // KB (out)
+  void *tpart;             // nsplit x m x KB complex64
+  int nsplit;
+  void *T;                 // m x KB complex128: A Q
+  const int *alldone;
+};
+int block_adj_parts(int64_t n);
+int block_fwd_splits(int64_t m, int64_t n, int sms);
+int block_col_parts(int64_t m);
+cudaError_t launch_block_mm(const void *M, int m, const void *V, void *out, void *out32, const int *alldone,
+                            cudaStream_t st);
+cudaError_t launch_block_adj(const BlockProductArgs &a, cudaStream_t st);   // Q = A^* W, qq, alpha
+cudaError_t launch_block_fwd(const BlockProductArgs &a, cudaStream_t st);   // T = A Q
+cudaError_t launch_block_get_col(int m, const void *Bk, int c, void *v, cudaStream_t st);
+cudaError_t launch_block_set_col(int m, const void *v, int c, void *Bk, cudaStream_t st);
+cudaError_t launch_block_load_rhs(int m, int kc, const void *B, int64_t ldb, void *R, cudaStream_t st);
+cudaError_t launch_block_dd_acc(int m, const int *use, void *Yh, void *Yl, const void *dY, cudaStream_t st);
+cudaError_t launch_block_colnorms(int m, const void *X, double *part, cudaStream_t st);
+cudaError_t launch_block_cg_init(int m, const void *G, void *U, void *S, void *P, double *part, const int *use,
+                                 double *gam, double *gam0, int *active, int *alldone, cudaStream_t st);
+cudaError_t launch_block_cg_update(int m, const double *alpha, void *P, const void *Np, void *U, void *S,
+                                   double *part, double tol2, double *gam, const double *gam0, int *active,
+                                   double *beta, int *iters, int *alldone, cudaStream_t st);
+
 // small dense m x m FP64 products: out = M v (M row-major), optionally also an FP32 copy
 cudaError_t launch_small_gemv(const void *M, int m, const void *v, void *out, void *out32, const int *skip,
                               cudaStream_t st);

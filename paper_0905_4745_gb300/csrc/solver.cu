@@ -80,6 +80,18 @@ struct minnorm_plan_s {
   double *d_fac = nullptr;                   // l complex128: c_{s_t} / sqrt(n)
   cudaEvent_t ev_sk0 = nullptr, ev_sk1 = nullptr, ev_sk2 = nullptr;  // sketch / QR timing events
   double *h_qr = nullptr;                    // pinned: QR error word, |R_11|, |R_mm| of the last sketch
+  // block right-hand sides (allocated by the first multi-column mixed solve)
+  bool blk_ready = false;
+  void *d_bG = nullptr, *d_bR = nullptr, *d_bU = nullptr, *d_bS = nullptr, *d_bP = nullptr, *d_bT = nullptr,
+       *d_bNp = nullptr, *d_bdY = nullptr, *d_bYh = nullptr, *d_bYl = nullptr, *d_bW32 = nullptr, *d_bQ = nullptr,
+       *d_btpart = nullptr;
+  float *d_bqqp = nullptr;
+  double *d_bpart = nullptr, *d_bscal = nullptr;  // scal: gam, gam0, alpha, beta (KB each)
+  int *d_bint = nullptr;                           // use, active, iters (KB each), alldone
+  int blk_nsplit = 1;
+  double *h_bpart = nullptr;                       // pinned: column-norm partials
+  int *h_bint = nullptr;                           // pinned: a copy of d_bint
+  double *h_bx = nullptr;                          // pinned: ||x_c||^2 per column
   int cap1 = 0, cap2 = 0;
   int32_t *d_idx1 = nullptr, *d_idx2 = nullptr, *d_halo1 = nullptr, *d_halo2 = nullptr;
   void *d_ph1 = nullptr, *d_ph2 = nullptr, *d_cs1 = nullptr, *d_cs2 = nullptr, *d_post = nullptr, *d_tw = nullptr;
@@ -829,6 +841,203 @@ minnorm_status plan_create_pooled(minnorm_plan_t *out, int64_t m, int64_t n, int
   return MINNORM_OK;
 }
 
+// ---- Steps 3-5 for blocks of right-hand sides (mixed precision) -------------------
+minnorm_status block_alloc(minnorm_plan_t plan) {
+  if (plan->blk_ready) return MINNORM_OK;
+  const int64_t m = plan->m, n = plan->n;
+  const size_t bz = sizeof(zd) * (size_t)m * kBlockRhs;
+  void **bufs[] = {&plan->d_bG, &plan->d_bR, &plan->d_bU, &plan->d_bS, &plan->d_bP, &plan->d_bT, &plan->d_bNp,
+                   &plan->d_bdY, &plan->d_bYh, &plan->d_bYl};
+  for (void **b : bufs) ALLOC(*b, bz);
+  ALLOC(plan->d_bW32, sizeof(zf) * (size_t)m * kBlockRhs);
+  ALLOC(plan->d_bQ, sizeof(zf) * (size_t)n * kBlockRhs);
+  ALLOC(plan->d_bqqp, sizeof(float) * (size_t)block_adj_parts(n) * kBlockRhs);
+  plan->blk_nsplit = block_fwd_splits(m, n, plan->sms);
+  ALLOC(plan->d_btpart, sizeof(zf) * (size_t)plan->blk_nsplit * m * kBlockRhs);
+  ALLOC(plan->d_bpart, sizeof(double) * (size_t)block_col_parts(m) * kBlockRhs);
+  ALLOC(plan->d_bscal, sizeof(double) * 4 * kBlockRhs);
+  ALLOC(plan->d_bint, sizeof(int) * (3 * kBlockRhs + 1));
+  if (cudaMallocHost(&plan->h_bpart, sizeof(double) * (size_t)block_col_parts(m) * kBlockRhs) != cudaSuccess)
+    return MINNORM_ENOMEM;
+  if (cudaMallocHost(&plan->h_bint, sizeof(int) * (3 * kBlockRhs + 1)) != cudaSuccess) return MINNORM_ENOMEM;
+  if (cudaMallocHost(&plan->h_bx, sizeof(double) * kBlockRhs) != cudaSuccess) return MINNORM_ENOMEM;
+  plan->blk_ready = true;
+  return MINNORM_OK;
+}
+
+// per-column ||G_c|| (host, after a sync)
+minnorm_status block_gnorms(minnorm_plan_t plan, double *gn) {
+  cudaStream_t st = plan->st;
+  const int m = (int)plan->m, np = block_col_parts(m);
+  CK(launch_block_colnorms(m, plan->d_bG, plan->d_bpart, st));
+  CK(cudaMemcpyAsync(plan->h_bpart, plan->d_bpart, sizeof(double) * np * kBlockRhs, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int c = 0; c < kBlockRhs; ++c) {
+    double t = 0.0;
+    for (int q = 0; q < np; ++q) t += plan->h_bpart[q * kBlockRhs + c];
+    gn[c] = std::sqrt(t);
+  }
+  return MINNORM_OK;
+}
+
+// the block inner CG on G (columns with use[c]); returns the iterations taken (max over columns)
+minnorm_status block_inner_cg(minnorm_plan_t plan, const void *Acg, int64_t lda_cg, double tol, int maxit,
+                              int *iters_out) {
+  cudaStream_t st = plan->st;
+  const int m = (int)plan->m;
+  double *gam = plan->d_bscal, *gam0 = gam + kBlockRhs, *alpha = gam0 + kBlockRhs, *beta = alpha + kBlockRhs;
+  int *use = plan->d_bint, *active = use + kBlockRhs, *iters = active + kBlockRhs, *alldone = iters + kBlockRhs;
+  CK(cudaMemsetAsync(iters, 0, sizeof(int) * kBlockRhs, st));
+  CK(launch_block_cg_init(m, plan->d_bG, plan->d_bU, plan->d_bS, plan->d_bP, plan->d_bpart, use, gam, gam0, active,
+                          alldone, st));
+  BlockProductArgs pa{};
+  pa.A = Acg;
+  pa.m = plan->m;
+  pa.n = plan->n;
+  pa.lda = lda_cg;
+  pa.W32 = plan->d_bW32;
+  pa.Q = plan->d_bQ;
+  pa.qqp = plan->d_bqqp;
+  pa.gam = gam;
+  pa.active = active;
+  pa.alpha = alpha;
+  pa.tpart = plan->d_btpart;
+  pa.nsplit = plan->blk_nsplit;
+  pa.T = plan->d_bT;
+  pa.alldone = alldone;
+  int it = 0;
+  while (it < maxit) {
+    const int todo = std::min(4, maxit - it);
+    for (int k = 0; k < todo; ++k) {
+      CK(launch_block_mm(plan->d_Wp, m, plan->d_bP, nullptr, plan->d_bW32, alldone, st));
+      { Timed tm(plan, 0); CK(launch_block_adj(pa, st)); }
+      { Timed tm(plan, 1); CK(launch_block_fwd(pa, st)); }
+      CK(launch_block_mm(plan->d_WpH, m, plan->d_bT, plan->d_bNp, nullptr, alldone, st));
+      CK(launch_block_cg_update(m, alpha, plan->d_bP, plan->d_bNp, plan->d_bU, plan->d_bS, plan->d_bpart, tol * tol,
+                                gam, gam0, active, beta, iters, alldone, st));
+    }
+    it += todo;
+    CK(cudaMemcpyAsync(plan->h_bint, plan->d_bint, sizeof(int) * (3 * kBlockRhs + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (plan->h_bint[3 * kBlockRhs]) break;
+  }
+  int mx = 0;
+  for (int c = 0; c < kBlockRhs; ++c) mx = std::max(mx, plan->h_bint[2 * kBlockRhs + c]);
+  *iters_out = mx;
+  return MINNORM_OK;
+}
+
+// Steps 3-5 for columns j0 .. j0 + kc - 1 of B (kc <= kBlockRhs), mixed precision: the block
+// CG replaces the per-column CG; the refinement's exact residuals and stopping tests stay per
+// column, exactly as in solve_impl.
+minnorm_status solve_block_chunk(minnorm_plan_t plan, const void *A, int64_t lda, const zd *B, int64_t ldb, int kc,
+                                 double eps, zd *X, int64_t ldx, minnorm_info *infos) {
+  cudaStream_t st = plan->st;
+  const int64_t m = plan->m, n = plan->n;
+  const void *Acg = plan->d_A32 ? (const void *)plan->d_A32 : A;
+  const int64_t lda_cg = plan->d_A32 ? n : lda;
+  const double tol_inner = 1e-3;
+  const int maxit = 40;
+  int *use = plan->d_bint;
+  struct Col {
+    int outer = 0, stagnant = 0, cg = 0, passes = 0;
+    double err = INFINITY, best = INFINITY, prev = INFINITY;
+    minnorm_status status = MINNORM_ENOCONV;
+    bool done = false;
+  };
+  std::vector<Col> col(kc);
+  CK(cudaMemsetAsync(plan->d_bYh, 0, sizeof(zd) * m * kBlockRhs, st));
+  CK(cudaMemsetAsync(plan->d_bYl, 0, sizeof(zd) * m * kBlockRhs, st));
+  CK(launch_block_load_rhs((int)m, kc, B, ldb, plan->d_bR, st));
+  for (int c = 0; c < kc; ++c) CK(cudaMemsetAsync(X + c * ldx, 0, sizeof(zd) * n, st));
+  std::vector<double> gn(kBlockRhs);
+  std::vector<int> huse(kBlockRhs);
+  for (int outer = 0; outer <= kMaxOuter; ++outer) {
+    // G = Wp^* R; per-column bound ||x - p|| <= ||g|| (x as of the last exact residual)
+    CK(launch_block_mm(plan->d_WpH, (int)m, plan->d_bR, plan->d_bG, nullptr, nullptr, st));
+    minnorm_status s = block_gnorms(plan, gn.data());
+    if (s != MINNORM_OK) return s;
+    bool any = false;
+    for (int c = 0; c < kBlockRhs; ++c) {
+      huse[c] = 0;
+      if (c >= kc || col[c].done) continue;
+      Col &q = col[c];
+      if (outer > 0) {
+        const double xn = std::sqrt(plan->h_bx[c]);
+        q.err = xn > 0 ? gn[c] / xn : INFINITY;
+        if (q.err <= eps) { q.status = MINNORM_OK; q.done = true; continue; }
+        if (q.err < q.best) q.best = q.err;
+        q.stagnant = (q.err > 0.5 * q.prev) ? q.stagnant + 1 : 0;
+        if (q.stagnant >= 2) { q.status = MINNORM_EFLOOR; q.done = true; continue; }
+        q.prev = q.err;
+      } else if (gn[c] == 0.0) {
+        q.err = 0.0;
+        q.status = MINNORM_OK;
+        q.done = true;
+        continue;
+      }
+      if (outer == kMaxOuter) { q.done = true; continue; }  // ENOCONV with the bound just taken
+      huse[c] = 1;
+      any = true;
+      q.outer = outer + 1;
+    }
+    if (!any) break;
+    CK(cudaMemcpyAsync(use, huse.data(), sizeof(int) * kBlockRhs, cudaMemcpyHostToDevice, st));
+    int it = 0;
+    s = block_inner_cg(plan, Acg, lda_cg, tol_inner, maxit, &it);
+    if (s != MINNORM_OK) return s;
+    // dY = Wp U; y += dY (double-double) on the iterating columns
+    CK(launch_block_mm(plan->d_Wp, (int)m, plan->d_bU, plan->d_bdY, nullptr, nullptr, st));
+    CK(launch_block_dd_acc((int)m, use, plan->d_bYh, plan->d_bYl, plan->d_bdY, st));
+    // exact x = A^* y and r = b - A x per iterating column
+    for (int c = 0; c < kc; ++c) {
+      if (!huse[c]) continue;
+      col[c].cg += plan->h_bint[2 * kBlockRhs + c];
+      CK(launch_block_get_col((int)m, plan->d_bYh, c, plan->d_yh, st));
+      CK(launch_block_get_col((int)m, plan->d_bYl, c, plan->d_yl, st));
+      {
+        Timed tm(plan, 2);
+        CK(launch_xresidual(xargs(plan, B + c * ldb), st));
+      }
+      col[c].passes += 2;
+      CK(launch_block_set_col((int)m, plan->d_r, c, plan->d_bR, st));
+      CK(cudaMemcpyAsync(X + c * ldx, plan->d_xh, sizeof(zd) * n, cudaMemcpyDeviceToDevice, st));
+      CK(launch_sumsq(n, plan->d_xh, plan->d_red + 1024, plan->d_norms + 1, st));
+      CK(cudaMemcpyAsync(plan->h_bx + c, plan->d_norms + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+  }
+  if (infos) {
+    for (int c = 0; c < kc; ++c) {
+      // residual norm for the report
+      CK(launch_block_get_col((int)m, plan->d_bR, c, plan->d_r, st));
+      CK(launch_sumsq(m, plan->d_r, plan->d_red, plan->d_norms + 2, st));
+      CK(launch_sumsq(m, B + c * ldb, plan->d_red + 1024, plan->d_norms + 3, st));
+      CK(cudaMemcpyAsync(plan->h_norms, plan->d_norms, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      minnorm_info &f = infos[c];
+      f.outer_steps = col[c].outer;
+      f.cg_iters = col[c].cg;
+      f.exact_passes = col[c].passes;
+      f.status = col[c].status;
+      f.err_bound = col[c].err;
+      const double bn = std::sqrt(plan->h_norms[3]);
+      f.resid_rel = bn > 0 ? std::sqrt(plan->h_norms[2]) / bn : 0.0;
+      f.rdiag_max = plan->rdiag_max;
+      f.rdiag_min = plan->rdiag_min;
+      f.ms_sketch = plan->ms_sketch;
+      f.ms_qr = plan->ms_qr;
+      f.ms_solve = 0.0f;
+      f.reserved = 0;
+    }
+  } else {
+    CK(cudaStreamSynchronize(st));
+  }
+  minnorm_status first = MINNORM_OK;
+  for (int c = 0; c < kc; ++c)
+    if (col[c].status != MINNORM_OK && first == MINNORM_OK) first = col[c].status;
+  return first;
+}
+
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
@@ -923,6 +1132,22 @@ minnorm_status minnorm_solve_many(minnorm_plan_t plan, const void *A, int64_t ld
   plan->g_hp.ld = lda;
   plan->g_cg.ld = plan->d_A32 ? plan->n : lda;
   minnorm_status first = MINNORM_OK;
+  if (plan->fp32 && nrhs > 1) {
+    // mixed precision: block CG over chunks of up to kBlockRhs columns
+    minnorm_status s = block_alloc(plan);
+    if (s != MINNORM_OK) return s;
+    for (int64_t j0 = 0; j0 < nrhs; j0 += kBlockRhs) {
+      const int kc = (int)std::min<int64_t>(kBlockRhs, nrhs - j0);
+      s = solve_block_chunk(plan, A, lda, static_cast<const zd *>(B) + j0 * ldb, ldb, kc, eps,
+                            static_cast<zd *>(X) + j0 * ldx, ldx, infos ? infos + j0 : nullptr);
+      if (s == MINNORM_EINVAL || s == MINNORM_ESTATE || s == MINNORM_ECUDA || s == MINNORM_ENOMEM ||
+          s == MINNORM_ETIMEOUT)
+        return s;
+      if (s != MINNORM_OK && first == MINNORM_OK) first = s;
+    }
+    if (plan->flags & MINNORM_FLAG_TIMING) collect_timers(plan);
+    return first;
+  }
   for (int64_t j = 0; j < nrhs; ++j) {
     const minnorm_status s = solve_impl(plan, A, lda, static_cast<const zd *>(B) + j * ldb, eps,
                                         static_cast<zd *>(X) + j * ldx, infos ? infos + j : nullptr);
@@ -966,6 +1191,9 @@ minnorm_status minnorm_plan_destroy(minnorm_plan_t plan) {
   if (plan->h_norms) cudaFreeHost(plan->h_norms);
   if (plan->h_cg) cudaFreeHost(plan->h_cg);
   if (plan->h_qr) cudaFreeHost(plan->h_qr);
+  if (plan->h_bpart) cudaFreeHost(plan->h_bpart);
+  if (plan->h_bint) cudaFreeHost(plan->h_bint);
+  if (plan->h_bx) cudaFreeHost(plan->h_bx);
   delete plan;
   return MINNORM_OK;
 }

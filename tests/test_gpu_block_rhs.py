@@ -1,6 +1,8 @@
 """GPU parity of the block right-hand-side entry point (minnorm_solve_many): several
 right-hand sides sharing one A, one SRFT realization and one pivoted QR, each
-checked against the oracle's double-double-refined minimal-norm solution p."""
+checked against the oracle's double-double-refined minimal-norm solution p. In mixed
+precision the columns run through the block CG (32-column chunks; the 37-column case
+spans two chunks, the second partly filled)."""
 import numpy as np
 import pytest
 
@@ -36,7 +38,7 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("m,n,nrhs,prec", [(128, 8192, 5, 1), (96, 4096, 3, 0), (64, 2048, 8, 1)])
+@pytest.mark.parametrize("m,n,nrhs,prec", [(128, 8192, 5, 1), (96, 4096, 3, 0), (64, 2048, 8, 1), (48, 1000, 37, 1)])
 def test_solve_many_matches_oracle(mn, m, n, nrhs, prec):
     import torch
     s = synth.make_system(m, n, exponent=6, seed=8100 + m, nrhs=nrhs)
@@ -55,12 +57,13 @@ def test_solve_many_matches_oracle(mn, m, n, nrhs, prec):
             p = oracle.minnorm_direct(s.A, s.b[:, j], steps=6)["p"]
             assert _rel(Xh[:, j], p) <= 1e-12, (j, infos[j])
             assert infos[j]["err_bound"] <= 1e-12
-        # the same plan, one column at a time, gives the same columns
+        # the same plan, one column at a time: the same solutions (in mixed precision the block
+        # CG takes different iterates, so both are only within eps of p)
         for j in (0, nrhs - 1):
             x = torch.empty(n, dtype=torch.complex128, device=_dev())
             mn.minnorm_solve(plan, A, B[:, j].contiguous(), 1e-12, x)
             torch.cuda.synchronize()
-            assert _rel(Xh[:, j], x.cpu().numpy()) <= 1e-14
+            assert _rel(Xh[:, j], x.cpu().numpy()) <= (1e-14 if prec == 0 else 2e-12)
     finally:
         mn.minnorm_plan_destroy(plan)
 
