@@ -209,6 +209,47 @@ def reference_arm(args):
     return 0
 
 
+def class_amount(k, m, n, l, launches):
+    """Algorithmic work of `launches` timed regions of kernel class k for an m x n system (mixed
+    precision, complex64 products): (amount, unit, bound)."""
+    if k in (0, 1, 5):     # one complex64 pass over A per CG product / fused iteration
+        return launches * 8.0 * m * n, "GB/s", "hbm"
+    if k == 2:             # x = A^* y and b - A x over the 16-byte fixed-point A
+        return launches * 2 * 16.0 * m * n, "GB/s", "alu"
+    if k == 3:             # pivoted QR + P R^-1
+        return launches * (8.0 * m * m * (l - m / 3.0) + 8.0 * m ** 3 / 6.0), "TFLOP/s", "alu"
+    return launches * (8.0 * m * n + 16.0 * l * m), "GB/s", "hbm"   # sketch: read A once, write Y
+
+
+def side_roofline(shapes, stats_of, pk):
+    """Roofline of the dominant kernel class over the last step: stats_of(i, k) -> (launches, ms)
+    for system i; shapes: (m, n) per system."""
+    totals = {}
+    for k in KERNEL_CLASSES:
+        amount, ms, unit, bound = 0.0, 0.0, None, None
+        for i, (m, n) in enumerate(shapes):
+            nl, t = stats_of(i, k)
+            a, unit, bound = class_amount(k, m, n, min(4 * m, n), nl)
+            amount += a
+            ms += t
+        totals[k] = (amount, ms, unit, bound)
+    dom = max(totals, key=lambda k: totals[k][1])
+    amount, ms, unit, bound = totals[dom]
+    if ms <= 0:
+        return None
+    if unit == "GB/s":
+        achieved = amount / (ms / 1000.0) / 1e9
+        peak, src = pk["hbm_gbs"], "measured HBM copy"
+        if dom == 2:   # integer-ALU bound: report the bytes rate against HBM for scale
+            src = "measured HBM copy (the pass is integer-ALU bound)"
+    else:
+        achieved = amount / (ms / 1000.0) / 1e12
+        peak, src = FP64_NOMINAL_TFLOPS, "FP64 from unit counts and clock"
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "traffic": None, "kernel": KERNEL_CLASSES[dom], "peak_source": src,
+            "ms_by_class": {KERNEL_CLASSES[k]: round(v[1], 3) for k, v in totals.items()}}
+
+
 def side_workload(args):
     """The batching workload (256 systems, m uniform in [32, 512], n = m k, k uniform in [8, 64],
     complex64, sigma 1..1e-4, eps 1e-10) or the block right-hand-side workload (4096 x 131072
@@ -228,33 +269,43 @@ def side_workload(args):
         systems = [synth.make_system(m, n, exponent=4, seed=4000 + i, dtype="c64", device="cuda:0")
                    for i, (m, n) in enumerate(shapes)]
         batch = mn.minnorm_batch_create([m for m, _ in shapes], [n for _, n in shapes], mn.C64, mn.MIXED,
-                                        seed=4000, stream=stream)
+                                        seed=4000, flags=mn.FLAG_TIMING, stream=stream)
         xs = [torch.empty(n, dtype=torch.complex128, device=dev) for _, n in shapes]
         As, bs = [q.A for q in systems], [q.b for q in systems]
 
         def step():
             return mn.minnorm_batch_solve(batch, As, bs, 1e-10, xs)
+
+        def stats_of(i, k):
+            return mn.minnorm_batch_kernel_stats(batch, i, k)
         units, name = len(shapes), ("batching: 256 systems, m in [32, 512], n = m k, k in [8, 64], complex64, "
                                     "sigma 1..1e-4, eps 1e-10 (mixed)")
+        stat_shapes = shapes
         hbm = sum(m * n * 8 for m, n in shapes)
     else:
         w = synth.WORKLOADS["c5_blockrhs_4096x131072"]
         m, n, k = w["m"], w["n"], w["nrhs"]
         q = synth.make_system(m, n, w["exponent"], w["seed"], dtype="c64", nrhs=k, device="cuda:0")
-        plan = mn.minnorm_plan_create(m, n, 0, mn.C64, mn.MIXED, seed=5, stream=stream)
+        plan = mn.minnorm_plan_create(m, n, 0, mn.C64, mn.MIXED, seed=5, flags=mn.FLAG_TIMING, stream=stream)
         B = q.b.T.contiguous().T
         X = torch.empty((k, n), dtype=torch.complex128, device=dev).T
 
         def step():
             mn.minnorm_sketch(plan, q.A)
             return mn.minnorm_solve_many(plan, q.A, B, w["eps"], X)
+
+        def stats_of(i, kk):
+            return mn.minnorm_kernel_stats(plan, kk)
         units, name = k, "block right-hand sides: 4096x131072 complex64, sigma 1..1e-6, 64 RHS, eps 1e-10 (mixed)"
+        stat_shapes = [(m, n)]
         hbm = m * n * 8
     for _ in range(warmup):
         step()
     launches0 = mn.minnorm_launch_count()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ck = Clocks(0)
+    ck.__enter__()
     e0.record(stream)
     statuses = []
     for _ in range(steps):
@@ -262,14 +313,33 @@ def side_workload(args):
         statuses.append(st)
     e1.record(stream)
     torch.cuda.synchronize()
+    ck.__exit__()
     ms = e0.elapsed_time(e1)
     worst = max(i["err_bound"] for i in infos)
+    pk, _ = peaks()
+    roof = side_roofline(stat_shapes, stats_of, pk)
+    cpu = None
+    if not args.no_oracle:
+        if args.workload == "batch":
+            total, count = 0.0, 0
+            while count < len(systems) and (total < 10.0 or count == 0):     # systems in index order, ~10 s
+                A_np = systems[count].A.cpu().numpy().astype(np.complex128)
+                secs, _ = run_oracle_solve(A_np, systems[count].b.cpu().numpy(), seed=4000 + count)
+                total += secs
+                count += 1
+            cpu = {"value": count / total, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": "the first %d systems of the batch (Steps 1-5, FP64, oracle O2), %.1f s" % (count, total)}
+        else:
+            cpu = {"value": None, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": "none: one oracle solve of this workload exceeds the bounded sample "
+                             "(its pivoted QR of 16384 x 4096 alone is ~2e12 flops on the host)"}
     print(json.dumps({"metric": "solves/s (%s workload)" % args.workload, "value": units * steps / (ms / 1000.0),
                       "unit": "solves/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
                       "ms_per_step": ms / steps, "higher_is_better": True, "dtype": "c64 products + f64 QR/R + "
                       "fixed-point residual", "data": "synthetic", "config": {"workload": name, "A_bytes": hbm},
-                      "status": mn.STATUS_NAMES[max(statuses)], "worst_err_bound": worst,
-                      "gpu_launches": mn.minnorm_launch_count() - launches0}), flush=True)
+                      "status": mn.STATUS_NAMES[max(statuses)], "worst_err_bound": worst, "roofline": roof,
+                      "cpu_baseline": cpu, "gpu_launches": mn.minnorm_launch_count() - launches0,
+                      "clocks": ck.summary()}), flush=True)
     return 0
 
 
