@@ -105,13 +105,18 @@ chain_kernel(const S *__restrict__ src, int64_t ld_src, cx<R> *__restrict__ dst,
 
   // the gather is latency-bound: issue the index loads, then the gathered loads, of several
   // elements per thread before using any of them
+  // (the phase and rotation loads do not depend on the gather: they go with the index loads)
   constexpr int kG = 8;
   for (int t0 = threadIdx.x; t0 < cnt; t0 += kG * blockDim.x) {
     int ix[kG];
+    cx<R> ph[kG], rc[kG];
 #pragma unroll
     for (int g = 0; g < kG; ++g) {
       const int t = t0 + g * blockDim.x;
-      ix[g] = t < cnt ? idx[lo + t] : 0;
+      const int j = lo + (t < cnt ? t : 0);
+      ix[g] = idx[j];
+      ph[g] = phase[j];
+      rc[g] = cs[j];
     }
     S a[kG];
 #pragma unroll
@@ -120,10 +125,9 @@ chain_kernel(const S *__restrict__ src, int64_t ld_src, cx<R> *__restrict__ dst,
     for (int g = 0; g < kG; ++g) {
       const int t = t0 + g * blockDim.x;
       if (t < cnt) {
-        const int j = lo + t;
         const cx<R> v = {R(a[g].re), CONJ ? -R(a[g].im) : R(a[g].im)};
-        V[t] = v * phase[j];
-        CS[t] = cs[j];
+        V[t] = v * ph[g];
+        CS[t] = rc[g];
       }
     }
   }
