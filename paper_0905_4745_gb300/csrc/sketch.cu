@@ -169,25 +169,31 @@ __device__ __forceinline__ int bitrev(int j, int logL) {
   return logL == 0 ? 0 : (int)(__brev((unsigned)j) >> (32 - logL));
 }
 
-// In-place radix-2 DIT FFT (forward, e^{-2 pi i jk/L}) of B contiguous
-// sequences of length L = 2^logL stored in bit-reversed order; twiddles
-// e^{-2 pi i k / NT} from the table tw (L divides NT).
+// stw[k] = e^{-2 pi i k / L} for k < L/2, copied from the table tw (NT entries, L divides NT)
+// into shared memory: every butterfly stage then reads its twiddle there
 template <typename R>
-__device__ __forceinline__ void smem_fft(cx<R> *data, int B, int logL, int stride, const cx<R> *__restrict__ tw,
-                                         int logNT) {
+__device__ __forceinline__ void load_twiddles(cx<R> *stw, int logL, const cx<R> *__restrict__ tw, int logNT) {
+  for (int k = threadIdx.x; k < (1 << (logL - 1)); k += blockDim.x) stw[k] = tw[(int64_t)k << (logNT - logL)];
+}
+
+// In-place radix-2 DIT FFT (forward, e^{-2 pi i jk/L}) of B sequences of length
+// L = 2^logL, `stride` elements apart, stored in bit-reversed order; twiddles
+// from stw (see load_twiddles).
+template <typename R>
+__device__ __forceinline__ void smem_fft(cx<R> *data, int B, int logL, int stride, const cx<R> *stw) {
   const int L = 1 << logL;
   const int halfL = L >> 1;
   const int total = B * halfL;
   for (int lh = 0; lh < logL; ++lh) {
     const int h = 1 << lh;
-    const int twshift = logNT - lh - 1;  // NT / (2h)
+    const int twshift = logL - lh - 1;  // (L/2) / h
     for (int b = threadIdx.x; b < total; b += blockDim.x) {
       const int seqi = b >> (logL - 1);
       const int bb = b & (halfL - 1);
       const int k = bb & (h - 1);
       const int pos = ((bb >> lh) << (lh + 1)) + k;
       cx<R> *d = data + seqi * stride;
-      const cx<R> w = tw[k << twshift];
+      const cx<R> w = stw[k << twshift];
       const cx<R> u = d[pos];
       const cx<R> v = d[pos + h] * w;
       d[pos] = u + v;
@@ -226,11 +232,25 @@ fft_row_kernel(const cx<R> *__restrict__ src, int64_t ld_src, int logn, const cx
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R> *data = reinterpret_cast<cx<R> *>(smem_raw);
   const int n = 1 << logn;
+  cx<R> *stw = data + n;  // n/2 twiddles
   const int64_t row = blockIdx.y;
   const cx<R> *s = src + row * ld_src;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) data[bitrev(j, logn)] = fft_in(s, j, chirp, nin);
+  load_twiddles<R>(stw, logn, tw, logn);
+  for (int j0 = threadIdx.x; j0 < n; j0 += 8 * blockDim.x) {  // eight loads in flight per thread
+    cx<R> v[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const int j = j0 + g * blockDim.x;
+      v[g] = j < n ? fft_in(s, j, chirp, nin) : cx<R>{R(0), R(0)};
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const int j = j0 + g * blockDim.x;
+      if (j < n) data[bitrev(j, logn)] = v[g];
+    }
+  }
   __syncthreads();
-  smem_fft<R>(data, 1, logn, n, tw, logn);
+  smem_fft<R>(data, 1, logn, n, stw);
   if (full) {
     cx<R> *f = full + row * ldf;
     for (int k = threadIdx.x; k < n; k += blockDim.x) f[k] = conjg(data[k] * bh[k]);
@@ -256,18 +276,41 @@ fft_pass_a_kernel(const cx<R> *__restrict__ src, int64_t ld, cx<R> *__restrict__
   const int64_t row = blockIdx.y;
   const cx<R> *s = src + row * ld;
   const int total = tj * N2;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int jj = e % tj, j2 = e / tj;
-    data[jj * (N2 + 1) + bitrev(j2, logN2)] = fft_in(s, (j1_0 + jj) + (int64_t)N1 * j2, chirp, nin);
+  cx<R> *stw = data + tj * (N2 + 1);  // N2/2 twiddles
+  load_twiddles<R>(stw, logN2, tw, logn);
+  for (int e0 = threadIdx.x; e0 < total; e0 += 8 * blockDim.x) {  // eight loads in flight per thread
+    cx<R> v[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const int e = e0 + g * blockDim.x;
+      const int jj = e % tj, j2 = e / tj;
+      v[g] = e < total ? fft_in(s, (j1_0 + jj) + (int64_t)N1 * j2, chirp, nin) : cx<R>{R(0), R(0)};
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const int e = e0 + g * blockDim.x;
+      if (e < total) data[(e % tj) * (N2 + 1) + bitrev(e / tj, logN2)] = v[g];
+    }
   }
   __syncthreads();
-  smem_fft<R>(data, tj, logN2, N2 + 1, tw, logn);
+  smem_fft<R>(data, tj, logN2, N2 + 1, stw);
   cx<R> *w = W + row * ldw;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int jj = e % tj, k2 = e / tj;
-    const int j1 = j1_0 + jj;
-    const int64_t tix = ((int64_t)j1 * k2) & (n - 1);
-    w[(int64_t)k2 * N1 + j1] = data[jj * (N2 + 1) + k2] * tw[tix];
+  for (int e0 = threadIdx.x; e0 < total; e0 += 8 * blockDim.x) {
+    cx<R> t8[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const int e = e0 + g * blockDim.x;
+      const int jj = e % tj, k2 = e / tj;
+      t8[g] = e < total ? tw[((int64_t)(j1_0 + jj) * k2) & (n - 1)] : cx<R>{R(0), R(0)};
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const int e = e0 + g * blockDim.x;
+      if (e < total) {
+        const int jj = e % tj, k2 = e / tj;
+        w[(int64_t)k2 * N1 + j1_0 + jj] = data[jj * (N2 + 1) + k2] * t8[g];
+      }
+    }
   }
 }
 
@@ -287,12 +330,23 @@ fft_pass_b_kernel(const cx<R> *__restrict__ W, int64_t ldw, int logn, int logN1,
   const int64_t row = blockIdx.y;
   const cx<R> *w = W + row * ldw + (int64_t)k2_0 * N1;
   const int total = tk * N1;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int kk = e >> logN1, j1 = e & (N1 - 1);
-    data[kk * (N1 + 1) + bitrev(j1, logN1)] = w[e];
+  cx<R> *stw = data + tk * (N1 + 1);  // N1/2 twiddles
+  load_twiddles<R>(stw, logN1, tw, logn);
+  for (int e0 = threadIdx.x; e0 < total; e0 += 8 * blockDim.x) {  // eight loads in flight per thread
+    cx<R> v[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const int e = e0 + g * blockDim.x;
+      v[g] = e < total ? w[e] : cx<R>{R(0), R(0)};
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const int e = e0 + g * blockDim.x;
+      if (e < total) data[(e >> logN1) * (N1 + 1) + bitrev(e & (N1 - 1), logN1)] = v[g];
+    }
   }
   __syncthreads();
-  smem_fft<R>(data, tk, logN1, N1 + 1, tw, logn);
+  smem_fft<R>(data, tk, logN1, N1 + 1, stw);
   if (full) {
     // X[N2 k1 + k2] for k2 = k2_0 + kk sits at data[kk (N1 + 1) + k1]; runs of tk consecutive outputs
     const int N2 = 1 << (logn - logN1);
@@ -369,7 +423,7 @@ static cudaError_t launch_fft_t(const FftArgs &a, cudaStream_t st) {
   const double scale = 1.0 / sqrt((double)(1LL << a.logn));
   cudaError_t e;
   if (a.logN1 == 0) {
-    const size_t smem = sizeof(cx<R>) << a.logn;
+    const size_t smem = (sizeof(cx<R>) << a.logn) + (sizeof(cx<R>) << (a.logn - 1));  // data + twiddles
     e = cudaFuncSetAttribute(fft_row_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     note_launch();
@@ -382,8 +436,8 @@ static cudaError_t launch_fft_t(const FftArgs &a, cudaStream_t st) {
   const int N1 = 1 << a.logN1, N2 = 1 << (a.logn - a.logN1);
   // sequences padded by one element: the strided transposes into and out of shared memory
   // then touch distinct banks
-  const size_t smemA = sizeof(cx<R>) * (size_t)a.tj * (N2 + 1);
-  const size_t smemB = sizeof(cx<R>) * (size_t)a.tk * (N1 + 1);
+  const size_t smemA = sizeof(cx<R>) * ((size_t)a.tj * (N2 + 1) + N2 / 2);
+  const size_t smemB = sizeof(cx<R>) * ((size_t)a.tk * (N1 + 1) + N1 / 2);
   e = cudaFuncSetAttribute(fft_pass_a_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemA);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(fft_pass_b_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemB);
