@@ -8,7 +8,11 @@
 // through a three-stage mbarrier pipeline, and used twice while resident:
 //     q_j  = sum_i conj(A_ij) w_i      for the sub-panel's 16 columns
 //     t_i += sum_j A_ij q_j            for all m rows (per-thread accumulators)
-// so A^* w and A (A^* w) cost one pass. The FP64 parts (w = Wp p,
+// so A^* w and A (A^* w) cost one pass. Successive iterations walk the own
+// sub-panels in opposite directions: the last kStages sub-panels of one
+// iteration are still in shared memory when the next begins (no reload), and
+// the ones read just before them were loaded with an L2 evict-last hint, so
+// the next iteration finds its first stretch of A in L2. The FP64 parts (w = Wp p,
 // Np = Wp^* t, the CG scalars) are spread over the CTAs by rows, between four
 // grid barriers per iteration (bounded waits, see common.cuh). The search
 // direction p is kept, identically, in every CTA's shared memory.
@@ -29,6 +33,7 @@ constexpr int kStages = 3;      // TMA ring depth
 
 struct CgFusedParams {
   int m, n, nbox;
+  int keep;         // sub-panels per CTA at the end of each sweep loaded with an L2 evict-last hint
   const zd *Wp, *WpH;
   const zd *g;
   zd *u, *s, *w, *t, *dy;
@@ -76,11 +81,41 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
   return true;
 }
 
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+// 2-D tile load with an L2 cache policy (createpolicy: evict_first or evict_last)
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
+                                            uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
       : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// warp sums of 32 floats, transposed: afterwards v[0] of lane L holds the sum over
+// the warp of v[L] (a butterfly: at offset o each lane keeps the half of its
+// remaining values selected by its bit o and receives the partner's partial sums)
+__device__ __forceinline__ void warp_transpose_sum32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool lo = !(lane & o);
+#pragma unroll
+    for (int k = 0; k < o; ++k) {
+      const float send = lo ? v[k + o] : v[k];
+      const float keep = lo ? v[k] : v[k + o];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
 }
 
 // warp sums of 4 floats, transposed: lane 0 gets v[0], lane 8 v[1], lane 16 v[2], lane 24 v[3]
@@ -121,17 +156,15 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
   const int m = P.m, nbox = P.nbox;
   const int rows_pad = nbox * kBoxRows;
   const int stage_bytes = rows_pad * 128;
-  unsigned char *stage[kStages];
-#pragma unroll
-  for (int q = 0; q < kStages; ++q) stage[q] = base + q * stage_bytes;
+  auto stage = [&](int q) { return base + q * stage_bytes; };
   zd *p_s = reinterpret_cast<zd *>(base + kStages * stage_bytes);  // m: search direction
   zd *v_s = p_s + m;                                               // m: t, then u
-  zf *w_s = reinterpret_cast<zf *>(v_s + m);                       // rows_pad: w in FP32
-  zf *q_s = w_s + rows_pad;                                        // 2 x 16: row halves' sums
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(q_s + 2 * kPanel); // kStages
+  float *q_f = reinterpret_cast<float *>(v_s + m);                 // 32: q of the current sub-panel
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(q_f + 2 * kPanel); // kStages
   __shared__ double red[32];
   __shared__ double s_scal[4];
   __shared__ double s_qq[kCgThreads / 32];
+  __shared__ float s_red[kCgThreads / 32][32];
 
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
@@ -158,11 +191,11 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
     P.s[i] = P.g[i];
     P.u[i] = {0.0, 0.0};
   }
-  for (int i = m + tid; i < rows_pad; i += blockDim.x) w_s[i] = {0.f, 0.f};
   double gamma = block_sum(loc, red);
   const double gamma0 = gamma;
   bool done = !(gamma > 0.0);
   uint32_t parity[kStages] = {};
+  const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
   int it = 0;
   bool ok = true;
 
@@ -172,86 +205,97 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
     if (!grid_sync(P.bar, G, epoch, P.limit_ns)) { ok = false; break; }
 
     // P2: q = A^* w and t = A q over the own sub-panels, A read once
-    for (int i = tid; i < m; i += blockDim.x) {
-      const zd wi = P.w[i];
-      w_s[i] = {(float)wi.re, (float)wi.im};
-    }
-    __syncthreads();
+    // thread i holds w_i and, per sub-panel, row i of the sub-panel in registers
+    const zf wreg = tid < m ? cvt<float>(P.w[tid]) : zf{0.f, 0.f};
     zf tacc = {0.f, 0.f};
-    // |q|^2 of this warp's columns in FP32 inside the loop (an FP64 instruction costs
-    // ~76 cycles of the SM sub-partition's FP64 pipe on GB300), widened once at the end
+    // |q|^2 in FP32 inside the loop (an FP64 instruction costs ~76 cycles of the SM
+    // sub-partition's FP64 pipe on GB300), widened once at the end
     float qq_loc = 0.f;
-    if (tid == 0) {
-      for (int q = 0; q < kStages && q < nsp; ++q) {
-        mbar_expect_tx(&mbar[q], stage_tx);
-        for (int bx = 0; bx < nbox; ++bx)
-          tma_load_2d(stage[q] + bx * kBoxRows * 128, &amap, (b + q * G) * 2 * kPanel, bx * kBoxRows, &mbar[q]);
-      }
+    // sweep direction alternates; the first nres positions of this sweep are the
+    // last ones of the previous sweep, still resident in their stages
+    const bool fwd = (it & 1) == 0;
+    const int nres = it > 0 ? (nsp < kStages ? nsp : kStages) : 0;
+    // stage of a sub-panel = its own index mod kStages: a load issued after position e
+    // is consumed (position e + kStages, in either direction) reuses e's stage
+    auto issue = [&](int e) {
+      const int ipn = fwd ? e : nsp - 1 - e;
+      const int sl = ipn % kStages;
+      const uint64_t pol = e >= nsp - P.keep ? pol_last : pol_first;
+      mbar_expect_tx(&mbar[sl], stage_tx);
+      for (int bx = 0; bx < nbox; ++bx)
+        tma_load_2d(stage(sl) + bx * kBoxRows * 128, &amap, (b + ipn * G) * 2 * kPanel, bx * kBoxRows, &mbar[sl],
+                    pol);
+    };
+    if (tid == 0 && it == 0) {
+      for (int e = 0; e < kStages && e < nsp; ++e) issue(e);
     }
-    int st = 0;
-    for (int ip = 0; ip < nsp; ++ip) {
+    for (int e = 0; e < nsp; ++e) {
+      const int ip = fwd ? e : nsp - 1 - e;
+      const int st = ip % kStages;
       const int sp = b + ip * G;
-      bool w_ok = mbar_wait(&mbar[st], parity[st], P.limit_ns);
-      if (!w_ok) w_ok = mbar_wait(&mbar[st], parity[st], P.limit_ns);  // a second bounded wait
-      w_ok = __all_sync(0xffffffffu, w_ok);  // warp-uniform: the q step below uses full-warp shuffles
-      parity[st] ^= 1u;
-      const unsigned char *S = stage[st];
-      // (a) q_j = sum_i conj(A_ij) w_i: warp w takes the column pair 2cp, 2cp+1 (cp = w / 2,
-      //     one 16-byte swizzled chunk per row) over half of the rows; 16-byte shared loads
-      //     need the fewest wavefronts. The two halves' sums go to q_s[half][16].
-      if (w_ok) {  // a thread whose wait expired skips the stage; the barrier below tells all
-        const int cp = wid >> 1, hf = wid & 1, half = rows_pad >> 1;
-        zf a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
-        for (int r = hf * half + lane; r < (hf + 1) * half; r += 32) {
-          const float4 v = *reinterpret_cast<const float4 *>(S + r * 128 + ((cp ^ (r & 7)) << 4));
-          const zf wr = w_s[r];
-          macc(a0, zf{v.x, v.y}, wr);
-          macc(a1, zf{v.z, v.w}, wr);
-        }
-        const float vals[4] = {a0.re, a0.im, a1.re, a1.im};
-        const float z = warp_sum_t4(vals, lane);
-        if ((lane & 7) == 0) reinterpret_cast<float *>(q_s)[hf * 2 * kPanel + 4 * cp + (lane >> 3)] = z;
+      bool w_ok = true;
+      if (e >= nres) {
+        w_ok = mbar_wait(&mbar[st], parity[st], P.limit_ns);
+        if (!w_ok) w_ok = mbar_wait(&mbar[st], parity[st], P.limit_ns);  // a second bounded wait
+        parity[st] ^= 1u;
       }
+      w_ok = __all_sync(0xffffffffu, w_ok);  // warp-uniform: the q step below uses full-warp shuffles
+      const unsigned char *S = stage(st);
+      // (a) row tid of the sub-panel into registers (eight 16-byte swizzled chunks), its
+      //     terms conj(A_ij) w_i of the 16 q_j, summed over the warp's 32 rows by a butterfly
+      float4 av[8];
+      if (w_ok && tid < rows_pad) {
+        const unsigned char *row = S + tid * 128;
+#pragma unroll
+        for (int kc = 0; kc < 8; ++kc) av[kc] = *reinterpret_cast<const float4 *>(row + ((kc ^ (tid & 7)) << 4));
+      } else {
+#pragma unroll
+        for (int kc = 0; kc < 8; ++kc) av[kc] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      float c[32];
+#pragma unroll
+      for (int kc = 0; kc < 8; ++kc) {
+        c[4 * kc + 0] = fmaf(av[kc].x, wreg.re, av[kc].y * wreg.im);
+        c[4 * kc + 1] = fmaf(av[kc].x, wreg.im, -av[kc].y * wreg.re);
+        c[4 * kc + 2] = fmaf(av[kc].z, wreg.re, av[kc].w * wreg.im);
+        c[4 * kc + 3] = fmaf(av[kc].z, wreg.im, -av[kc].w * wreg.re);
+      }
+      warp_transpose_sum32(c, lane);
+      s_red[wid][lane] = c[0];
       if (__syncthreads_or(!w_ok)) {
         // give up uniformly; later stages may still hold issued copies: wait for them (bounded)
         ok = false;
-        for (int q = 1; q < kStages && ip + q < nsp; ++q) {
-          const int s2 = (st + q) % kStages;
+        for (int e2 = e + 1; e2 < e + kStages && e2 < nsp; ++e2) {
+          if (e2 < nres) continue;  // resident, nothing in flight
+          const int s2 = (fwd ? e2 : nsp - 1 - e2) % kStages;
           mbar_wait(&mbar[s2], parity[s2], P.limit_ns);
         }
         break;
       }
-      // (b) t_i += sum_j A_ij q_j, one row per thread
+      // stage st is free (the sub-panel is in registers): refill it now
+      if (tid == 0 && e + kStages < nsp) issue(e + kStages);
+      // (b) q over the 16 warps (fixed order), and |q|^2 of the columns inside A
+      if (wid == 0) {
+        float qf = 0.f;
+#pragma unroll
+        for (int w2 = 0; w2 < kCgThreads / 32; ++w2) qf += s_red[w2][lane];
+        q_f[lane] = qf;
+        if (sp * kPanel + (lane >> 1) < P.n) qq_loc = fmaf(qf, qf, qq_loc);
+      }
+      __syncthreads();
+      // (c) t_i += sum_j A_ij q_j from the registers
       if (tid < m) {
-        const int i = tid;
-        const unsigned char *row = S + i * 128;
 #pragma unroll
         for (int kc = 0; kc < 8; ++kc) {
-          const float4 v = *reinterpret_cast<const float4 *>(row + ((kc ^ (i & 7)) << 4));
-          const zf a0 = {v.x, v.y}, a1 = {v.z, v.w};
-          const zf q0 = q_s[2 * kc] + q_s[kPanel + 2 * kc], q1 = q_s[2 * kc + 1] + q_s[kPanel + 2 * kc + 1];
-          mac(tacc, a0, q0);
-          mac(tacc, a1, q1);
+          const float4 q4 = *reinterpret_cast<const float4 *>(q_f + 4 * kc);
+          mac(tacc, zf{av[kc].x, av[kc].y}, zf{q4.x, q4.y});
+          mac(tacc, zf{av[kc].z, av[kc].w}, zf{q4.z, q4.w});
         }
       }
-      if (tid == 0) {
-#pragma unroll
-        for (int j = 0; j < kPanel; ++j) {
-          const zf qj = q_s[j] + q_s[kPanel + j];
-          if (sp * kPanel + j < P.n) qq_loc = fmaf(qj.re, qj.re, fmaf(qj.im, qj.im, qq_loc));
-        }
-      }
-      __syncthreads();  // stage st is free
-      if (tid == 0 && ip + kStages < nsp) {
-        mbar_expect_tx(&mbar[st], stage_tx);
-        for (int bx = 0; bx < nbox; ++bx)
-          tma_load_2d(stage[st] + bx * kBoxRows * 128, &amap, (sp + kStages * G) * 2 * kPanel, bx * kBoxRows,
-                      &mbar[st]);
-      }
-      st = (st + 1 == kStages) ? 0 : st + 1;
     }
     if (!ok) break;
     if (tid < m) P.tpart[(int64_t)b * m + tid] = tacc;
+    qq_loc = warp_sum(qq_loc);
     if (lane == 0) s_qq[wid] = (double)qq_loc;
     __syncthreads();
     if (tid == 0) {
@@ -370,8 +414,8 @@ bool cg_fused_supported(int64_t m, int64_t n, int64_t lda, const void *A) {
 size_t cg_fused_smem(int64_t m) {
   const int nbox = (int)((m + kBoxRows - 1) / kBoxRows);
   const size_t rows_pad = (size_t)nbox * kBoxRows;
-  return 1024 + kStages * rows_pad * 128 + 2 * (size_t)m * sizeof(zd) + rows_pad * sizeof(zf) +
-         2 * kPanel * sizeof(zf) + kStages * sizeof(uint64_t);
+  return 1024 + kStages * rows_pad * 128 + 2 * (size_t)m * sizeof(zd) + 2 * kPanel * sizeof(float) +
+         kStages * sizeof(uint64_t);
 }
 
 cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st) {
@@ -413,6 +457,12 @@ cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int NP = (int)((a.n + kPanel - 1) / kPanel);
   const int G = a.grid < NP ? a.grid : NP;
+  // sub-panels per CTA kept in L2 between sweeps: about 60 % of L2
+  int dev = 0, l2 = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+    l2 = 0;
+  const double stage_bytes = (double)P.nbox * kBoxRows * 128;
+  P.keep = (int)(0.6 * (double)l2 / ((double)G * stage_bytes));
   void *args[] = {(void *)&map, (void *)&P};
   note_launch();
   return cudaLaunchCooperativeKernel((const void *)cg_fused_kernel, dim3(G), dim3(kCgThreads), args, smem, st);
