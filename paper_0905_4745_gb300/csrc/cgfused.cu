@@ -3,18 +3,21 @@
 //     (Wp^* A A^* Wp) du = g,   Wp = P R^{-1},
 // with every iteration reading A (complex64) from HBM exactly once.
 //
-// Each CTA owns every G-th 16-column sub-panel of A (m <= 512 rows). A sub-panel (m x 16 complex64, 128 bytes per row) is brought into
-// shared memory by 2-D TMA loads (cp.async.bulk.tensor, 128-byte swizzle)
-// through a three-stage mbarrier pipeline, and used twice while resident:
-//     q_j  = sum_i conj(A_ij) w_i      for the sub-panel's 16 columns
-//     t_i += sum_j A_ij q_j            for all m rows (per-thread accumulators)
+// Each CTA owns every G-th 16-column sub-panel of A (m <= 512 rows). A sub-panel
+// (m x 16 complex64, 128 bytes per row) is brought into shared memory by 2-D TMA
+// loads (cp.async.bulk.tensor, 128-byte swizzle) through a three-stage mbarrier
+// pipeline. Each thread copies eight columns of two rows of it into registers (the
+// stage is refilled at once) and uses them twice:
+//     q_j  = sum_i conj(A_ij) w_i      (in-thread over its two rows, then a warp
+//                                        butterfly and a fixed-order sum over warps)
+//     t_i += sum_j A_ij q_j            (per-thread accumulators)
 // so A^* w and A (A^* w) cost one pass. Successive iterations walk the own
 // sub-panels in opposite directions: the last kStages sub-panels of one
 // iteration are still in shared memory when the next begins (no reload), and
-// the ones read just before them were loaded with an L2 evict-last hint, so
-// the next iteration finds its first stretch of A in L2. The FP64 parts (w = Wp p,
-// Np = Wp^* t, the CG scalars) are spread over the CTAs by rows, between four
-// grid barriers per iteration (bounded waits, see common.cuh). The search
+// the ones read just before them were loaded with an L2 evict-last hint. The
+// FP64 parts (w = Wp p, Np = Wp^* t, the CG scalars) are spread over the CTAs by
+// rows, between four grid barriers per iteration (bounded waits, see
+// common.cuh); s and u of a CTA's rows stay in its registers. The search
 // direction p is kept, identically, in every CTA's shared memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -102,12 +105,13 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
   return p;
 }
 
-// warp sums of 32 floats, transposed: afterwards v[0] of lane L holds the sum over
-// the warp of v[L] (a butterfly: at offset o each lane keeps the half of its
-// remaining values selected by its bit o and receives the partner's partial sums)
-__device__ __forceinline__ void warp_transpose_sum32(float (&v)[32], int lane) {
+// warp sums of 16 floats, transposed: afterwards v[0] of lane L holds the warp
+// sum of v[L & 15] (a butterfly: at offset o each lane keeps the half of its
+// remaining values selected by its bit o and receives the partner's partial sums;
+// the last step adds the two half-warps)
+__device__ __forceinline__ void warp_transpose_sum16(float (&v)[16], int lane) {
 #pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
+  for (int o = 8; o >= 1; o >>= 1) {
     const bool lo = !(lane & o);
 #pragma unroll
     for (int k = 0; k < o; ++k) {
@@ -116,24 +120,25 @@ __device__ __forceinline__ void warp_transpose_sum32(float (&v)[32], int lane) {
       v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
-// warp sums of 4 floats, transposed: lane 0 gets v[0], lane 8 v[1], lane 16 v[2], lane 24 v[3]
-__device__ __forceinline__ float warp_sum_t4(const float (&v)[4], int lane) {
-  const bool lo = !(lane & 16);
-  const float w0 = (lo ? v[0] : v[2]) + __shfl_xor_sync(0xffffffffu, lo ? v[2] : v[0], 16);
-  const float w1 = (lo ? v[1] : v[3]) + __shfl_xor_sync(0xffffffffu, lo ? v[3] : v[1], 16);
-  const bool lo2 = !(lane & 8);
-  float z = (lo2 ? w0 : w1) + __shfl_xor_sync(0xffffffffu, lo2 ? w1 : w0, 8);
+// warp sums of re and im in one butterfly (lanes 0-15 carry re, 16-31 im: five
+// FP64 additions instead of ten); the result is valid in lane 0
+__device__ __forceinline__ zd warp_sum_pair(double re, double im, int lane) {
+  const bool lo = lane < 16;
+  double z = (lo ? re : im) + __shfl_xor_sync(0xffffffffu, lo ? im : re, 16);
+  z += __shfl_xor_sync(0xffffffffu, z, 8);
   z += __shfl_xor_sync(0xffffffffu, z, 4);
   z += __shfl_xor_sync(0xffffffffu, z, 2);
   z += __shfl_xor_sync(0xffffffffu, z, 1);
-  return z;
+  return {z, __shfl_sync(0xffffffffu, z, 16)};
 }
 
-// out[i] = sum_k M[i][k] v[k] for i in [r0, r1): one warp per row (FP64)
-__device__ __forceinline__ void rows_dot(const zd *__restrict__ M, const zd *v, int m, int r0, int r1,
-                                         zd *out) {
+// out[i] = sum_k M[i][k] v[k] for i in [r0, r1): one warp per row (FP64), v in
+// shared memory; out is global (gout) or shared (sout[i - r0])
+__device__ __forceinline__ void rows_dot(const zd *__restrict__ M, const zd *v, int m, int r0, int r1, zd *gout,
+                                         zd *sout) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = r0 + wid; i < r1; i += nw) {
     const zd *row = M + (int64_t)i * m;
@@ -143,9 +148,11 @@ __device__ __forceinline__ void rows_dot(const zd *__restrict__ M, const zd *v, 
       re = fma(a.re, x.re, fma(-a.im, x.im, re));
       im = fma(a.re, x.im, fma(a.im, x.re, im));
     }
-    re = warp_sum(re);
-    im = warp_sum(im);
-    if (lane == 0) out[i] = {re, im};
+    const zd r = warp_sum_pair(re, im, lane);
+    if (lane == 0) {
+      if (gout) gout[i] = r;
+      else sout[i - r0] = r;
+    }
   }
 }
 
@@ -159,7 +166,8 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
   auto stage = [&](int q) { return base + q * stage_bytes; };
   zd *p_s = reinterpret_cast<zd *>(base + kStages * stage_bytes);  // m: search direction
   zd *v_s = p_s + m;                                               // m: t, then u
-  float *q_f = reinterpret_cast<float *>(v_s + m);                 // 32: q of the current sub-panel
+  zd *np_s = v_s + m;                                              // m: Np of the own u-space rows
+  float *q_f = reinterpret_cast<float *>(np_s + m);                // 32: q of the current sub-panel
   uint64_t *mbar = reinterpret_cast<uint64_t *>(q_f + 2 * kPanel); // kStages
   __shared__ double red[32];
   __shared__ double s_scal[4];
@@ -168,7 +176,7 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
 
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
-  const int r0 = (int)((long long)m * b / G), r1 = (int)((long long)m * (b + 1) / G);
+  const int r0 = (int)((long long)m * b / G), r1 = (int)((long long)m * (b + 1) / G);  // own rows
   // sub-panels b, b + G, b + 2G, ...: at any moment the grid reads one contiguous
   // stretch of every row (DRAM page locality), not G scattered 128-byte pieces
   const int NP = (P.n + kPanel - 1) / kPanel;
@@ -187,10 +195,10 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
     p_s[i] = gi;
     loc = fma(gi.re, gi.re, fma(gi.im, gi.im, loc));
   }
-  for (int i = r0 + tid; i < r1; i += blockDim.x) {
-    P.s[i] = P.g[i];
-    P.u[i] = {0.0, 0.0};
-  }
+  // s and u of the own row r0 + tid live in registers (only this CTA updates them)
+  const bool own_su = tid < r1 - r0;
+  zd s_reg = own_su ? P.g[r0 + tid] : zd{0.0, 0.0};
+  zd u_reg = {0.0, 0.0};
   double gamma = block_sum(loc, red);
   const double gamma0 = gamma;
   bool done = !(gamma > 0.0);
@@ -201,13 +209,17 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
 
   while (!done && it < P.maxit) {
     // P1: w = Wp p (own rows)
-    rows_dot(P.Wp, p_s, m, r0, r1, P.w);
+    rows_dot(P.Wp, p_s, m, r0, r1, P.w, nullptr);
     if (!grid_sync(P.bar, G, epoch, P.limit_ns)) { ok = false; break; }
 
-    // P2: q = A^* w and t = A q over the own sub-panels, A read once
-    // thread i holds w_i and, per sub-panel, row i of the sub-panel in registers
-    const zf wreg = tid < m ? cvt<float>(P.w[tid]) : zf{0.f, 0.f};
-    zf tacc = {0.f, 0.f};
+    // P2: q = A^* w and t = A q over the own sub-panels, A read once.
+    // Thread (warp wid, lane) takes columns 8h..8h+7 (h = wid & 1) of rows ra and
+    // ra + 256 (ra = 32 (wid >> 1) + lane) of every sub-panel into registers: its two
+    // rows' terms of a q_j are added in the thread, so the warp reduces 16 values.
+    const int h = wid & 1, ra = 32 * (wid >> 1) + lane, rb = ra + 256;
+    const zf w0 = ra < m ? cvt<float>(P.w[ra]) : zf{0.f, 0.f};
+    const zf w1 = rb < m ? cvt<float>(P.w[rb]) : zf{0.f, 0.f};
+    zf t0 = {0.f, 0.f}, t1 = {0.f, 0.f};
     // |q|^2 in FP32 inside the loop (an FP64 instruction costs ~76 cycles of the SM
     // sub-partition's FP64 pipe on GB300), widened once at the end
     float qq_loc = 0.f;
@@ -241,27 +253,37 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
       }
       w_ok = __all_sync(0xffffffffu, w_ok);  // warp-uniform: the q step below uses full-warp shuffles
       const unsigned char *S = stage(st);
-      // (a) row tid of the sub-panel into registers (eight 16-byte swizzled chunks), its
-      //     terms conj(A_ij) w_i of the 16 q_j, summed over the warp's 32 rows by a butterfly
-      float4 av[8];
-      if (w_ok && tid < rows_pad) {
-        const unsigned char *row = S + tid * 128;
+      // (a) the thread's two half rows (four 16-byte swizzled chunks each) into registers;
+      //     their terms conj(A_ij) w_i of the 8 q_j, summed over the warp by a butterfly
+      float4 a0[4], a1[4];
 #pragma unroll
-        for (int kc = 0; kc < 8; ++kc) av[kc] = *reinterpret_cast<const float4 *>(row + ((kc ^ (tid & 7)) << 4));
-      } else {
-#pragma unroll
-        for (int kc = 0; kc < 8; ++kc) av[kc] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int kc = 0; kc < 4; ++kc) {
+        a0[kc] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a1[kc] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      float c[32];
+      if (w_ok) {
+        const int ch = 4 * h;
+        if (ra < rows_pad) {
 #pragma unroll
-      for (int kc = 0; kc < 8; ++kc) {
-        c[4 * kc + 0] = fmaf(av[kc].x, wreg.re, av[kc].y * wreg.im);
-        c[4 * kc + 1] = fmaf(av[kc].x, wreg.im, -av[kc].y * wreg.re);
-        c[4 * kc + 2] = fmaf(av[kc].z, wreg.re, av[kc].w * wreg.im);
-        c[4 * kc + 3] = fmaf(av[kc].z, wreg.im, -av[kc].w * wreg.re);
+          for (int kc = 0; kc < 4; ++kc)
+            a0[kc] = *reinterpret_cast<const float4 *>(S + ra * 128 + (((ch + kc) ^ (ra & 7)) << 4));
+        }
+        if (rb < rows_pad) {
+#pragma unroll
+          for (int kc = 0; kc < 4; ++kc)
+            a1[kc] = *reinterpret_cast<const float4 *>(S + rb * 128 + (((ch + kc) ^ (rb & 7)) << 4));
+        }
       }
-      warp_transpose_sum32(c, lane);
-      s_red[wid][lane] = c[0];
+      float c[16];
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc) {
+        c[4 * kc + 0] = fmaf(a0[kc].x, w0.re, fmaf(a0[kc].y, w0.im, fmaf(a1[kc].x, w1.re, a1[kc].y * w1.im)));
+        c[4 * kc + 1] = fmaf(a0[kc].x, w0.im, fmaf(-a0[kc].y, w0.re, fmaf(a1[kc].x, w1.im, -a1[kc].y * w1.re)));
+        c[4 * kc + 2] = fmaf(a0[kc].z, w0.re, fmaf(a0[kc].w, w0.im, fmaf(a1[kc].z, w1.re, a1[kc].w * w1.im)));
+        c[4 * kc + 3] = fmaf(a0[kc].z, w0.im, fmaf(-a0[kc].w, w0.re, fmaf(a1[kc].z, w1.im, -a1[kc].w * w1.re)));
+      }
+      warp_transpose_sum16(c, lane);
+      if (lane < 16) s_red[wid][lane] = c[0];
       if (__syncthreads_or(!w_ok)) {
         // give up uniformly; later stages may still hold issued copies: wait for them (bounded)
         ok = false;
@@ -275,26 +297,37 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
       // stage st is free (the sub-panel is in registers): refill it now
       if (tid == 0 && e + kStages < nsp) issue(e + kStages);
       // (b) q over the 16 warps (fixed order), and |q|^2 of the columns inside A
-      if (wid == 0) {
+      if (wid == 0) {  // lane = 16 h' + v: value v of column half h', over the 8 warps of that half
         float qf = 0.f;
 #pragma unroll
-        for (int w2 = 0; w2 < kCgThreads / 32; ++w2) qf += s_red[w2][lane];
+        for (int w2 = 0; w2 < kCgThreads / 64; ++w2) qf += s_red[2 * w2 + (lane >> 4)][lane & 15];
         q_f[lane] = qf;
         if (sp * kPanel + (lane >> 1) < P.n) qq_loc = fmaf(qf, qf, qq_loc);
       }
       __syncthreads();
-      // (c) t_i += sum_j A_ij q_j from the registers
-      if (tid < m) {
+      // (c) t_i += sum_j A_ij q_j over the thread's 8 columns, from the registers
 #pragma unroll
-        for (int kc = 0; kc < 8; ++kc) {
-          const float4 q4 = *reinterpret_cast<const float4 *>(q_f + 4 * kc);
-          mac(tacc, zf{av[kc].x, av[kc].y}, zf{q4.x, q4.y});
-          mac(tacc, zf{av[kc].z, av[kc].w}, zf{q4.z, q4.w});
-        }
+      for (int kc = 0; kc < 4; ++kc) {
+        const float4 q4 = *reinterpret_cast<const float4 *>(q_f + 16 * h + 4 * kc);
+        mac(t0, zf{a0[kc].x, a0[kc].y}, zf{q4.x, q4.y});
+        mac(t0, zf{a0[kc].z, a0[kc].w}, zf{q4.z, q4.w});
+        mac(t1, zf{a1[kc].x, a1[kc].y}, zf{q4.x, q4.y});
+        mac(t1, zf{a1[kc].z, a1[kc].w}, zf{q4.z, q4.w});
       }
     }
     if (!ok) break;
-    if (tid < m) P.tpart[(int64_t)b * m + tid] = tacc;
+    {  // the two column halves of a row meet in shared memory (np_s is free here)
+      zf *th = reinterpret_cast<zf *>(np_s);
+      if (h == 1) {
+        if (ra < m) th[ra] = t0;
+        if (rb < m) th[rb] = t1;
+      }
+      __syncthreads();
+      if (h == 0) {
+        if (ra < m) P.tpart[(int64_t)b * m + ra] = t0 + th[ra];
+        if (rb < m) P.tpart[(int64_t)b * m + rb] = t1 + th[rb];
+      }
+    }
     qq_loc = warp_sum(qq_loc);
     if (lane == 0) s_qq[wid] = (double)qq_loc;
     __syncthreads();
@@ -306,20 +339,19 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
     if (!grid_sync(P.bar, G, epoch, P.limit_ns)) { ok = false; break; }
 
     // P3a: t (own rows) = sum of the partials; qq = sum of the per-CTA |q|^2
-    for (int i = r0 + wid; i < r1; i += blockDim.x >> 5) {
+    for (int i = r0 + wid - 1; wid > 0 && i < r1; i += (blockDim.x >> 5) - 1) {   // warps 1..15
       double re = 0.0, im = 0.0;
       for (int c = lane; c < G; c += 32) {
-        const zf v = P.tpart[(int64_t)c * m + i];
+        const zf v = ldcg(P.tpart + (int64_t)c * m + i);
         re += (double)v.re;
         im += (double)v.im;
       }
-      re = warp_sum(re);
-      im = warp_sum(im);
-      if (lane == 0) P.t[i] = {re, im};
+      const zd ti = warp_sum_pair(re, im, lane);
+      if (lane == 0) stcg(P.t + i, ti);
     }
     if (wid == 0) {
       double qs = 0.0;
-      for (int c = lane; c < G; c += 32) qs += P.qq_part[c];
+      for (int c = lane; c < G; c += 32) qs += ldcg(P.qq_part + c);
       qs = warp_sum(qs);
       if (lane == 0) s_scal[0] = qs;
     }
@@ -328,44 +360,46 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
     const double alpha = qq > 0.0 ? gamma / qq : 0.0;
 
     // P3b: Np = Wp^* t (own rows); s -= alpha Np; u += alpha p; partial ||s||^2
-    for (int i = tid; i < m; i += blockDim.x) v_s[i] = P.t[i];
+    for (int i = tid; i < m; i += blockDim.x) v_s[i] = ldcg(P.t + i);
     __syncthreads();
-    rows_dot(P.WpH, v_s, m, r0, r1, P.dy);   // dy holds Np for the own rows here
+    rows_dot(P.WpH, v_s, m, r0, r1, nullptr, np_s);
     __syncthreads();
     double gl = 0.0;
-    for (int i = r0 + tid; i < r1; i += blockDim.x) {
-      const zd np = P.dy[i], pi = p_s[i];
-      zd si = P.s[i], ui = P.u[i];
-      si.re = fma(-alpha, np.re, si.re);
-      si.im = fma(-alpha, np.im, si.im);
-      ui.re = fma(alpha, pi.re, ui.re);
-      ui.im = fma(alpha, pi.im, ui.im);
-      P.s[i] = si;
-      P.u[i] = ui;
-      gl = fma(si.re, si.re, fma(si.im, si.im, gl));
+    if (own_su) {
+      const zd np = np_s[tid], pi = p_s[r0 + tid];
+      s_reg.re = fma(-alpha, np.re, s_reg.re);
+      s_reg.im = fma(-alpha, np.im, s_reg.im);
+      u_reg.re = fma(alpha, pi.re, u_reg.re);
+      u_reg.im = fma(alpha, pi.im, u_reg.im);
+      stcg(P.s + r0 + tid, s_reg);
+      gl = fma(s_reg.re, s_reg.re, s_reg.im * s_reg.im);
     }
-    if (wid == 0) {
-      const double gs = warp_sum(gl);
-      if (lane == 0) P.gg_part[b] = gs;
+    gl = warp_sum(gl);
+    if (lane == 0) s_qq[wid] = gl;
+    __syncthreads();
+    if (tid == 0) {
+      double gs = 0.0;
+      for (int w2 = 0; w2 < kCgThreads / 32; ++w2) gs += s_qq[w2];
+      P.gg_part[b] = gs;
     }
     if (!grid_sync(P.bar, G, epoch, P.limit_ns)) { ok = false; break; }
 
-    // P4: gamma' and the new direction, identically in every CTA
+    // P4: gamma' and the new direction, identically in every CTA (s loaded first)
+    const zd s_all = tid < m ? ldcg(P.s + tid) : zd{0.0, 0.0};
     if (wid == 0) {
       double gs = 0.0;
-      for (int c = lane; c < G; c += 32) gs += P.gg_part[c];
+      for (int c = lane; c < G; c += 32) gs += ldcg(P.gg_part + c);
       gs = warp_sum(gs);
       if (lane == 0) s_scal[1] = gs;
     }
     __syncthreads();
     const double gnew = s_scal[1];
     const double beta = gamma > 0.0 ? gnew / gamma : 0.0;
-    for (int i = tid; i < m; i += blockDim.x) {
-      const zd si = P.s[i];
-      zd pi = p_s[i];
-      pi.re = fma(beta, pi.re, si.re);
-      pi.im = fma(beta, pi.im, si.im);
-      p_s[i] = pi;
+    if (tid < m) {
+      zd pi = p_s[tid];
+      pi.re = fma(beta, pi.re, s_all.re);
+      pi.im = fma(beta, pi.im, s_all.im);
+      p_s[tid] = pi;
     }
     gamma = gnew;
     ++it;
@@ -377,14 +411,15 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
     // no TMA load is left in flight: every issued stage was waited for above
     return;
   }
-  // dy = Wp u (own rows)
+  // dy = Wp u
+  if (own_su) stcg(P.u + r0 + tid, u_reg);
   if (!grid_sync(P.bar, G, epoch, P.limit_ns)) {
     if (tid == 0) atomicExch(P.err, 1);
     return;
   }
-  for (int i = tid; i < m; i += blockDim.x) v_s[i] = P.u[i];
+  for (int i = tid; i < m; i += blockDim.x) v_s[i] = ldcg(P.u + i);
   __syncthreads();
-  rows_dot(P.Wp, v_s, m, r0, r1, P.dy);
+  rows_dot(P.Wp, v_s, m, r0, r1, P.dy, nullptr);
   if (b == 0 && tid == 0) {
     P.sc->iters = it;
     P.sc->gamma = gamma;
@@ -394,6 +429,7 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
 }
 
 // ---- host -------------------------------------------------------------------
+
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -414,7 +450,7 @@ bool cg_fused_supported(int64_t m, int64_t n, int64_t lda, const void *A) {
 size_t cg_fused_smem(int64_t m) {
   const int nbox = (int)((m + kBoxRows - 1) / kBoxRows);
   const size_t rows_pad = (size_t)nbox * kBoxRows;
-  return 1024 + kStages * rows_pad * 128 + 2 * (size_t)m * sizeof(zd) + 2 * kPanel * sizeof(float) +
+  return 1024 + kStages * rows_pad * 128 + 3 * (size_t)m * sizeof(zd) + 2 * kPanel * sizeof(float) +
          kStages * sizeof(uint64_t);
 }
 

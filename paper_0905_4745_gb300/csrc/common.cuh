@@ -64,6 +64,10 @@ __device__ __forceinline__ zd ldcg(const zd *p) {
   return {v.x, v.y};
 }
 __device__ __forceinline__ void stcg(zd *p, zd v) { __stcg(reinterpret_cast<double2 *>(p), make_double2(v.re, v.im)); }
+__device__ __forceinline__ zf ldcg(const zf *p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+  return {v.x, v.y};
+}
 
 // ---- reductions ---------------------------------------------------------
 template <typename T>
