@@ -164,13 +164,19 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+__device__ __forceinline__ void red_release_add_u32(unsigned int *p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // All blocks of a co-resident (cooperative) grid meet here. Returns false,
 // on every thread of the block, if the barrier gave up: after `limit_ns` of
 // waiting, or when another block already reported a failure. The arrival
 // counter only grows: the e-th barrier of a launch is complete once it reaches
 // e * nblocks, so one atomic per block and a poll of the same word suffice
 // (`epoch` counts this block's barriers; it starts at 0 and the counter must be
-// zero at launch).
+// zero at launch). The arrival is a release reduction (no returned value to wait
+// for) and the poll an acquire load, which order the block's writes before, and
+// the other blocks' writes after, the barrier; the clock is read every 64 polls.
 __device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned int nblocks, unsigned int &epoch,
                                           uint64_t limit_ns) {
   __shared__ int s_ok;
@@ -179,16 +185,17 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned int nblocks, 
   if (threadIdx.x == 0) {
     int ok = 1;
     const unsigned int target = epoch * nblocks;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&b->count, 1u) + 1u;
-    if ((int)(target - arrived) > 0) {
+    red_release_add_u32(&b->count, 1u);
+    if ((int)(target - ld_acquire_u32(&b->count)) > 0) {
       const uint64_t t0 = global_ns();
+      unsigned int polls = 0;
       while ((int)(target - ld_acquire_u32(&b->count)) > 0) {
-        if (ld_volatile_i32(&b->err)) { ok = 0; break; }
-        if (global_ns() - t0 > limit_ns) { atomicExch(&b->err, 1); ok = 0; break; }
+        if ((++polls & 63u) == 0) {
+          if (ld_volatile_i32(&b->err)) { ok = 0; break; }
+          if (global_ns() - t0 > limit_ns) { atomicExch(&b->err, 1); ok = 0; break; }
+        }
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
