@@ -328,13 +328,9 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
         if (rb < m) P.tpart[(int64_t)b * m + rb] = t1 + th[rb];
       }
     }
-    qq_loc = warp_sum(qq_loc);
-    if (lane == 0) s_qq[wid] = (double)qq_loc;
-    __syncthreads();
-    if (tid == 0) {
-      double qsum = 0.0;
-      for (int w2 = 0; w2 < kCgThreads / 32; ++w2) qsum += s_qq[w2];
-      P.qq_part[b] = qsum;
+    if (wid == 0) {  // only warp 0 accumulated |q|^2
+      qq_loc = warp_sum(qq_loc);
+      if (lane == 0) P.qq_part[b] = (double)qq_loc;
     }
     if (!grid_sync(P.bar, G, epoch, P.limit_ns)) { ok = false; break; }
 
@@ -349,15 +345,18 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
       const zd ti = warp_sum_pair(re, im, lane);
       if (lane == 0) stcg(P.t + i, ti);
     }
-    if (wid == 0) {
-      double qs = 0.0;
+    if (wid == 0) {  // the CG scalars are formed by one thread (an FP64 division is a
+      double qs = 0.0;  // long chain of FP64 instructions) and read by all
       for (int c = lane; c < G; c += 32) qs += ldcg(P.qq_part + c);
       qs = warp_sum(qs);
-      if (lane == 0) s_scal[0] = qs;
+      if (lane == 0) {
+        s_scal[0] = qs;
+        s_scal[2] = qs > 0.0 ? gamma / qs : 0.0;
+      }
     }
     if (!grid_sync(P.bar, G, epoch, P.limit_ns)) { ok = false; break; }
     const double qq = s_scal[0];
-    const double alpha = qq > 0.0 ? gamma / qq : 0.0;
+    const double alpha = s_scal[2];
 
     // P3b: Np = Wp^* t (own rows); s -= alpha Np; u += alpha p; partial ||s||^2
     for (int i = tid; i < m; i += blockDim.x) v_s[i] = ldcg(P.t + i);
@@ -374,13 +373,20 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
       stcg(P.s + r0 + tid, s_reg);
       gl = fma(s_reg.re, s_reg.re, s_reg.im * s_reg.im);
     }
-    gl = warp_sum(gl);
-    if (lane == 0) s_qq[wid] = gl;
-    __syncthreads();
-    if (tid == 0) {
-      double gs = 0.0;
-      for (int w2 = 0; w2 < kCgThreads / 32; ++w2) gs += s_qq[w2];
-      P.gg_part[b] = gs;
+    if (r1 - r0 <= 32) {  // the own rows are all in warp 0
+      if (wid == 0) {
+        gl = warp_sum(gl);
+        if (lane == 0) P.gg_part[b] = gl;
+      }
+    } else {
+      gl = warp_sum(gl);
+      if (lane == 0) s_qq[wid] = gl;
+      __syncthreads();
+      if (tid == 0) {
+        double gs = 0.0;
+        for (int w2 = 0; w2 < kCgThreads / 32; ++w2) gs += s_qq[w2];
+        P.gg_part[b] = gs;
+      }
     }
     if (!grid_sync(P.bar, G, epoch, P.limit_ns)) { ok = false; break; }
 
@@ -390,11 +396,14 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
       double gs = 0.0;
       for (int c = lane; c < G; c += 32) gs += ldcg(P.gg_part + c);
       gs = warp_sum(gs);
-      if (lane == 0) s_scal[1] = gs;
+      if (lane == 0) {
+        s_scal[1] = gs;
+        s_scal[3] = gamma > 0.0 ? gs / gamma : 0.0;
+      }
     }
     __syncthreads();
     const double gnew = s_scal[1];
-    const double beta = gamma > 0.0 ? gnew / gamma : 0.0;
+    const double beta = s_scal[3];
     if (tid < m) {
       zd pi = p_s[tid];
       pi.re = fma(beta, pi.re, s_all.re);
