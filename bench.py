@@ -36,7 +36,8 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.0
 # DRAM bytes (read + write) per launch of a kernel class, from one ncu capture of the current
 # kernels on this workload: class 3 = qrp_reg_kernel<16> (16.91 + 2.77 MB) + prinv_kernel<1>
 # (2.14 MB + 0.5 KB). Y (16 MiB) stays in L2 through the QR, so traffic is one read of Y.
-PROFILED_TRAFFIC = {3: 21.82e6}
+# Class 5 (fused CG) per iteration: 2.059 GB read + 7.5 MB written over a 10-iteration launch.
+PROFILED_TRAFFIC = {3: 21.82e6, 5: (2.059e9 + 7.5e6) / 10}
 KERNEL_CLASSES = {0: "cg_adjoint_product", 1: "cg_forward_product", 2: "exact_residual", 3: "pivoted_qr",
                   4: "srft_sketch", 5: "cg_fused"}
 REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
@@ -478,6 +479,14 @@ def main():
     else:                   # separate A^* w and A q passes
         cg_ms = (stats[0][1] + stats[1][1]) / max(1, stats[0][0] + stats[1][0])
     cg_gbs = m * n * (8 if mixed else 16) / (cg_ms / 1000.0) / 1e9 if cg_ms > 0 else None
+    cg_roof = None
+    if cg_gbs:
+        # one pass over A per CG iteration (algorithmic bytes), launch overhead included
+        cg_roof = {"bound": "hbm", "achieved": cg_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                   "frac": cg_gbs / pk["hbm_gbs"], "bytes_per_iteration": m * n * (8 if mixed else 16),
+                   "traffic": (PROFILED_TRAFFIC.get(5) if (m, n) == (W["m"], W["n"]) and stats[5][0] > 0
+                               else None),
+                   "peak_source": pk_kind}
     breakdown = {KERNEL_CLASSES[k]: {"launches": v[0], "ms_total": v[1]} for k, v in stats.items()}
 
     err_main = err_other = None
@@ -515,6 +524,7 @@ def main():
                                              "rel_err_vs_oracle": err_other,
                                              "err_bound": infos_other[-1][1]["err_bound"]},
         "cg_matvec_gbs": cg_gbs,
+        "cg_matvec_roofline": cg_roof,
         "roofline": roof,
         "kernel_breakdown": breakdown,
         "cpu_baseline": cpu,
