@@ -245,6 +245,22 @@ minnorm_status minnorm_get_factor(minnorm_plan_t plan, void *R_out, void *piv_ou
 minnorm_status minnorm_cg_products(minnorm_plan_t plan, const void *A, int64_t lda,
                                    const void *w, void *q, void *t);
 
+/* The products of the block CG (Step 4 for 32 right-hand sides sharing A, as
+ * minnorm_solve_many runs it in MINNORM_MIXED): Q = A^* W and T = A Q for W
+ * (device, m x 32 complex128, row-major: column c of row i at i * 32 + c),
+ * Q (device, n x 32 complex128, row-major) and T (device, m x 32 complex128,
+ * row-major). W is rounded to complex64; Q = A^* W and T = A Q (with Q as
+ * returned, complex64) are computed on the tensor cores from exact three-way
+ * BF16 splits of both operands with FP32 accumulation (the six leading cross
+ * products: FP32-level accuracy); the partial sums of T over column ranges
+ * are added in FP64.
+ * A is the complex64 copy made by minnorm_sketch (complex128 plans) or A
+ * itself (complex64 plans). The plan must be MINNORM_MIXED. Synchronizes the
+ * plan's stream. Errors: EINVAL, ESTATE, ETIMEOUT (a bounded wait inside the
+ * tensor-core kernel expired). */
+minnorm_status minnorm_block_products(minnorm_plan_t plan, const void *A, int64_t lda,
+                                      const void *W, void *Q, void *T);
+
 /* The accurate residual of the refinement: for y = y_hi + y_lo (device, m
  * complex128 each; y_lo may be NULL) computes x = A^* y into x_hi + x_lo
  * (device, n complex128 each, a double-double pair) and r = b - A x (device,

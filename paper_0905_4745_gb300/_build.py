@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libminnorm.so")
-SOURCES = ["solver.cu", "sketch.cu", "qr.cu", "gemv.cu", "xprod.cu", "cgfused.cu", "blockcg.cu", "noalloc.cu", "vec.cu",
+SOURCES = ["solver.cu", "sketch.cu", "qr.cu", "gemv.cu", "xprod.cu", "cgfused.cu", "blockcg.cu", "tcblock.cu", "noalloc.cu", "vec.cu",
            "params.cpp"]
 HEADERS = ["common.cuh", "kernels.h", "params.h", "vec.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

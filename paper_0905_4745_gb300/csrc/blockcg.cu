@@ -382,10 +382,17 @@ cudaError_t launch_block_mm(const void *M, int m, const void *V, void *out, void
 }
 
 cudaError_t launch_block_adj(const BlockProductArgs &a, cudaStream_t st) {
-  note_launch();
-  block_adj_kernel<kBlockRhs><<<block_adj_parts(a.n), 128, 0, st>>>((const zf *)a.A, a.lda, (int)a.m, a.n,
-                                                                    (const zf *)a.W32, (zf *)a.Q, a.qqp, a.alldone);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (a.Bsplit && tc_block_supported(a.m, a.n, a.lda, a.A)) {
+    e = launch_tc_block_adj(a.A, a.m, a.n, a.lda, a.W32, a.Bsplit, a.Q, a.qqp, a.alldone, a.err, a.limit_ns, a.sms,
+                            st);
+  } else {
+    note_launch();
+    block_adj_kernel<kBlockRhs><<<block_adj_parts(a.n), 128, 0, st>>>((const zf *)a.A, a.lda, (int)a.m, a.n,
+                                                                      (const zf *)a.W32, (zf *)a.Q, a.qqp,
+                                                                      a.alldone);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   note_launch();
   block_alpha_kernel<kBlockRhs><<<1, 32 * kBlockRhs, 0, st>>>(a.qqp, block_adj_parts(a.n), a.gam, a.active, a.alpha,
@@ -394,12 +401,18 @@ cudaError_t launch_block_adj(const BlockProductArgs &a, cudaStream_t st) {
 }
 
 cudaError_t launch_block_fwd(const BlockProductArgs &a, cudaStream_t st) {
-  const int ns = a.nsplit;
-  const int64_t chunk = (a.n + ns - 1) / ns;
-  note_launch();
-  block_fwd_kernel<kBlockRhs><<<dim3((unsigned)((a.m + 63) / 64), (unsigned)ns), 128, 0, st>>>(
-      (const zf *)a.A, a.lda, (int)a.m, a.n, chunk, (const zf *)a.Q, (zf *)a.tpart, a.alldone);
-  cudaError_t e = cudaGetLastError();
+  int ns = a.nsplit;
+  cudaError_t e;
+  if (a.Bsplit2 && a.nsplit_tc > 0 && tc_block_supported(a.m, a.n, a.lda, a.A)) {
+    ns = a.nsplit_tc;
+    e = launch_tc_block_fwd(a.A, a.m, a.n, a.lda, a.Q, a.Bsplit2, a.tpart, ns, a.alldone, a.err, a.limit_ns, st);
+  } else {
+    const int64_t chunk = (a.n + ns - 1) / ns;
+    note_launch();
+    block_fwd_kernel<kBlockRhs><<<dim3((unsigned)((a.m + 63) / 64), (unsigned)ns), 128, 0, st>>>(
+        (const zf *)a.A, a.lda, (int)a.m, a.n, chunk, (const zf *)a.Q, (zf *)a.tpart, a.alldone);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   note_launch();
   block_fwd_reduce_kernel<kBlockRhs><<<(unsigned)std::min<int64_t>(1024, (a.m * kBlockRhs + 255) / 256), 256, 0,

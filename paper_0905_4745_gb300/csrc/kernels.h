@@ -167,6 +167,12 @@ struct BlockProductArgs {
   int nsplit;
   void *T;                 // m x KB complex128: A Q
   const int *alldone;
+  void *Bsplit;            // tc_split_bytes(m): BF16 pieces of W for the tensor-core product (or NULL)
+  void *Bsplit2;           // tc_split2_bytes(n): BF16 pieces of Q for the tensor-core product (or NULL)
+  int nsplit_tc;           // K ranges of the tensor-core T = A Q (tpart holds that many partials)
+  int *err;                // set to 1 when a bounded wait of the tensor-core kernel expired
+  uint64_t limit_ns;
+  int sms;
 };
 int block_adj_parts(int64_t n);
 int block_fwd_splits(int64_t m, int64_t n, int sms);
@@ -174,6 +180,17 @@ int block_col_parts(int64_t m);
 cudaError_t launch_block_mm(const void *M, int m, const void *V, void *out, void *out32, const int *alldone,
                             cudaStream_t st);
 cudaError_t launch_block_adj(const BlockProductArgs &a, cudaStream_t st);   // Q = A^* W, qq, alpha
+// tcblock.cu: Q = A^* W and T = A Q on the tensor cores (split BF16, FP32 accumulation)
+size_t tc_split_bytes(int64_t m);
+size_t tc_split2_bytes(int64_t n);
+int tc_fwd_splits(int64_t m, int64_t n, int sms);
+bool tc_block_supported(int64_t m, int64_t n, int64_t lda, const void *A);
+cudaError_t launch_tc_block_fwd(const void *A, int64_t m, int64_t n, int64_t lda, const void *Q32, void *Bsplit2,
+                                void *tpart, int nsplit, const int *alldone, int *err, uint64_t limit_ns,
+                                cudaStream_t st);
+cudaError_t launch_tc_block_adj(const void *A, int64_t m, int64_t n, int64_t lda, const void *W32, void *Bsplit,
+                                void *Q, float *qqp, const int *alldone, int *err, uint64_t limit_ns, int sms,
+                                cudaStream_t st);
 cudaError_t launch_block_fwd(const BlockProductArgs &a, cudaStream_t st);   // T = A Q
 cudaError_t launch_block_get_col(int m, const void *Bk, int c, void *v, cudaStream_t st);
 cudaError_t launch_block_set_col(int m, const void *v, int c, void *Bk, cudaStream_t st);

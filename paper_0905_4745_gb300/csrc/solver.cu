@@ -86,6 +86,9 @@ struct minnorm_plan_s {
        *d_bNp = nullptr, *d_bdY = nullptr, *d_bYh = nullptr, *d_bYl = nullptr, *d_bW32 = nullptr, *d_bQ = nullptr,
        *d_btpart = nullptr;
   float *d_bqqp = nullptr;
+  void *d_bsplit = nullptr;   // BF16 pieces of W for the tensor-core adjoint product
+  void *d_bsplit2 = nullptr;  // BF16 pieces of Q for the tensor-core forward product
+  int blk_nsplit_tc = 0;
   double *d_bpart = nullptr, *d_bscal = nullptr;  // scal: gam, gam0, alpha, beta (KB each)
   int *d_bint = nullptr;                           // use, active, iters (KB each), alldone
   int blk_nsplit = 1;
@@ -852,8 +855,12 @@ minnorm_status block_alloc(minnorm_plan_t plan) {
   ALLOC(plan->d_bW32, sizeof(zf) * (size_t)m * kBlockRhs);
   ALLOC(plan->d_bQ, sizeof(zf) * (size_t)n * kBlockRhs);
   ALLOC(plan->d_bqqp, sizeof(float) * (size_t)block_adj_parts(n) * kBlockRhs);
+  ALLOC(plan->d_bsplit, tc_split_bytes(m));
+  ALLOC(plan->d_bsplit2, tc_split2_bytes(n));
   plan->blk_nsplit = block_fwd_splits(m, n, plan->sms);
-  ALLOC(plan->d_btpart, sizeof(zf) * (size_t)plan->blk_nsplit * m * kBlockRhs);
+  plan->blk_nsplit_tc = tc_fwd_splits(m, n, plan->sms);
+  ALLOC(plan->d_btpart,
+        sizeof(zf) * (size_t)std::max(plan->blk_nsplit, plan->blk_nsplit_tc) * m * kBlockRhs);
   ALLOC(plan->d_bpart, sizeof(double) * (size_t)block_col_parts(m) * kBlockRhs);
   ALLOC(plan->d_bscal, sizeof(double) * 4 * kBlockRhs);
   ALLOC(plan->d_bint, sizeof(int) * (3 * kBlockRhs + 1));
@@ -905,6 +912,13 @@ minnorm_status block_inner_cg(minnorm_plan_t plan, const void *Acg, int64_t lda_
   pa.nsplit = plan->blk_nsplit;
   pa.T = plan->d_bT;
   pa.alldone = alldone;
+  pa.Bsplit = plan->d_bsplit;
+  pa.Bsplit2 = plan->d_bsplit2;
+  pa.nsplit_tc = plan->blk_nsplit_tc;
+  pa.err = plan->d_err;
+  pa.limit_ns = kBarrierLimitNs;
+  pa.sms = plan->sms;
+  CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
   int it = 0;
   while (it < maxit) {
     const int todo = std::min(4, maxit - it);
@@ -920,6 +934,13 @@ minnorm_status block_inner_cg(minnorm_plan_t plan, const void *Acg, int64_t lda_
     CK(cudaMemcpyAsync(plan->h_bint, plan->d_bint, sizeof(int) * (3 * kBlockRhs + 1), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (plan->h_bint[3 * kBlockRhs]) break;
+  }
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (err) {
+    plan->failed = true;
+    return MINNORM_ETIMEOUT;
   }
   int mx = 0;
   for (int c = 0; c < kBlockRhs; ++c) mx = std::max(mx, plan->h_bint[2 * kBlockRhs + c]);
@@ -1244,6 +1265,53 @@ minnorm_status minnorm_cg_products(minnorm_plan_t plan, const void *A, int64_t l
     if (t) CK(launch_gemv_fwd(plan->g_cg, Acg, plan->d_q, t, plan->d_part, nullptr, st));
   }
   return MINNORM_OK;
+}
+
+minnorm_status minnorm_block_products(minnorm_plan_t plan, const void *A, int64_t lda, const void *W, void *Q,
+                                      void *T) {
+  if (!plan || !A || !W || !Q || !T) return MINNORM_EINVAL;
+  if (lda < plan->n || !plan->fp32) return MINNORM_EINVAL;
+  if (plan->dtype == MINNORM_C128 && !plan->sketched) return MINNORM_ESTATE;
+  minnorm_status s = block_alloc(plan);
+  if (s != MINNORM_OK) return s;
+  cudaStream_t st = plan->st;
+  const int64_t m = plan->m, n = plan->n;
+  const void *Acg = plan->d_A32 ? (const void *)plan->d_A32 : A;
+  const int64_t lda_cg = plan->d_A32 ? n : lda;
+  double *gam = plan->d_bscal, *gam0 = gam + kBlockRhs, *alpha = gam0 + kBlockRhs;
+  int *use = plan->d_bint, *active = use + kBlockRhs, *alldone = active + 2 * kBlockRhs;
+  CK(cudaMemsetAsync(plan->d_bscal, 0, sizeof(double) * 4 * kBlockRhs, st));
+  CK(cudaMemsetAsync(plan->d_bint, 0, sizeof(int) * (3 * kBlockRhs + 1), st));
+  CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
+  CK(launch_narrow(m * kBlockRhs, W, plan->d_bW32, st));
+  BlockProductArgs pa{};
+  pa.A = Acg;
+  pa.m = m;
+  pa.n = n;
+  pa.lda = lda_cg;
+  pa.W32 = plan->d_bW32;
+  pa.Q = plan->d_bQ;
+  pa.qqp = plan->d_bqqp;
+  pa.gam = gam;
+  pa.active = active;
+  pa.alpha = alpha;
+  pa.tpart = plan->d_btpart;
+  pa.nsplit = plan->blk_nsplit;
+  pa.T = T;
+  pa.alldone = alldone;
+  pa.Bsplit = plan->d_bsplit;
+  pa.Bsplit2 = plan->d_bsplit2;
+  pa.nsplit_tc = plan->blk_nsplit_tc;
+  pa.err = plan->d_err;
+  pa.limit_ns = kBarrierLimitNs;
+  pa.sms = plan->sms;
+  CK(launch_block_adj(pa, st));
+  CK(launch_block_fwd(pa, st));
+  CK(launch_widen(n * kBlockRhs, plan->d_bQ, Q, st));
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return err ? MINNORM_ETIMEOUT : MINNORM_OK;
 }
 
 minnorm_status minnorm_residual_dd(minnorm_plan_t plan, const void *A, int64_t lda, const void *y_hi,

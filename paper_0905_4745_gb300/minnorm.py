@@ -24,7 +24,7 @@ EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_sketch", "
            "minnorm_solve_host", "minnorm_plan_destroy", "minnorm_status_string", "minnorm_get_sketch",
            "minnorm_get_factor", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats",
            "minnorm_launch_count", "minnorm_qr_noalloc", "minnorm_solve_many", "minnorm_batch_create",
-           "minnorm_batch_solve", "minnorm_batch_destroy", "minnorm_batch_kernel_stats"]
+           "minnorm_batch_solve", "minnorm_batch_destroy", "minnorm_batch_kernel_stats", "minnorm_block_products"]
 
 
 class MinnormError(RuntimeError):
@@ -72,6 +72,7 @@ def lib():
         L.minnorm_get_sketch.argtypes = [p, p]
         L.minnorm_get_factor.argtypes = [p, p, p]
         L.minnorm_cg_products.argtypes = [p, p, i64, p, p, p]
+        L.minnorm_block_products.argtypes = [p, p, i64, p, p, p]
         L.minnorm_residual_dd.argtypes = [p, p, i64, p, p, p, p, p, p]
         L.minnorm_kernel_stats.argtypes = [p, i32, C.POINTER(i32), C.POINTER(d)]
         L.minnorm_qr_noalloc.argtypes = [p, i64, i64, i64, p, p, p]
@@ -227,6 +228,12 @@ def minnorm_cg_products(plan, A, w, q=None, t=None, lda=None):
     lda = A.shape[-1] if lda is None else lda
     return _check(lib().minnorm_cg_products(plan, _ptr(A), int(lda), _ptr(w), _ptr(q), _ptr(t)),
                   "minnorm_cg_products")
+
+
+def minnorm_block_products(plan, A, W, Q, T, lda=None):
+    lda = A.shape[-1] if lda is None else lda
+    return _check(lib().minnorm_block_products(plan, _ptr(A), int(lda), _ptr(W), _ptr(Q), _ptr(T)),
+                  "minnorm_block_products")
 
 
 def minnorm_residual_dd(plan, A, y_hi, y_lo, b, r, x_hi, x_lo, lda=None):
