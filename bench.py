@@ -55,9 +55,10 @@ def parse():
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error check and CPU baseline")
     ap.add_argument("--m", type=int, default=W["m"], help="rows (profiling runs of a smaller case)")
     ap.add_argument("--n", type=int, default=W["n"], help="columns (profiling runs of a smaller case)")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "block"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "block", "products"],
                     help="plain: the benchmark line; batch / block: the batching and block right-hand-side "
-                         "workloads, measured on their own (one line each, not the benchmark line)")
+                         "workloads, measured on their own (one line each, not the benchmark line); products: "
+                         "the block-CG products alone (tensor cores), 4096x131072 complex64, 32 columns")
     return ap.parse_args()
 
 
@@ -344,10 +345,56 @@ def side_workload(args):
     return 0
 
 
+def products_workload(args):
+    """Q = A^* W and T = A Q of the block CG (minnorm_block_products: tensor cores, split BF16) on a
+    seeded 4096 x 131072 complex64 A (4.3 GB, larger than L2) and 32 columns; a step is one call
+    (both products, the W and Q conversions and the final synchronisation)."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_0905_4745_gb300 import minnorm as mn
+    m, n = 4096, 131072
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    A = torch.randn(m, n, dtype=torch.complex64, device="cuda", generator=gen)
+    Wm = torch.randn(m, 32, dtype=torch.complex128, device="cuda", generator=gen)
+    Q = torch.empty(n, 32, dtype=torch.complex128, device="cuda")
+    T = torch.empty(m, 32, dtype=torch.complex128, device="cuda")
+    plan = mn.minnorm_plan_create(m, n, 0, mn.C64, mn.MIXED, seed=1)
+    steps, warmup = max(1, args.steps), max(1, args.warmup)
+    for _ in range(warmup):
+        mn.minnorm_block_products(plan, A, Wm, Q, T)
+    torch.cuda.synchronize()
+    launches0 = mn.minnorm_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ck = Clocks(0)
+    ck.__enter__()
+    e0.record()
+    for _ in range(steps):
+        mn.minnorm_block_products(plan, A, Wm, Q, T)
+    e1.record()
+    torch.cuda.synchronize()
+    ck.__exit__()
+    mn.minnorm_plan_destroy(plan)
+    ms = e0.elapsed_time(e1) / steps
+    pk, kind = peaks()
+    gbs = 2 * 8.0 * m * n / (ms / 1000.0) / 1e9    # two passes over A per call
+    print(json.dumps({"metric": "block-CG products (Q = A^* W and T = A Q, 32 columns)", "value": 1000.0 / ms,
+                      "unit": "calls/s", "ms_per_step": ms, "steps": steps, "warmup": warmup,
+                      "higher_is_better": True, "dtype": "bf16 x3 split -> f32 (tensor cores)", "data": "synthetic",
+                      "config": {"workload": "4096x131072 complex64 (4.3 GB), 32 right-hand sides", "m": m, "n": n},
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                   "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_source": kind,
+                                   "bytes_per_step": 2 * 8 * m * n},
+                      "gpu_launches": mn.minnorm_launch_count() - launches0, "clocks": ck.summary()}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "products":
+        return products_workload(args)
     if args.workload != "plain":
         return side_workload(args)
     import torch
