@@ -122,12 +122,14 @@ struct XprodArgs {
   int64_t chunk;
   void *xpart;            // xadj_partial_bytes(rows, cols): row-split partial sums of A^* y
   void *xfix;             // xfix_bytes(cols): x in 128-bit fixed point for the forward product
+  int xsplit;             // row splits of x = A^* y (0: xadj_splits); at most xadj_max_splits(rows)
 };
 cudaError_t launch_fix_prep(const void *A, int64_t lda, bool c64, int64_t rows, int64_t cols, void *afix,
                             int32_t *E, void *A32, cudaStream_t st);
 cudaError_t launch_xresidual(const XprodArgs &a, cudaStream_t st);
 size_t xprod_partial_bytes(int64_t rows, int nchunk);
 int xadj_splits(int64_t rows, int64_t cols);
+int xadj_max_splits(int64_t rows);
 size_t xadj_partial_bytes(int64_t rows, int64_t cols);
 size_t xfix_bytes(int64_t cols);
 

@@ -24,6 +24,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "../../include/minnorm.h"
@@ -133,6 +135,9 @@ struct minnorm_plan_s {
   int *d_F = nullptr;   // [0] = Fy, [1] = Fx
   int x_nchunk = 1;
   int64_t x_chunk = 1;
+  int x_nchunk_max = 1;   // the forward partial buffer holds this many column chunks
+  int x_split = 0;        // row splits of x = A^* y (0: the default)
+  bool x_tuned = false;
   // fused CG (mixed precision, m <= 512)
   bool fused_ok = false;
   zf *d_tpart = nullptr;
@@ -458,7 +463,8 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
     while (row_blocks * nchunk < 8 * plan->sms && n / (nchunk * 2) >= 1024) nchunk *= 2;
     plan->x_nchunk = (int)nchunk;
     plan->x_chunk = (n + nchunk - 1) / nchunk;
-    ALLOC(plan->d_xpart, xprod_partial_bytes(m, plan->x_nchunk));
+    plan->x_nchunk_max = n / (nchunk * 2) >= 256 ? (int)nchunk * 2 : (int)nchunk;
+    ALLOC(plan->d_xpart, xprod_partial_bytes(m, plan->x_nchunk_max));
     ALLOC(plan->d_xapart, xadj_partial_bytes(m, n));
     ALLOC(plan->d_xfix, xfix_bytes(n));
   }
@@ -720,7 +726,91 @@ XprodArgs xargs(minnorm_plan_t plan, const void *b) {
   a.chunk = plan->x_chunk;
   a.xpart = plan->d_xapart;
   a.xfix = plan->d_xfix;
+  a.xsplit = plan->x_split;
   return a;
+}
+
+// ---- autotuning of the exact residual's work split ------------------------------
+// The exact residual (x = A^* y and b - A x in 128-bit fixed point) gives bit-identical
+// results for any split of its work, so on a plan's first residual the candidates
+// (column chunks of the forward pass: the default, half, twice; row splits of the
+// adjoint pass: 1, 2, 4, 8) are run on the actual data, timed with CUDA events on the
+// plan's stream, and the fastest kept, also for later plans of the same shape (process-
+// wide cache). Small systems keep the default split (a residual there takes microseconds).
+struct TuneKey {
+  int64_t m, n;
+  int sms;
+  bool operator<(const TuneKey &o) const {
+    return m != o.m ? m < o.m : (n != o.n ? n < o.n : sms < o.sms);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tune_cache;  // -> (column chunks, row splits)
+
+minnorm_status tune_xresidual(minnorm_plan_t plan, const void *b) {
+  plan->x_tuned = true;
+  const int64_t m = plan->m, n = plan->n;
+  if (m * n < ((int64_t)1 << 22)) return MINNORM_OK;
+  const TuneKey key{m, n, plan->sms};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      plan->x_nchunk = it->second.first;
+      plan->x_chunk = (n + plan->x_nchunk - 1) / plan->x_nchunk;
+      plan->x_split = it->second.second;
+      return MINNORM_OK;
+    }
+  }
+  cudaStream_t st = plan->st;
+  std::vector<int> chunks = {plan->x_nchunk};
+  if (plan->x_nchunk > 1) chunks.push_back(plan->x_nchunk / 2);
+  if (plan->x_nchunk_max > plan->x_nchunk) chunks.push_back(plan->x_nchunk_max);
+  std::vector<int> splits;
+  for (int sp = 1; sp <= xadj_max_splits(m); sp *= 2) splits.push_back(sp);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = INFINITY;
+  int best_c = plan->x_nchunk, best_s = 0;
+  for (int nc : chunks) {
+    for (int sp : splits) {
+      XprodArgs a = xargs(plan, b);
+      a.nchunk = nc;
+      a.chunk = (n + nc - 1) / nc;
+      a.xsplit = sp;
+      CK(launch_xresidual(a, st));  // warm
+      CK(cudaEventRecord(e0, st));
+      CK(launch_xresidual(a, st));
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_c = nc;
+        best_s = sp;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  plan->x_nchunk = best_c;
+  plan->x_chunk = (n + best_c - 1) / best_c;
+  plan->x_split = best_s;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = {best_c, best_s};
+  return MINNORM_OK;
+}
+
+// one exact residual with the plan's (tuned) split
+minnorm_status xresidual(minnorm_plan_t plan, const void *b) {
+  if (!plan->x_tuned) {
+    minnorm_status s = tune_xresidual(plan, b);
+    if (s != MINNORM_OK) return s;
+  }
+  CK(launch_xresidual(xargs(plan, b), plan->st));
+  return MINNORM_OK;
 }
 
 minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const void *b, double eps, void *x,
@@ -769,7 +859,7 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
     CK(launch_dd_accumulate(m, plan->d_yh, plan->d_yl, plan->d_dy, st));
     {
       Timed tm(plan, 2);
-      CK(launch_xresidual(xargs(plan, b), st));
+      { minnorm_status xs = xresidual(plan, b); if (xs != MINNORM_OK) return xs; }
       dd_passes += 2;
     }
   }
@@ -1018,7 +1108,7 @@ minnorm_status solve_block_chunk(minnorm_plan_t plan, const void *A, int64_t lda
       CK(launch_block_get_col((int)m, plan->d_bYl, c, plan->d_yl, st));
       {
         Timed tm(plan, 2);
-        CK(launch_xresidual(xargs(plan, B + c * ldb), st));
+        { minnorm_status xs = xresidual(plan, B + c * ldb); if (xs != MINNORM_OK) return xs; }
       }
       col[c].passes += 2;
       CK(launch_block_set_col((int)m, plan->d_r, c, plan->d_bR, st));
@@ -1331,6 +1421,13 @@ minnorm_status minnorm_residual_dd(minnorm_plan_t plan, const void *A, int64_t l
 }
 
 int64_t minnorm_launch_count(void) { return (int64_t)launches_so_far(); }
+
+minnorm_status minnorm_plan_tuning(minnorm_plan_t plan, int32_t *x_chunks, int32_t *x_splits) {
+  if (!plan || !x_chunks || !x_splits) return MINNORM_EINVAL;
+  *x_chunks = plan->x_nchunk;
+  *x_splits = plan->x_split > 0 ? plan->x_split : xadj_splits(plan->m, plan->n);
+  return plan->x_tuned ? MINNORM_OK : MINNORM_ESTATE;
+}
 
 minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *launches, double *ms) {
   if (!plan || k < 0 || k > 5 || !launches || !ms) return MINNORM_EINVAL;

@@ -367,7 +367,15 @@ int xadj_splits(int64_t rows, int64_t cols) {
   while (s < 8 && nbx * s < 4096 && rows / (2 * s) >= 64) s *= 2;
   return s;
 }
-size_t xadj_partial_bytes(int64_t rows, int64_t cols) { return sizeof(i128c) * (size_t)cols * xadj_splits(rows, cols); }
+// largest row split the partial buffer is sized for: up to 8, each split >= 64 rows
+int xadj_max_splits(int64_t rows) {
+  int s = 1;
+  while (s < 8 && rows / (2 * s) >= 64) s *= 2;
+  return s;
+}
+size_t xadj_partial_bytes(int64_t rows, int64_t cols) {
+  return sizeof(i128c) * (size_t)cols * xadj_max_splits(rows);
+}
 size_t xfix_bytes(int64_t cols) { return sizeof(i128c) * (size_t)cols; }
 
 cudaError_t launch_xresidual(const XprodArgs &a, cudaStream_t st) {
@@ -380,7 +388,7 @@ cudaError_t launch_xresidual(const XprodArgs &a, cudaStream_t st) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {
     const int64_t nbx = (a.cols + kXadjThreads - 1) / kXadjThreads;
-    const int nsplit = xadj_splits(a.rows, a.cols);
+    const int nsplit = a.xsplit > 0 ? a.xsplit : xadj_splits(a.rows, a.cols);
     note_launch();
     xadj_kernel<<<dim3((unsigned)nbx, (unsigned)nsplit), kXadjThreads, 0, st>>>(
         (const fixc *)a.afix, a.rows, a.cols, (const i128c *)a.yfix, (i128c *)a.xpart);

@@ -24,7 +24,7 @@ EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_sketch", "
            "minnorm_solve_host", "minnorm_plan_destroy", "minnorm_status_string", "minnorm_get_sketch",
            "minnorm_get_factor", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats",
            "minnorm_launch_count", "minnorm_qr_noalloc", "minnorm_solve_many", "minnorm_batch_create",
-           "minnorm_batch_solve", "minnorm_batch_destroy", "minnorm_batch_kernel_stats", "minnorm_block_products"]
+           "minnorm_batch_solve", "minnorm_batch_destroy", "minnorm_batch_kernel_stats", "minnorm_block_products", "minnorm_plan_tuning"]
 
 
 class MinnormError(RuntimeError):
@@ -73,6 +73,7 @@ def lib():
         L.minnorm_get_factor.argtypes = [p, p, p]
         L.minnorm_cg_products.argtypes = [p, p, i64, p, p, p]
         L.minnorm_block_products.argtypes = [p, p, i64, p, p, p]
+        L.minnorm_plan_tuning.argtypes = [p, C.POINTER(i32), C.POINTER(i32)]
         L.minnorm_residual_dd.argtypes = [p, p, i64, p, p, p, p, p, p]
         L.minnorm_kernel_stats.argtypes = [p, i32, C.POINTER(i32), C.POINTER(d)]
         L.minnorm_qr_noalloc.argtypes = [p, i64, i64, i64, p, p, p]
@@ -240,6 +241,15 @@ def minnorm_residual_dd(plan, A, y_hi, y_lo, b, r, x_hi, x_lo, lda=None):
     lda = A.shape[-1] if lda is None else lda
     return _check(lib().minnorm_residual_dd(plan, _ptr(A), int(lda), _ptr(y_hi), _ptr(y_lo), _ptr(b),
                                             _ptr(r), _ptr(x_hi), _ptr(x_lo)), "minnorm_residual_dd")
+
+
+def minnorm_plan_tuning(plan):
+    """(column chunks, row splits, tuned) of the plan's exact residual."""
+    c, r = C.c_int32(), C.c_int32()
+    st = lib().minnorm_plan_tuning(plan, C.byref(c), C.byref(r))
+    if st not in (OK, ESTATE):
+        raise MinnormError(st, "minnorm_plan_tuning")
+    return c.value, r.value, st == OK
 
 
 def minnorm_kernel_stats(plan, k):
