@@ -206,6 +206,18 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
   const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
   int it = 0;
   bool ok = true;
+  // the first sweep's first stages do not depend on w: start them now, under the set-up
+  // and the first w = Wp p (until that sweep begins they are this thread's to wait for)
+  const int nearly = nsp < kStages ? nsp : kStages;
+  bool early_pending = !done && nearly > 0;
+  if (tid == 0 && early_pending) {
+    for (int e = 0; e < nearly; ++e) {
+      mbar_expect_tx(&mbar[e], stage_tx);
+      for (int bx = 0; bx < nbox; ++bx)
+        tma_load_2d(stage(e) + bx * kBoxRows * 128, &amap, (b + e * G) * 2 * kPanel, bx * kBoxRows, &mbar[e],
+                    e >= nsp - P.keep ? pol_last : pol_first);
+    }
+  }
 
   while (!done && it < P.maxit) {
     // P1: w = Wp p (own rows)
@@ -238,9 +250,7 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
         tma_load_2d(stage(sl) + bx * kBoxRows * 128, &amap, (b + ipn * G) * 2 * kPanel, bx * kBoxRows, &mbar[sl],
                     pol);
     };
-    if (tid == 0 && it == 0) {
-      for (int e = 0; e < kStages && e < nsp; ++e) issue(e);
-    }
+    early_pending = false;  // issued before the loop; waited for below like any other stage
     for (int e = 0; e < nsp; ++e) {
       const int ip = fwd ? e : nsp - 1 - e;
       const int st = ip % kStages;
@@ -415,6 +425,9 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
     if (gnew <= P.tol2 * gamma0 || !(qq > 0.0)) done = true;
     __syncthreads();
   }
+  if (early_pending && tid == 0) {  // the loop ended before the first sweep: wait for its copies
+    for (int e = 0; e < nearly; ++e) mbar_wait(&mbar[e], 0, P.limit_ns);
+  }
   if (!ok) {
     if (tid == 0) atomicExch(P.err, 1);
     // no TMA load is left in flight: every issued stage was waited for above
@@ -502,12 +515,12 @@ cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int NP = (int)((a.n + kPanel - 1) / kPanel);
   const int G = a.grid < NP ? a.grid : NP;
-  // sub-panels per CTA kept in L2 between sweeps: about 60 % of L2
+  // sub-panels per CTA kept in L2 between sweeps: about 80 % of L2
   int dev = 0, l2 = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
     l2 = 0;
   const double stage_bytes = (double)P.nbox * kBoxRows * 128;
-  P.keep = (int)(0.6 * (double)l2 / ((double)G * stage_bytes));
+  P.keep = (int)(0.8 * (double)l2 / ((double)G * stage_bytes));
   void *args[] = {(void *)&map, (void *)&P};
   note_launch();
   return cudaLaunchCooperativeKernel((const void *)cg_fused_kernel, dim3(G), dim3(kCgThreads), args, smem, st);
