@@ -136,10 +136,12 @@ __device__ __forceinline__ zd warp_sum_pair(double re, double im, int lane) {
 }
 
 // out[i] = sum_k M[i][k] v[k] for i in [r0, r1): one warp per row (FP64), v in
-// shared memory; out is global (gout) or shared (sout[i - r0])
-__device__ __forceinline__ void rows_dot(const zd *__restrict__ M, const zd *v, int m, int r0, int r1, zd *gout,
-                                         zd *sout) {
+// shared memory; out is global (gout) or shared (sout[i - r0]). Returns, in lane 0,
+// the warp's last row.
+__device__ __forceinline__ zd rows_dot(const zd *__restrict__ M, const zd *v, int m, int r0, int r1, zd *gout,
+                                       zd *sout) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  zd last = {0.0, 0.0};
   for (int i = r0 + wid; i < r1; i += nw) {
     const zd *row = M + (int64_t)i * m;
     double re = 0.0, im = 0.0;
@@ -153,7 +155,9 @@ __device__ __forceinline__ void rows_dot(const zd *__restrict__ M, const zd *v, 
       if (gout) gout[i] = r;
       else sout[i - r0] = r;
     }
+    last = r;
   }
+  return last;
 }
 
 __global__ void __launch_bounds__(kCgThreads, 1)
@@ -195,6 +199,12 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
     p_s[i] = gi;
     loc = fma(gi.re, gi.re, fma(gi.im, gi.im, loc));
   }
+  // dy = Wp u = sum over the iterations of alpha_k Wp p_k = sum alpha_k w_k: when every warp
+  // has at most one own row, lane 0 of warp w accumulates row r0 + w of it from the w_k it
+  // computed (no product with Wp after the loop)
+  const bool acc_dy = (m + G - 1) / G <= kCgThreads / 32;
+  const bool dy_row = acc_dy && lane == 0 && r0 + wid < r1;
+  zd w_mine = {0.0, 0.0}, dy_mine = {0.0, 0.0};
   // s and u of the own row r0 + tid live in registers (only this CTA updates them)
   const bool own_su = tid < r1 - r0;
   zd s_reg = own_su ? P.g[r0 + tid] : zd{0.0, 0.0};
@@ -221,7 +231,7 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
 
   while (!done && it < P.maxit) {
     // P1: w = Wp p (own rows)
-    rows_dot(P.Wp, p_s, m, r0, r1, P.w, nullptr);
+    w_mine = rows_dot(P.Wp, p_s, m, r0, r1, P.w, nullptr);
     if (!grid_sync(P.bar, G, epoch, P.limit_ns)) { ok = false; break; }
 
     // P2: q = A^* w and t = A q over the own sub-panels, A read once.
@@ -367,6 +377,10 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
     if (!grid_sync(P.bar, G, epoch, P.limit_ns)) { ok = false; break; }
     const double qq = s_scal[0];
     const double alpha = s_scal[2];
+    if (dy_row) {
+      dy_mine.re = fma(alpha, w_mine.re, dy_mine.re);
+      dy_mine.im = fma(alpha, w_mine.im, dy_mine.im);
+    }
 
     // P3b: Np = Wp^* t (own rows); s -= alpha Np; u += alpha p; partial ||s||^2
     for (int i = tid; i < m; i += blockDim.x) v_s[i] = ldcg(P.t + i);
@@ -435,13 +449,17 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
   }
   // dy = Wp u
   if (own_su) stcg(P.u + r0 + tid, u_reg);
-  if (!grid_sync(P.bar, G, epoch, P.limit_ns)) {
-    if (tid == 0) atomicExch(P.err, 1);
-    return;
+  if (acc_dy) {
+    if (dy_row) P.dy[r0 + wid] = dy_mine;
+  } else {
+    if (!grid_sync(P.bar, G, epoch, P.limit_ns)) {
+      if (tid == 0) atomicExch(P.err, 1);
+      return;
+    }
+    for (int i = tid; i < m; i += blockDim.x) v_s[i] = ldcg(P.u + i);
+    __syncthreads();
+    rows_dot(P.Wp, v_s, m, r0, r1, P.dy, nullptr);
   }
-  for (int i = tid; i < m; i += blockDim.x) v_s[i] = ldcg(P.u + i);
-  __syncthreads();
-  rows_dot(P.Wp, v_s, m, r0, r1, P.dy, nullptr);
   if (b == 0 && tid == 0) {
     P.sc->iters = it;
     P.sc->gamma = gamma;
