@@ -36,8 +36,7 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.0
 # DRAM bytes (read + write) per launch of a kernel class, from one ncu capture of the current
 # kernels on this workload: class 3 = qrp_reg_kernel<16> (16.91 + 2.77 MB) + prinv_kernel<1>
 # (2.14 MB + 0.5 KB). Y (16 MiB) stays in L2 through the QR, so traffic is one read of Y.
-# Class 5 (fused CG) per iteration: 2.059 GB read + 7.5 MB written over a 10-iteration launch.
-PROFILED_TRAFFIC = {3: 21.82e6, 5: (2.059e9 + 7.5e6) / 10}
+PROFILED_TRAFFIC = {3: 21.82e6}
 KERNEL_CLASSES = {0: "cg_adjoint_product", 1: "cg_forward_product", 2: "exact_residual", 3: "pivoted_qr",
                   4: "srft_sketch", 5: "cg_fused"}
 REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
