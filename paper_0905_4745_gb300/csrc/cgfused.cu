@@ -17,8 +17,9 @@
 // the ones read just before them were loaded with an L2 evict-last hint. The
 // FP64 parts (w = Wp p, Np = Wp^* t, the CG scalars) are spread over the CTAs by
 // rows, between four grid barriers per iteration (bounded waits, see
-// common.cuh); s and u of a CTA's rows stay in its registers. The search
-// direction p is kept, identically, in every CTA's shared memory.
+// common.cuh); s and u of a CTA's rows stay in its registers, and dy = Wp u is
+// accumulated as the sum of alpha_k w_k by the owners of the rows of w. The
+// search direction p is kept, identically, in every CTA's shared memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
