@@ -142,9 +142,11 @@ struct minnorm_plan_s {
   bool fused_ok = false;
   zf *d_tpart = nullptr;
   double *d_qqp = nullptr, *d_ggp = nullptr;
-  // host staging (minnorm_solve_host)
+  // host staging (minnorm_solve_host): A arrives in row blocks on a copy stream
   void *d_Ah = nullptr;
   zd *d_bh = nullptr, *d_xo = nullptr;
+  cudaStream_t st_copy = nullptr;
+  cudaEvent_t ev_host[9] = {};
   // host pinned scalars
   double *h_norms = nullptr;
   CgScalars *h_cg = nullptr;
@@ -612,6 +614,89 @@ minnorm_status sketch_impl(minnorm_plan_t plan, const void *A, int64_t lda) {
   minnorm_status s = sketch_transform(plan, A, lda);
   if (s != MINNORM_OK) return s;
   s = sketch_factor(plan);
+  if (s != MINNORM_OK) return s;
+  return sketch_finish(plan);
+}
+
+// ---- Steps 1-2 with A in host memory ------------------------------------------
+// A is copied to the plan's staging buffer in kHostBlocks row blocks on a copy stream, and
+// each block's part of Step 1 (fixed-point copy, chains, FFT) runs on the plan's stream as
+// soon as its rows have arrived: every kernel of the sketch is row-local, so the result is
+// the one sketch_transform gives over all rows, and the copy of block k + 1 overlaps the
+// sketch of block k. Power-of-two n (the Bluestein path keeps the single copy).
+static constexpr int kHostBlocks = 8;
+
+minnorm_status sketch_from_host(minnorm_plan_t plan, const void *A_host, int64_t lda) {
+  cudaStream_t st = plan->st;
+  const int64_t m = plan->m, n = plan->n;
+  const size_t es = plan->dtype == MINNORM_C128 ? sizeof(zd) : sizeof(zf);
+  const size_t rc = plan->fp32 ? sizeof(zf) : sizeof(zd);
+  const bool timing = plan->flags & MINNORM_FLAG_TIMING;
+  if (!plan->st_copy) {
+    CK(cudaStreamCreateWithFlags(&plan->st_copy, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : plan->ev_host) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  reset_stats(plan);
+  plan->sketched = false;
+  plan->g_hp.ld = n;
+  plan->g_cg.ld = n;
+  if (timing) {
+    plan->ev_sk0 = next_event(plan);
+    plan->ev_sk1 = next_event(plan);
+    CK(cudaEventRecord(plan->ev_sk0, st));
+  }
+  // the staging buffer is free once the plan's stream has finished its earlier work
+  CK(cudaEventRecord(plan->ev_host[kHostBlocks], st));
+  CK(cudaStreamWaitEvent(plan->st_copy, plan->ev_host[kHostBlocks], 0));
+  const int K = (int)std::min<int64_t>(kHostBlocks, m);
+  const bool via32 = plan->fp32 && plan->dtype == MINNORM_C128;
+  for (int k = 0; k < K; ++k) {
+    const int64_t r0 = m * k / K, r1 = m * (k + 1) / K, rows = r1 - r0;
+    char *Ab = static_cast<char *>(plan->d_Ah) + (size_t)r0 * n * es;
+    CK(cudaMemcpy2DAsync(Ab, es * n, static_cast<const char *>(A_host) + (size_t)r0 * lda * es, es * lda, es * n,
+                         rows, cudaMemcpyHostToDevice, plan->st_copy));
+    CK(cudaEventRecord(plan->ev_host[k], plan->st_copy));
+    CK(cudaStreamWaitEvent(st, plan->ev_host[k], 0));
+    zf *A32 = plan->d_A32 ? plan->d_A32 + r0 * n : nullptr;
+    CK(launch_fix_prep(Ab, n, plan->dtype == MINNORM_C64, rows, n,
+                       reinterpret_cast<char *>(plan->d_afix) + (size_t)r0 * n * 2 * sizeof(int64_t), plan->d_E + r0,
+                       A32, st));
+    const void *src = via32 ? (const void *)A32 : (const void *)Ab;
+    const bool src_c64 = via32 || plan->dtype == MINNORM_C64;
+    char *S1 = reinterpret_cast<char *>(plan->d_S1) + (size_t)r0 * n * rc;
+    char *S2 = reinterpret_cast<char *>(plan->d_S2) + (size_t)r0 * n * rc;
+    Timed tm(plan, 4);
+    ChainArgs c1{src, n, S1, n, plan->d_idx1, plan->d_ph1, plan->d_cs1, nullptr, plan->d_halo1,
+                 (int)n, kSeg, plan->cap1, (int)rows, src_c64, true, plan->fp32};
+    CK(launch_chain(c1, st));
+    ChainArgs c2{S1, n, S2, n, plan->d_idx2, plan->d_ph2, plan->d_cs2, plan->d_post,
+                 plan->d_halo2, (int)n, kSeg, plan->cap2, (int)rows, plan->fp32, false, plan->fp32};
+    CK(launch_chain(c2, st));
+    FftArgs f{};
+    f.tw = plan->d_tw;
+    f.logn = plan->logn;
+    f.logN1 = plan->logN1;
+    f.tj = plan->tj;
+    f.tk = plan->tk;
+    f.samp_off = plan->d_samp_off;
+    f.samp_t = plan->d_samp_t;
+    f.samp_loc = plan->d_samp_loc;
+    f.l = (int)plan->l;
+    f.rows = (int)rows;
+    f.Y = plan->d_Y;
+    f.ldy = plan->l;
+    f.row_offset = (int)r0;
+    f.real_fp32 = plan->fp32;
+    f.src = S2;
+    f.ld = n;
+    f.work = S1;
+    f.ldw = n;
+    CK(launch_fft(f, st));
+  }
+  if (plan->d_Ykeep)
+    CK(cudaMemcpyAsync(plan->d_Ykeep, plan->d_Y, sizeof(zd) * plan->l * m, cudaMemcpyDeviceToDevice, st));
+  if (timing) CK(cudaEventRecord(plan->ev_sk1, st));
+  minnorm_status s = sketch_factor(plan);
   if (s != MINNORM_OK) return s;
   return sketch_finish(plan);
 }
@@ -1282,10 +1367,17 @@ minnorm_status minnorm_solve_host(minnorm_plan_t plan, const void *A_host, int64
     ALLOC(plan->d_xo, sizeof(zd) * n);
   }
   cudaStream_t st = plan->st;
-  CK(cudaMemcpy2DAsync(plan->d_Ah, es * n, A_host, es * lda, es * n, m, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(plan->d_bh, b_host, sizeof(zd) * m, cudaMemcpyHostToDevice, st));
-  minnorm_status s = minnorm_sketch(plan, plan->d_Ah, n);
-  if (s != MINNORM_OK) return s;
+  minnorm_status s;
+  if (!plan->bluestein) {  // copy in row blocks, each sketched as it arrives
+    s = sketch_from_host(plan, A_host, lda);
+    if (s != MINNORM_OK) return s;
+    CK(cudaMemcpyAsync(plan->d_bh, b_host, sizeof(zd) * m, cudaMemcpyHostToDevice, st));
+  } else {
+    CK(cudaMemcpy2DAsync(plan->d_Ah, es * n, A_host, es * lda, es * n, m, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(plan->d_bh, b_host, sizeof(zd) * m, cudaMemcpyHostToDevice, st));
+    s = minnorm_sketch(plan, plan->d_Ah, n);
+    if (s != MINNORM_OK) return s;
+  }
   minnorm_status r = minnorm_solve(plan, plan->d_Ah, n, plan->d_bh, eps, plan->d_xo, info);
   if (r != MINNORM_OK && r != MINNORM_ENOCONV && r != MINNORM_EFLOOR) return r;
   CK(cudaMemcpyAsync(x_host, plan->d_xo, sizeof(zd) * n, cudaMemcpyDeviceToHost, st));
@@ -1297,6 +1389,11 @@ minnorm_status minnorm_plan_destroy(minnorm_plan_t plan) {
   if (!plan) return MINNORM_OK;
   if (plan->st) cudaStreamSynchronize(plan->st);
   else cudaDeviceSynchronize();
+  if (plan->st_copy) {
+    cudaStreamSynchronize(plan->st_copy);
+    cudaStreamDestroy(plan->st_copy);
+    for (cudaEvent_t e : plan->ev_host) cudaEventDestroy(e);
+  }
   for (void *p : plan->allocs) cudaFree(p);
   for (cudaEvent_t e : plan->event_pool) cudaEventDestroy(e);
   if (plan->h_norms) cudaFreeHost(plan->h_norms);
