@@ -45,8 +45,8 @@ namespace mn {
 namespace {
 
 constexpr int kTcThreads = 256;
-constexpr int kTcCols = 64;           // complex columns of A per tile (M = 128 floats)
-constexpr int kTcK = 64;              // rows of A per K-block
+constexpr int kTcCols = 64;           // Q: complex columns of A per tile (M = 128 floats)
+constexpr int kTcK = 64;              // K values per K-block (Q: rows of A; T: floats of A's rows)
 constexpr int kTcAStages = 3;         // FP32 tiles in flight
 constexpr int kTcAStage = kTcK * 2 * kTcCols * 4;  // 32 KB
 constexpr int kTcPiece = 128 * kTcK * 2;           // one BF16 operand: 16 KB
