@@ -514,7 +514,7 @@ def main():
         return ms, stats, infos, mn.minnorm_launch_count() - launches0, (ck.summary() if clocks else None)
 
     ms_main, stats, infos, launches, clk = timed(plans["main"], args.steps, args.warmup, clocks=True)
-    xc, xs, _ = mn.minnorm_plan_tuning(plans["main"])
+    xc, xs, ck, _ = mn.minnorm_plan_tuning(plans["main"])
     ms_max = reduce_max(pg, ms_main, device)
     value = aggregate_value(world, args.steps, ms_max)
     x_main = x.clone()
@@ -636,8 +636,9 @@ def main():
         "roofline": roof,
         "kernel_breakdown": breakdown,
         "cpu_baseline": cpu,
-        "tuning": {"exact_residual": {"column_chunks": xc, "row_splits": xs,
-                                      "how": "fastest of the candidates timed on the plan's first residual"}},
+        "tuning": {"exact_residual": {"column_chunks": xc, "row_splits": xs},
+                   "cg_fused": {"l2_keep_pct": ck},
+                   "how": "fastest of the candidates timed on the plan's first residual / inner solve"},
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": m * n * 16 + m * 16,
                 "d2h_bytes_per_step": n * 16},
         "gpu_launches": launches,

@@ -273,13 +273,16 @@ minnorm_status minnorm_residual_dd(minnorm_plan_t plan, const void *A, int64_t l
                                    const void *y_hi, const void *y_lo, const void *b,
                                    void *r, void *x_hi, void *x_lo);
 
-/* The work split the plan's exact residual uses: *x_chunks column chunks of
- * b - A x and *x_splits row splits of x = A^* y. A plan picks them by timing
- * the candidates on its first residual (CUDA events on its stream; the
- * residual is exact, so every split gives the same bits) and keeps the choice
- * for later plans of the same shape in this process. Returns ESTATE (with the
- * default split) while the plan has not yet run a residual. Errors: EINVAL. */
-minnorm_status minnorm_plan_tuning(minnorm_plan_t plan, int32_t *x_chunks, int32_t *x_splits);
+/* The schedule choices of the plan's autotuner: *x_chunks column chunks of
+ * b - A x and *x_splits row splits of x = A^* y in the exact residual, and
+ * *cg_l2_keep_pct, the share of L2 (percent) into which the fused CG loads the
+ * tail of each sweep over A for the next, reversed sweep. A plan picks them by
+ * timing the candidates on its first residual and its first inner solve (CUDA
+ * events on its stream; every candidate gives the same bits) and keeps the
+ * choices for later plans of the same shape in this process. Returns ESTATE
+ * (with the defaults) while the plan has not yet run a residual. Errors: EINVAL. */
+minnorm_status minnorm_plan_tuning(minnorm_plan_t plan, int32_t *x_chunks, int32_t *x_splits,
+                                   int32_t *cg_l2_keep_pct);
 
 /* Number of kernels this library has launched in the calling process so far
  * (host-side count of every launch it enqueues, on any plan). */

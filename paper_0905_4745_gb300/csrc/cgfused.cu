@@ -534,12 +534,13 @@ cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int NP = (int)((a.n + kPanel - 1) / kPanel);
   const int G = a.grid < NP ? a.grid : NP;
-  // sub-panels per CTA kept in L2 between sweeps: about 80 % of L2
+  // sub-panels per CTA kept in L2 between sweeps: a share of L2 (80 % unless tuned)
   int dev = 0, l2 = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
     l2 = 0;
   const double stage_bytes = (double)P.nbox * kBoxRows * 128;
-  P.keep = (int)(0.8 * (double)l2 / ((double)G * stage_bytes));
+  const double frac = a.keep_frac >= 0.0 ? a.keep_frac : 0.8;
+  P.keep = (int)(frac * (double)l2 / ((double)G * stage_bytes));
   void *args[] = {(void *)&map, (void *)&P};
   note_launch();
   return cudaLaunchCooperativeKernel((const void *)cg_fused_kernel, dim3(G), dim3(kCgThreads), args, smem, st);

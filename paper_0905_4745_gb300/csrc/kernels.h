@@ -149,6 +149,8 @@ struct CgFusedArgs {
   int *err;
   uint64_t limit_ns;
   int grid;                // CTAs (one per SM)
+  double keep_frac;        // share of L2 the tail of each sweep is loaded into with an evict-last hint
+                           // (negative: the default); a cache hint only, results do not depend on it
 };
 bool cg_fused_supported(int64_t m, int64_t n, int64_t lda, const void *A);
 cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st);

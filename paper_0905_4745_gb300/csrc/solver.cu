@@ -138,6 +138,8 @@ struct minnorm_plan_s {
   int x_nchunk_max = 1;   // the forward partial buffer holds this many column chunks
   int x_split = 0;        // row splits of x = A^* y (0: the default)
   bool x_tuned = false;
+  double cg_keep = -1.0;  // fused CG: share of L2 kept between sweeps (negative: the default)
+  bool cg_tuned = false;
   // fused CG (mixed precision, m <= 512)
   bool fused_ok = false;
   zf *d_tpart = nullptr;
@@ -701,6 +703,78 @@ minnorm_status sketch_from_host(minnorm_plan_t plan, const void *A_host, int64_t
   return sketch_finish(plan);
 }
 
+// autotuning caches, keyed by the system's shape and the SM count (process-wide)
+struct TuneKey {
+  int64_t m, n;
+  int sms;
+  bool operator<(const TuneKey &o) const {
+    return m != o.m ? m < o.m : (n != o.n ? n < o.n : sms < o.sms);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tune_cache;  // -> (column chunks, row splits)
+static std::map<TuneKey, double> g_cg_keep_cache;             // -> fused CG L2 share
+
+// The fused CG's L2 share (how much of each sweep's tail is loaded with an evict-last hint
+// for the next, reversed sweep) is a cache hint: every choice gives the same bits. On a plan's
+// first inner solve the candidates run that solve (from the same g, so the run afterwards is
+// unchanged) and the fastest is kept, for later plans of the same shape too. Small systems,
+// whose A fits in L2, keep the default.
+minnorm_status tune_cg_keep(minnorm_plan_t plan, CgFusedArgs a) {
+  plan->cg_tuned = true;
+  const int64_t m = plan->m, n = plan->n;
+  if (m * n * (int64_t)sizeof(zf) < ((int64_t)64 << 20)) return MINNORM_OK;
+  const TuneKey key{m, n, plan->sms};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_cg_keep_cache.find(key);
+    if (it != g_cg_keep_cache.end()) {
+      plan->cg_keep = it->second;
+      return MINNORM_OK;
+    }
+  }
+  cudaStream_t st = plan->st;
+  const double cand[] = {0.0, 0.4, 0.6, 0.8, 1.0};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = INFINITY;
+  double best_f = -1.0;
+  for (double f : cand) {
+    a.keep_frac = f;
+    for (int rep = 0; rep < 2; ++rep) {  // warm, then timed
+      CK(cudaMemsetAsync(plan->d_bar, 0, sizeof(GridBarrier), st));
+      CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
+      if (rep == 1) CK(cudaEventRecord(e0, st));
+      CK(launch_cg_fused(a, st));
+      if (rep == 1) CK(cudaEventRecord(e1, st));
+    }
+    CK(cudaEventSynchronize(e1));
+    int err = 0;
+    CK(cudaMemcpy(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      plan->failed = true;
+      return MINNORM_ETIMEOUT;
+    }
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_f = f;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaMemsetAsync(plan->d_bar, 0, sizeof(GridBarrier), st));
+  CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
+  plan->cg_keep = best_f;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_cg_keep_cache[key] = best_f;
+  return MINNORM_OK;
+}
+
 // ---- Steps 3-5 --------------------------------------------------------------
 // Inner solve: CG on (Wp^* A A^* Wp) du = g, Wp = P R^{-1}; dy = Wp du.
 minnorm_status inner_cg(minnorm_plan_t plan, const void *Acg, double tol, int maxit, int *iters) {
@@ -733,6 +807,11 @@ minnorm_status inner_cg(minnorm_plan_t plan, const void *Acg, double tol, int ma
     a.err = plan->d_err;
     a.limit_ns = kBarrierLimitNs;
     a.grid = plan->sms;
+    if (!plan->cg_tuned) {
+      minnorm_status ts = tune_cg_keep(plan, a);
+      if (ts != MINNORM_OK) return ts;
+    }
+    a.keep_frac = plan->cg_keep;
     {
       Timed tm(plan, 5);
       CK(launch_cg_fused(a, st));
@@ -822,15 +901,6 @@ XprodArgs xargs(minnorm_plan_t plan, const void *b) {
 // adjoint pass: 1, 2, 4, 8) are run on the actual data, timed with CUDA events on the
 // plan's stream, and the fastest kept, also for later plans of the same shape (process-
 // wide cache). Small systems keep the default split (a residual there takes microseconds).
-struct TuneKey {
-  int64_t m, n;
-  int sms;
-  bool operator<(const TuneKey &o) const {
-    return m != o.m ? m < o.m : (n != o.n ? n < o.n : sms < o.sms);
-  }
-};
-static std::mutex g_tune_mu;
-static std::map<TuneKey, std::pair<int, int>> g_tune_cache;  // -> (column chunks, row splits)
 
 minnorm_status tune_xresidual(minnorm_plan_t plan, const void *b) {
   plan->x_tuned = true;
@@ -1519,10 +1589,12 @@ minnorm_status minnorm_residual_dd(minnorm_plan_t plan, const void *A, int64_t l
 
 int64_t minnorm_launch_count(void) { return (int64_t)launches_so_far(); }
 
-minnorm_status minnorm_plan_tuning(minnorm_plan_t plan, int32_t *x_chunks, int32_t *x_splits) {
-  if (!plan || !x_chunks || !x_splits) return MINNORM_EINVAL;
+minnorm_status minnorm_plan_tuning(minnorm_plan_t plan, int32_t *x_chunks, int32_t *x_splits,
+                                   int32_t *cg_l2_keep_pct) {
+  if (!plan || !x_chunks || !x_splits || !cg_l2_keep_pct) return MINNORM_EINVAL;
   *x_chunks = plan->x_nchunk;
   *x_splits = plan->x_split > 0 ? plan->x_split : xadj_splits(plan->m, plan->n);
+  *cg_l2_keep_pct = (int32_t)std::lround(100.0 * (plan->cg_keep >= 0.0 ? plan->cg_keep : 0.8));
   return plan->x_tuned ? MINNORM_OK : MINNORM_ESTATE;
 }
 

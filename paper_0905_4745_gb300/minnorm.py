@@ -73,7 +73,7 @@ def lib():
         L.minnorm_get_factor.argtypes = [p, p, p]
         L.minnorm_cg_products.argtypes = [p, p, i64, p, p, p]
         L.minnorm_block_products.argtypes = [p, p, i64, p, p, p]
-        L.minnorm_plan_tuning.argtypes = [p, C.POINTER(i32), C.POINTER(i32)]
+        L.minnorm_plan_tuning.argtypes = [p, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
         L.minnorm_residual_dd.argtypes = [p, p, i64, p, p, p, p, p, p]
         L.minnorm_kernel_stats.argtypes = [p, i32, C.POINTER(i32), C.POINTER(d)]
         L.minnorm_qr_noalloc.argtypes = [p, i64, i64, i64, p, p, p]
@@ -244,12 +244,12 @@ def minnorm_residual_dd(plan, A, y_hi, y_lo, b, r, x_hi, x_lo, lda=None):
 
 
 def minnorm_plan_tuning(plan):
-    """(column chunks, row splits, tuned) of the plan's exact residual."""
-    c, r = C.c_int32(), C.c_int32()
-    st = lib().minnorm_plan_tuning(plan, C.byref(c), C.byref(r))
+    """(exact-residual column chunks, row splits, fused-CG L2 share in percent, tuned)."""
+    c, r, k = C.c_int32(), C.c_int32(), C.c_int32()
+    st = lib().minnorm_plan_tuning(plan, C.byref(c), C.byref(r), C.byref(k))
     if st not in (OK, ESTATE):
         raise MinnormError(st, "minnorm_plan_tuning")
-    return c.value, r.value, st == OK
+    return c.value, r.value, k.value, st == OK
 
 
 def minnorm_kernel_stats(plan, k):

@@ -31,7 +31,7 @@ def test_tuned_split_gives_identical_residual(mn):
     outs = []
     plan = mn.minnorm_plan_create(m, n, 0, mn.C64, mn.MIXED, seed=4)
     try:
-        c0, r0, tuned0 = mn.minnorm_plan_tuning(plan)
+        c0, r0, k0, tuned0 = mn.minnorm_plan_tuning(plan)
         assert not tuned0
         for stage in range(2):
             r = torch.empty(m, dtype=torch.complex128, device="cuda:0")
@@ -45,8 +45,8 @@ def test_tuned_split_gives_identical_residual(mn):
                 x = torch.empty(n, dtype=torch.complex128, device="cuda:0")
                 st, info = mn.minnorm_solve(plan, s.A, s.b, 1e-10, x)
                 assert st == mn.OK
-        c1, r1, tuned1 = mn.minnorm_plan_tuning(plan)
-        assert tuned1 and c1 >= 1 and r1 >= 1
+        c1, r1, k1, tuned1 = mn.minnorm_plan_tuning(plan)
+        assert tuned1 and c1 >= 1 and r1 >= 1 and 0 <= k1 <= 100
     finally:
         mn.minnorm_plan_destroy(plan)
     for a, b in zip(outs[0], outs[1]):
