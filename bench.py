@@ -157,6 +157,26 @@ def aggregate_value(world, steps, ms_max):
     return world * steps / (ms_max / 1000.0)
 
 
+def batch_cost(m, n):
+    """Relative cost of one system of the batch: its QR (~m^2 l, l = 4m) and its passes over A (~m n
+    each, a number of them proportional to m for the refinement's fixed-point passes): m^3 + m^2 n."""
+    return float(m) ** 3 + float(m) ** 2 * n
+
+
+def partition_batch(shapes, world):
+    """Shards of the batch's independent systems over `world` GPUs, balanced by cost: systems in
+    decreasing cost, each to the least-loaded rank (ties to the lower rank). Returns, per rank, the
+    sorted indices of its systems; no system is shared and no exchange is needed."""
+    order = sorted(range(len(shapes)), key=lambda i: (-batch_cost(*shapes[i]), i))
+    loads = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (loads[q], q))
+        parts[r].append(i)
+        loads[r] += batch_cost(*shapes[i])
+    return [sorted(p) for p in parts]
+
+
 def reduce_max(pg, value, device):
     if pg is None:
         return value
@@ -262,14 +282,19 @@ def side_workload(args):
     g.build()
     from paper_0905_4745_gb300 import minnorm as mn
     import synth
-    dev = torch.device("cuda", 0)
+    # batch under torchrun: the 256 systems are sharded over the ranks by cost (no exchange);
+    # the block workload runs on rank 0 alone
+    rank, world, local, pg = dist_setup(args.gpus) if args.workload == "batch" else (0, 1, 0, None)
+    dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     steps, warmup = max(1, args.steps), max(1, args.warmup)
     if args.workload == "batch":
-        shapes = synth.batch_shapes(256, seed=4000)
-        systems = [synth.make_system(m, n, exponent=4, seed=4000 + i, dtype="c64", device="cuda:0")
-                   for i, (m, n) in enumerate(shapes)]
+        all_shapes = synth.batch_shapes(256, seed=4000)
+        mine = partition_batch(all_shapes, world)[rank]
+        shapes = [all_shapes[i] for i in mine]
+        systems = [synth.make_system(m, n, exponent=4, seed=4000 + i, dtype="c64", device=str(dev))
+                   for i, (m, n) in zip(mine, shapes)]
         batch = mn.minnorm_batch_create([m for m, _ in shapes], [n for _, n in shapes], mn.C64, mn.MIXED,
                                         seed=4000, flags=mn.FLAG_TIMING, stream=stream)
         xs = [torch.empty(n, dtype=torch.complex128, device=dev) for _, n in shapes]
@@ -280,10 +305,10 @@ def side_workload(args):
 
         def stats_of(i, k):
             return mn.minnorm_batch_kernel_stats(batch, i, k)
-        units, name = len(shapes), ("batching: 256 systems, m in [32, 512], n = m k, k in [8, 64], complex64, "
-                                    "sigma 1..1e-4, eps 1e-10 (mixed)")
+        units, name = len(all_shapes), ("batching: 256 systems, m in [32, 512], n = m k, k in [8, 64], complex64, "
+                                        "sigma 1..1e-4, eps 1e-10 (mixed)")
         stat_shapes = shapes
-        hbm = sum(m * n * 8 for m, n in shapes)
+        hbm = sum(m * n * 8 for m, n in all_shapes)
     else:
         w = synth.WORKLOADS["c5_blockrhs_4096x131072"]
         m, n, k = w["m"], w["n"], w["nrhs"]
@@ -304,9 +329,10 @@ def side_workload(args):
     for _ in range(warmup):
         step()
     launches0 = mn.minnorm_launch_count()
+    barrier(pg, dev)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ck = Clocks(0)
+    ck = Clocks(local)
     ck.__enter__()
     e0.record(stream)
     statuses = []
@@ -316,8 +342,13 @@ def side_workload(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ck.__exit__()
-    ms = e0.elapsed_time(e1)
-    worst = max(i["err_bound"] for i in infos)
+    barrier(pg, dev)
+    ms = reduce_max(pg, e0.elapsed_time(e1), dev)
+    worst = reduce_max(pg, max(i["err_bound"] for i in infos), dev)
+    status = int(reduce_max(pg, float(max(statuses)), dev))
+    if rank != 0:
+        pg.destroy_process_group()
+        return 0
     pk, _ = peaks()
     roof = side_roofline(stat_shapes, stats_of, pk)
     cpu = None
@@ -326,20 +357,24 @@ def side_workload(args):
             total, count = 0.0, 0
             while count < len(systems) and (total < 10.0 or count == 0):     # systems in index order, ~10 s
                 A_np = systems[count].A.cpu().numpy().astype(np.complex128)
-                secs, _ = run_oracle_solve(A_np, systems[count].b.cpu().numpy(), seed=4000 + count)
+                secs, _ = run_oracle_solve(A_np, systems[count].b.cpu().numpy(), seed=4000 + mine[count])
                 total += secs
                 count += 1
             cpu = {"value": count / total, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                   "sample": "the first %d systems of the batch (Steps 1-5, FP64, oracle O2), %.1f s" % (count, total)}
+                   "sample": "the first %d systems of rank 0's share of the batch (Steps 1-5, FP64, oracle O2), "
+                             "%.1f s" % (count, total)}
         else:
             cpu = {"value": None, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": "none: one oracle solve of this workload exceeds the bounded sample "
                              "(its pivoted QR of 16384 x 4096 alone is ~2e12 flops on the host)"}
+    if pg is not None:
+        pg.destroy_process_group()
     print(json.dumps({"metric": "solves/s (%s workload)" % args.workload, "value": units * steps / (ms / 1000.0),
-                      "unit": "solves/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
+                      "unit": "solves/s", "n_gpus": world, "steps": steps, "warmup": warmup,
+                      "scaling": "strong" if args.workload == "batch" else None,
                       "ms_per_step": ms / steps, "higher_is_better": True, "dtype": "c64 products + f64 QR/R + "
                       "fixed-point residual", "data": "synthetic", "config": {"workload": name, "A_bytes": hbm},
-                      "status": mn.STATUS_NAMES[max(statuses)], "worst_err_bound": worst, "roofline": roof,
+                      "status": mn.STATUS_NAMES[status], "worst_err_bound": worst, "roofline": roof,
                       "cpu_baseline": cpu, "gpu_launches": mn.minnorm_launch_count() - launches0,
                       "clocks": ck.summary()}), flush=True)
     return 0

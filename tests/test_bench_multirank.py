@@ -1,7 +1,8 @@
 """The host side of bench.py's N-GPU run (replicas: one system per rank, no exchange
 in the solver), on CPU with two gloo ranks: process-group setup from the torchrun
 environment, the max-over-ranks timing reduction, the barrier, the whole-job
-aggregate and the per-rank seeds. No GPU and no library call is involved."""
+aggregate and the per-rank seeds; and the cost-balanced sharding of the batching
+workload's independent systems. No GPU and no library call is involved."""
 import json
 import os
 import socket
@@ -63,3 +64,18 @@ def test_single_rank_defaults(monkeypatch):
     assert (rank, world, local, pg) == (0, 1, 0, None)
     assert bench.reduce_max(None, 3.5, None) == 3.5
     assert bench.aggregate_value(1, 10, 250.0) == pytest.approx(40.0)
+
+
+def test_batch_partition_is_a_balanced_cover():
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+    shapes = synth.batch_shapes(256, seed=4000)
+    biggest = max(bench.batch_cost(m, n) for m, n in shapes)
+    for world in (1, 2, 3, 4, 8):
+        parts = bench.partition_batch(shapes, world)
+        assert len(parts) == world
+        assert sorted(i for p in parts for i in p) == list(range(256))      # every system exactly once
+        loads = [sum(bench.batch_cost(*shapes[i]) for i in p) for p in parts]
+        assert max(loads) - min(loads) <= biggest                           # greedy longest-first bound
+    assert bench.partition_batch(shapes, 1)[0] == list(range(256))
