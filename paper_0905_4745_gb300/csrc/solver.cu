@@ -749,9 +749,9 @@ minnorm_status tune_cg_keep(minnorm_plan_t plan, CgFusedArgs a) {
       CK(launch_cg_fused(a, st));
       if (rep == 1) CK(cudaEventRecord(e1, st));
     }
-    CK(cudaEventSynchronize(e1));
     int err = 0;
-    CK(cudaMemcpy(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     if (err) {
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
