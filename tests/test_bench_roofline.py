@@ -1,0 +1,40 @@
+"""bench.py's roofline arithmetic (CPU): the algorithmic bytes and flops each kernel
+class is charged with, the choice of the dominant class and the fraction of peak."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def test_class_amounts():
+    import bench
+    m, n, l = 512, 65536, 2048
+    assert bench.class_amount(5, m, n, l, 10) == (10 * 8.0 * m * n, "GB/s", "hbm")      # one pass per iteration
+    assert bench.class_amount(0, m, n, l, 3)[0] == 3 * 8.0 * m * n
+    assert bench.class_amount(2, m, n, l, 1) == (2 * 16.0 * m * n, "GB/s", "alu")      # two fixed-point passes
+    qr = bench.class_amount(3, m, n, l, 1)
+    assert qr[1:] == ("TFLOP/s", "alu")
+    assert qr[0] == pytest.approx(8.0 * m * m * (l - m / 3.0) + 8.0 * m ** 3 / 6.0)    # Householder QR + R^-1
+    assert bench.class_amount(4, m, n, l, 1)[0] == 8.0 * m * n + 16.0 * l * m          # read A, write Y
+
+
+def test_side_roofline_picks_the_dominant_class():
+    import bench
+    shapes = [(512, 65536)]
+    times = {0: (0, 0.0), 1: (0, 0.0), 2: (10, 5.0), 3: (1, 12.0), 4: (1, 2.0), 5: (60, 3.5)}
+    pk = {"hbm_gbs": 6690.5}
+    r = bench.side_roofline(shapes, lambda i, k: times[k], pk)
+    assert r["kernel"] == "pivoted_qr"
+    flops = 8.0 * 512 ** 2 * (2048 - 512 / 3.0) + 8.0 * 512 ** 3 / 6.0
+    assert r["achieved"] == pytest.approx(flops / 0.012 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_NOMINAL_TFLOPS)
+    assert r["ms_by_class"]["cg_fused"] == 3.5
+
+
+def test_aggregate_and_batch_cost():
+    import bench
+    assert bench.aggregate_value(4, 10, 2000.0) == pytest.approx(20.0)    # 40 solves in 2 s
+    assert bench.batch_cost(2, 10) == 8 + 40
