@@ -316,7 +316,8 @@ minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *lau
  * the array: calls whose work may overlap on the GPU (other streams, other
  * host threads) race and must be serialized by the caller. Work is enqueued
  * on `stream` (cudaStream_t as void*); the call synchronizes it to read the
- * barrier's status. Errors: EINVAL (null pointers, sizes), ENOTSUP (m > 4096),
+ * barrier's status. Errors: EINVAL (null pointers, sizes, Y or R_out not
+ * 16-byte aligned, piv_out not 8-byte aligned), ENOTSUP (m > 4096),
  * ETIMEOUT (a bounded wait between the kernel's steps expired), ECUDA. */
 minnorm_status minnorm_qr_noalloc(void *Y, int64_t ldy, int64_t l, int64_t m, void *R_out, void *piv_out,
                                   void *stream);

@@ -9,6 +9,11 @@ namespace mn {
 
 struct GridBarrier;
 
+// Longest a bounded device-side wait (a grid barrier, a pivot exchange, an
+// mbarrier phase) may spin before the kernel records MINNORM_ETIMEOUT and
+// returns: 2 s. Every entry point passes this same limit.
+constexpr uint64_t kBarrierLimitNs = 2000000000ULL;
+
 // count of kernels launched by this library (every launch site calls it)
 void note_launch();
 long long launches_so_far();

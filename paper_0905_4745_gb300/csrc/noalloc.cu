@@ -72,6 +72,9 @@ extern "C" minnorm_status minnorm_qr_noalloc(void *Y, int64_t ldy, int64_t l, in
   if (!Y || !R_out || !piv_out) return MINNORM_EINVAL;
   if (m < 1 || l < m || ldy != l || l > (int64_t)1 << 30) return MINNORM_EINVAL;
   if (m > kNoAllocMaxM) return MINNORM_ENOTSUP;  // beyond the fixed scratch
+  // the kernels access Y and R as 16-byte complex128 and the pivots as int64: an offset view
+  // would fault on the GPU, so it is refused here, before any device work
+  if (((uintptr_t)Y & 15u) || ((uintptr_t)R_out & 15u) || ((uintptr_t)piv_out & 7u)) return MINNORM_EINVAL;
   unsigned char *base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return MINNORM_ECUDA;
   cudaStream_t st = (cudaStream_t)stream;
@@ -100,7 +103,7 @@ extern "C" minnorm_status minnorm_qr_noalloc(void *Y, int64_t ldy, int64_t l, in
   q.R = R_out;
   q.mail = mail;
   q.err = err;
-  q.limit_ns = 2000000000ULL;
+  q.limit_ns = kBarrierLimitNs;
   if (launch_qrp(q, st) != cudaSuccess) return MINNORM_ECUDA;
   note_launch();
   widen_piv_kernel<<<(int)((m + 255) / 256), 256, 0, st>>>(piv, (int64_t *)piv_out, (int)m);

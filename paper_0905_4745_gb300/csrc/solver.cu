@@ -46,7 +46,6 @@ namespace {
 
 constexpr int kSeg = 2048;                 // chain segment (outputs per CTA)
 constexpr int kChainCap = 4096;            // loaded elements per chain CTA
-constexpr uint64_t kBarrierLimitNs = 2000000000ULL;  // 2 s per grid-barrier wait
 constexpr int kMaxOuter = 12;
 
 struct KernelTimer {
@@ -1417,7 +1416,10 @@ minnorm_status minnorm_solve_many(minnorm_plan_t plan, const void *A, int64_t ld
   for (int64_t j = 0; j < nrhs; ++j) {
     const minnorm_status s = solve_impl(plan, A, lda, static_cast<const zd *>(B) + j * ldb, eps,
                                         static_cast<zd *>(X) + j * ldx, infos ? infos + j : nullptr);
-    if (s == MINNORM_EINVAL || s == MINNORM_ESTATE || s == MINNORM_ECUDA) return s;
+    // a failed plan (ETIMEOUT) or a missing allocation stops at once, as in the block path
+    if (s == MINNORM_EINVAL || s == MINNORM_ESTATE || s == MINNORM_ECUDA || s == MINNORM_ENOMEM ||
+        s == MINNORM_ETIMEOUT)
+      return s;
     if (s != MINNORM_OK && first == MINNORM_OK) first = s;
   }
   return first;

@@ -70,3 +70,15 @@ def test_plan_create_validates_before_touching_the_device(libpath):
     assert L.minnorm_sketch(None, None, 64) == minnorm.EINVAL
     assert L.minnorm_solve(None, None, 64, None, 1e-3, None, None) == minnorm.EINVAL
     assert L.minnorm_plan_destroy(None) == minnorm.OK
+
+
+def test_qr_noalloc_refuses_unaligned_buffers_before_any_launch(libpath):
+    # offset views of complex128 / int64 buffers would fault inside the kernels; the entry point
+    # returns EINVAL from its argument checks, which run before any CUDA call (so on CPU too)
+    from paper_0905_4745_gb300 import minnorm
+    L = minnorm.lib()
+    good, odd8, odd4 = 0x10000, 0x10008, 0x10004
+    l, m = 64, 16
+    assert L.minnorm_qr_noalloc(odd8, l, l, m, good, good, None) == minnorm.EINVAL   # Y offset by 8 bytes
+    assert L.minnorm_qr_noalloc(good, l, l, m, odd8, good, None) == minnorm.EINVAL   # R offset by 8 bytes
+    assert L.minnorm_qr_noalloc(good, l, l, m, good, odd4, None) == minnorm.EINVAL   # pivots offset by 4 bytes

@@ -6,7 +6,10 @@ fixed array inside the library instead of plan workspace. Two calls in a row,
 on two different sketches, must each reproduce what the plan path
 (minnorm_sketch + minnorm_get_factor) gives for the same matrix: the same
 pivots and R within the QR parity tolerance of the other tests (1e-12
-relative). The second call also checks that the shared scratch is reset.
+relative). The calls run a larger system, then a smaller one, then the larger
+one again, so a smaller call meets the flags, posts and partial norms a larger
+call left in the shared scratch (each call must clear what has to start at
+zero); one call is enqueued on a side stream instead of the current one.
 This file is collected last on purpose.
 """
 import numpy as np
@@ -50,15 +53,17 @@ def _plan_factor(mn, A, m, n, seed):
 def test_qr_noalloc_matches_plan_path_twice(mn):
     import torch
     dev = torch.device("cuda:0")
-    cases = [(48, 4096, 5), (200, 2048, 6)]
-    for m, n, seed in cases:                       # two calls in a row
+    side = torch.cuda.Stream(device=dev)
+    cases = [(200, 2048, 6, None), (48, 4096, 5, side), (200, 2048, 7, None)]
+    for m, n, seed, stream in cases:               # calls in a row: large, small, large
         s = synth.make_system(m, n, exponent=2, seed=900 + m)
         A = torch.from_numpy(s.A).to(dev)
         Y, R_ref, piv_ref = _plan_factor(mn, A, m, n, seed)
         Yw = Y.clone()                              # overwritten by the call
         R = torch.full((m, m), complex(np.nan, np.nan), dtype=torch.complex128, device=dev)
         piv = torch.full((m,), -1, dtype=torch.int64, device=dev)
-        st = mn.minnorm_qr_noalloc(Yw, 4 * m, m, R, piv)
+        torch.cuda.synchronize()
+        st = mn.minnorm_qr_noalloc(Yw, 4 * m, m, R, piv, stream=stream)
         torch.cuda.synchronize()
         assert st == mn.OK
         assert torch.equal(piv, piv_ref)
