@@ -1,12 +1,15 @@
 #!/usr/bin/env python
 """Benchmark of the randomized minimal-norm solver on one GB300.
 
-Workload: m = 512, n = 65536, A = U diag(sigma) V^* stored complex128 (512 MiB),
-sigma log-spaced from 1 to 1e-6, complex Gaussian b, eps = 1e-12, l = 4m.
-A step is one whole solve of the hot path, Steps 1-5: minnorm_sketch (SRFT
-sketch, pivoted QR, P R^{-1}) + minnorm_solve (preconditioned CG inside the
-double-double refinement) with A and b resident in HBM. A (512 MiB) is larger
-than L2 (129 MB), so no flush is needed between steps.
+Workload (the precision workload): m = 2048, n = 262144, A = U diag(sigma) V^*
+stored complex64 (4.3 GB), sigma log-spaced from 1 to 1e-5, complex Gaussian b,
+eps = 1e-10, l = 4m; mixed precision, with the plain FP64 form timed on the same
+inputs beside it. A step is one whole solve of the hot path, Steps 1-5:
+minnorm_sketch (SRFT sketch, pivoted QR, P R^{-1}) + minnorm_solve
+(preconditioned CG inside the exact-residual refinement) with A and b resident
+in HBM. A (4.3 GB) is larger than L2 (129 MB), so no flush is needed between
+steps. `--workload c2` runs the plain-method workload instead (512 x 65536
+complex128, sigma 1..1e-6, eps 1e-12).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
     python bench.py --impl reference      # the CPU oracle (Steps 1-5 in FP64)
@@ -29,14 +32,29 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "solves/s at <=1e-10 rel. error (mixed vs plain FP64 GPU); CG matvec HBM GB/s"
-W = dict(m=512, n=65536, exponent=6, dtype="c128", eps=1e-12, seed=1002)
-WORKLOAD_NAME = ("512x65536 complex128, sigma 1..1e-6, complex Gaussian b, eps 1e-12, l = 4m "
-                 "(plain-method workload)")
+# the precision workload (the one the metric is quoted on) and the plain-method workload
+WORKLOADS = {
+    "c3": dict(m=2048, n=262144, exponent=5, dtype="c64", eps=1e-10, seed=1003,
+               name="2048x262144 complex64 (4.3 GB), sigma 1..1e-5, complex Gaussian b, eps 1e-10, l = 4m "
+                    "(precision workload)"),
+    "c2": dict(m=512, n=65536, exponent=6, dtype="c128", eps=1e-12, seed=1002,
+               name="512x65536 complex128 (512 MiB), sigma 1..1e-6, complex Gaussian b, eps 1e-12, l = 4m "
+                    "(plain-method workload)"),
+}
+W = WORKLOADS["c3"]
+WORKLOAD_NAME = W["name"]
+# O1 (the oracle's dense pivoted-QR solve, ~8 m^2 n flops on the host) is run for the error
+# report only up to this many entries of A; above it the oracle's O2 solve (Steps 1-5, FP64)
+# of the cpu_baseline sample is the comparison
+O1_MAX_ENTRIES = 512 * 65536
+# a budget for the reference arm's timed whole O2 solves (seconds of host time)
+REFERENCE_BUDGET_S = 240.0
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26 TFLOP/s
-# DRAM bytes (read + write) per launch of a kernel class, from one ncu capture of the current
-# kernels on this workload: class 3 = qrp_reg_kernel<16> (16.91 + 2.77 MB) + prinv_kernel<1>
-# (2.14 MB + 0.5 KB). Y (16 MiB) stays in L2 through the QR, so traffic is one read of Y.
-PROFILED_TRAFFIC = {3: 21.82e6}
+# DRAM bytes (read + write) per launch of a kernel class, keyed by (workload, class), from one ncu
+# capture of the current kernels: on the plain-method workload class 3 = qrp_reg_kernel<16>
+# (16.91 + 2.77 MB) + prinv_kernel<1> (2.14 MB + 0.5 KB); Y (16 MiB) stays in L2 through the QR,
+# so traffic is one read of Y.
+PROFILED_TRAFFIC = {("c2", 3): 21.82e6}
 KERNEL_CLASSES = {0: "cg_adjoint_product", 1: "cg_forward_product", 2: "exact_residual", 3: "pivoted_qr",
                   4: "srft_sketch", 5: "cg_fused"}
 REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
@@ -52,10 +70,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error check and CPU baseline")
-    ap.add_argument("--m", type=int, default=W["m"], help="rows (profiling runs of a smaller case)")
-    ap.add_argument("--n", type=int, default=W["n"], help="columns (profiling runs of a smaller case)")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "block", "products", "paper"],
-                    help="plain: the benchmark line; batch / block: the batching and block right-hand-side "
+    ap.add_argument("--m", type=int, default=0, help="rows (profiling runs of a smaller case)")
+    ap.add_argument("--n", type=int, default=0, help="columns (profiling runs of a smaller case)")
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "batch", "block", "products", "paper"],
+                    help="c3: the benchmark line (precision workload); c2: the plain-method workload "
+                         "(512x65536 complex128); batch / block: the batching and block right-hand-side "
                          "workloads, measured on their own (one line each, not the benchmark line); products: "
                          "the block-CG products alone (tensor cores), 4096x131072 complex64, 32 columns; paper: "
                          "the shapes of the paper's Tables 1-4 with its b, 10 T-seeds each")
@@ -147,9 +166,9 @@ def dist_setup(n_gpus):
     return rank, world, local, pg
 
 
-def replica_seed(rank):
+def replica_seed(rank, w=None):
     """Seed of the system rank `rank` solves: every replica gets its own A and b."""
-    return W["seed"] + 100 * rank
+    return (w or W)["seed"] + 100 * rank
 
 
 def aggregate_value(world, steps, ms_max):
@@ -192,12 +211,14 @@ def barrier(pg, device):
         pg.barrier(device_ids=[device.index]) if device.type == "cuda" else pg.barrier()
 
 
-def run_oracle_solve(A, b, seed=1):
+def run_oracle_solve(A, b, seed=1, exponent=None):
     """The oracle's Steps 1-5 (FP64, literal), one solve: returns (seconds, x)."""
     import oracle
     m, n = A.shape
     l = 4 * m
-    kappa = 10.0 ** W["exponent"]
+    kappa = 10.0 ** (W["exponent"] if exponent is None else exponent)
+    if A.dtype != np.complex128:
+        A = A.astype(np.complex128)       # the stored values, exactly
     delta = (1e-14 * kappa) ** 2 * m / n       # the paper's Step 4 request (Section 7)
     P = oracle.draw_params(n, l, seed)
     t0 = time.perf_counter()
@@ -206,25 +227,37 @@ def run_oracle_solve(A, b, seed=1):
 
 
 def reference_arm(args):
+    """The oracle's O2 (Steps 1-5 literally, FP64, all host cores) on the benchmark workload's
+    inputs. A step is one whole solve. One solve of the precision workload takes about a minute
+    on the host, so the arm times at most `--steps` solves within REFERENCE_BUDGET_S (at least
+    one) after at most one warm-up solve (the oracle has no compilation or cache to warm), and
+    prints the numbers it actually ran."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import synth
-    s = synth.make_system(W["m"], W["n"], W["exponent"], W["seed"])
-    for _ in range(max(0, args.warmup)):
-        run_oracle_solve(s.A, s.b)
-    times = [run_oracle_solve(s.A, s.b)[0] for _ in range(max(1, args.steps))]
+    w = WORKLOADS["c2" if args.workload == "c2" else "c3"]
+    s = synth.make_system(w["m"], w["n"], w["exponent"], w["seed"], dtype=w["dtype"])
+    warm = min(max(0, args.warmup), 1)
+    for _ in range(warm):
+        run_oracle_solve(s.A, s.b, exponent=w["exponent"])
+    times = []
+    while len(times) < max(1, args.steps) and (not times or sum(times) + times[-1] <= REFERENCE_BUDGET_S):
+        times.append(run_oracle_solve(s.A, s.b, exponent=w["exponent"])[0])
     total = sum(times)
     value = len(times) / total
     cores = os.cpu_count()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-        "steps": len(times), "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+        "steps": len(times), "steps_requested": args.steps, "warmup": warm, "warmup_requested": args.warmup,
+        "ms_per_step": 1000 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "m": W["m"], "n": W["n"], "l": 4 * W["m"],
-                                        "eps": W["eps"]},
+        "data": "synthetic", "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "l": 4 * w["m"],
+                                        "eps": w["eps"], "storage": w["dtype"]},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d whole solves (Steps 1-5, FP64, oracle O2) of the workload" % len(times)},
+                         "sample": "%d whole solves (Steps 1-5, FP64, oracle O2) of the workload, %.1f s (at most "
+                                   "%d requested, within a %.0f s budget)" % (len(times), total, args.steps,
+                                                                              REFERENCE_BUDGET_S)},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -490,8 +523,9 @@ def main():
         return products_workload(args)
     if args.workload == "paper":
         return paper_workload(args)
-    if args.workload != "plain":
+    if args.workload not in ("c3", "c2"):
         return side_workload(args)
+    w = WORKLOADS[args.workload]
     import torch
     rank, world, local, pg = dist_setup(args.gpus)
     device = torch.device("cuda", local)
@@ -504,15 +538,20 @@ def main():
     from paper_0905_4745_gb300 import minnorm as mn
     import synth
 
-    m, n, eps = args.m, args.n, W["eps"]
-    cache = os.environ.get("MINNORM_INPUT_CACHE", os.path.join(tempfile.gettempdir(), "minnorm_inputs"))
-    s = synth.make_system(m, n, W["exponent"], replica_seed(rank), device=str(device), cache_dir=cache)
+    m, n, eps = args.m or w["m"], args.n or w["n"], w["eps"]
+    full = (m, n) == (w["m"], w["n"])
+    c64 = w["dtype"] == "c64"
+    # inputs built on the GPU from the seeded draws (the 4.3 GB workload takes ~40 s; no host cache)
+    s = synth.make_system(m, n, w["exponent"], replica_seed(rank, w), dtype=w["dtype"], device=str(device))
     A, b = s.A, s.b
+    del s
+    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     prec_main = mn.MIXED if args.precision == "mixed" else mn.FP64
+    dt = mn.C64 if c64 else mn.C128
     plans = {}
     for name, prec in (("main", prec_main), ("other", mn.FP64 if prec_main == mn.MIXED else mn.MIXED)):
-        plans[name] = mn.minnorm_plan_create(m, n, 0, mn.C128, prec, seed=1, flags=mn.FLAG_TIMING, stream=stream)
+        plans[name] = mn.minnorm_plan_create(m, n, 0, dt, prec, seed=1, flags=mn.FLAG_TIMING, stream=stream)
     x = torch.empty(n, dtype=torch.complex128, device=device)
 
     def step(plan):
@@ -594,9 +633,10 @@ def main():
     l = 4 * m
     per_launch_ms = stats[dom][1] / max(1, stats[dom][0])
     mixed = prec_main == mn.MIXED
+    esz = 8 if (mixed or c64) else 16      # bytes per entry of the A the CG products stream
     if dom in (0, 1, 5):
         # per CG iteration (k = 5 counts iterations): one pass over A in the fused kernel
-        bytes_per = m * n * (8 if mixed else 16)
+        bytes_per = m * n * esz
         achieved = bytes_per / (per_launch_ms / 1000.0) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s"}
     elif dom == 2:
@@ -608,59 +648,74 @@ def main():
         achieved = flops / (per_launch_ms / 1000.0) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s"}
     else:
-        bytes_per = m * n * (8 if mixed else 16) + 16 * l * m
+        bytes_per = m * n * esz + 16 * l * m
         achieved = bytes_per / (per_launch_ms / 1000.0) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = PROFILED_TRAFFIC.get(dom) if (m, n) == (W["m"], W["n"]) else None
+    roof["traffic"] = PROFILED_TRAFFIC.get((args.workload, dom)) if full else None
     roof["kernel"] = KERNEL_CLASSES[dom]
     roof["peak_source"] = (pk_kind if roof["unit"] == "GB/s" else
-                           "FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe 1.25)")
+                           "derived, not measured: FP64 from unit counts and clock, 152 SMs x 2 DFMA/clk x 2 "
+                           "x 2.07 GHz (recipe table 1.25 TFLOP/s)")
     # CG matvec bandwidth (the metric's second half)
     if stats[5][0] > 0:     # fused CG: one pass over A per iteration
         cg_ms = stats[5][1] / stats[5][0]
     else:                   # separate A^* w and A q passes
         cg_ms = (stats[0][1] + stats[1][1]) / max(1, stats[0][0] + stats[1][0])
-    cg_gbs = m * n * (8 if mixed else 16) / (cg_ms / 1000.0) / 1e9 if cg_ms > 0 else None
+    # one pass over A per CG iteration for the fused kernel, two (A^* w, then A q) otherwise
+    cg_passes = 1 if stats[5][0] > 0 else 2
+    cg_gbs = m * n * esz / (cg_ms / 1000.0) / 1e9 if cg_ms > 0 else None
     cg_roof = None
     if cg_gbs:
         # one pass over A per CG iteration (algorithmic bytes), launch overhead included
         cg_roof = {"bound": "hbm", "achieved": cg_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                   "frac": cg_gbs / pk["hbm_gbs"], "bytes_per_iteration": m * n * (8 if mixed else 16),
-                   "traffic": (PROFILED_TRAFFIC.get(5) if (m, n) == (W["m"], W["n"]) and stats[5][0] > 0
-                               else None),
+                   "frac": cg_gbs / pk["hbm_gbs"], "bytes_per_pass": m * n * esz, "passes_per_iteration": cg_passes,
+                   "traffic": PROFILED_TRAFFIC.get((args.workload, 5 if stats[5][0] > 0 else 0)) if full else None,
                    "peak_source": pk_kind}
     breakdown = {KERNEL_CLASSES[k]: {"launches": v[0], "ms_total": v[1]} for k, v in stats.items()}
 
     err_main = err_other = None
+    err_kind = None
     cpu = None
     if not args.no_oracle:
         import oracle
-        A_np, b_np = A.cpu().numpy(), b.cpu().numpy()
-        p_ref = oracle.minnorm_direct(A_np, b_np, steps=5)["p"]
-        nref = np.linalg.norm(p_ref)
-        err_main = float(np.linalg.norm(x_main.cpu().numpy() - p_ref) / nref)
-        err_other = float(np.linalg.norm(x_other.cpu().numpy() - p_ref) / nref)
-        total, count = 0.0, 0
-        while count < 8 and (total < 10.0 or count == 0):      # a bounded sample of ~10 s
-            secs, _ = run_oracle_solve(A_np, b_np, seed=1 + count)
+        A_np, b_np = A_h.numpy(), b_h.numpy()     # the pinned host copies of the e2e leg
+        total, count, x_o2 = 0.0, 0, None
+        while count < 8 and (total < 10.0 or count == 0):      # a bounded sample: ~10 s, at least one solve
+            secs, xo = run_oracle_solve(A_np, b_np, seed=1 + count, exponent=w["exponent"])
+            x_o2 = xo if x_o2 is None else x_o2
             total += secs
             count += 1
         cpu = {"value": count / total, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "%d whole solves (Steps 1-5, FP64, oracle O2) of the workload, %.1f s" % (count, total)}
+               "sample": "%d whole solve(s) (Steps 1-5, FP64, oracle O2) of the workload, %.1f s" % (count, total)}
+        if m * n <= O1_MAX_ENTRIES:
+            # O1: the dense pivoted-QR minimal-norm solution with double-double refinement
+            p_ref = oracle.minnorm_direct(A_np, b_np, steps=5)["p"]
+            err_kind = "||x - p|| / ||p||, p from the oracle's O1 (dense pivoted QR + double-double refinement)"
+        else:
+            # O1 would take many minutes on the host: the oracle's own O2 solve is the reference
+            # (FP64 throughout, its error near kappa * 2^-53 dominates the difference)
+            p_ref = x_o2
+            err_kind = ("||x - x_O2|| / ||x_O2||, x_O2 from the oracle's O2 solve (Steps 1-5 in FP64, no "
+                        "refinement: its own error is of order kappa * 2^-53)")
+        nref = np.linalg.norm(p_ref)
+        err_main = float(np.linalg.norm(x_main.cpu().numpy() - p_ref) / nref)
+        err_other = float(np.linalg.norm(x_other.cpu().numpy() - p_ref) / nref)
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64 products + f64 QR/R + dd residual" if mixed else "f64 + dd residual",
+        "dtype": "c64 products + f64 QR/R + fixed-point residual" if mixed else "f64 + fixed-point residual",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME if (m, n) == (W["m"], W["n"]) else
-                   "%dx%d complex128 (profiling case, not the benchmark workload)" % (m, n),
+        "config": {"workload": w["name"] if full else
+                   "%dx%d %s (profiling case, not the benchmark workload)" % (m, n, w["dtype"]),
                    "m": m, "n": n, "l": l, "eps": eps,
-                   "precision": "mixed" if mixed else "fp64", "storage": "complex128",
-                   "l2": "no flush: A (512 MiB) exceeds L2 (129 MB)", "replicas": world},
-        "rel_err_vs_oracle": err_main, "err_bound": last_info["err_bound"], "status": mn.STATUS_NAMES[last_st],
+                   "precision": "mixed" if mixed else "fp64", "storage": "complex64" if c64 else "complex128",
+                   "l2": "no flush: A (%.2f GB) exceeds L2 (129 MB)" % (m * n * (8 if c64 else 16) / 1e9),
+                   "replicas": world},
+        "rel_err_vs_oracle": err_main, "rel_err_kind": err_kind, "err_bound": last_info["err_bound"],
+        "status": mn.STATUS_NAMES[last_st],
         "solve_info": last_info,
         "plain_fp64" if mixed else "mixed": {"value": other_value, "unit": "solves/s",
                                              "ms_per_step": ms_other / max(3, args.steps // 2),
@@ -674,7 +729,7 @@ def main():
         "tuning": {"exact_residual": {"column_chunks": xc, "row_splits": xs},
                    "cg_fused": {"l2_keep_pct": ck},
                    "how": "fastest of the candidates timed on the plan's first residual / inner solve"},
-        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": m * n * 16 + m * 16,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": m * n * (8 if c64 else 16) + m * 16,
                 "d2h_bytes_per_step": n * 16},
         "gpu_launches": launches,
         "clocks": clk,

@@ -340,3 +340,45 @@ def pcg_normal(A, b, R, piv, iters, u_start=None):
     lib().orc_pcg_normal(m, n, _ptr(A), n, _ptr(b), Rf.ctypes.data_as(C.c_void_p), m, _ptr(piv),
                          _ptr(us), int(iters), _ptr(hist), _ptr(y))
     return hist[:iters], y
+
+
+# ----------------------------------------------------------- certificate ----
+def error_certificate(A, b, X, seed=1, l=None):
+    """A posteriori bound on ||x - p|| / ||x|| for each column x of X, computed on the host
+    from the oracle's own FP64 sketch (Section 5's argument, applied after the fact).
+
+    Y = T A^* is the oracle's sketch (Step 1, Eq. randmat) for the SRFT drawn from `seed`, and
+    Y = Q R any QR of it (LAPACK's unpivoted one: Steps 2-4 need only some R with Y R^{-1}
+    orthonormal). Then T A^* R^{-1} = Q, and since T has orthonormal rows (Section 3),
+    sigma_min(A^* R^{-1}) >= 1 - delta, delta covering the FP64 rounding of the sketch and the
+    QR (a priori: 8 (n + log2 n + 2 m) 2^-53 ||A||_F ||R^{-1}||_F). For x = A^* y (the form of
+    Step 5, Eq. output) and p = A^* y*, x - p = A^* (y - y*) and R^{-*} A (x - p) =
+    (A^* R^{-1})^* (x - p), so ||x - p|| <= ||R^{-*} (b - A x)|| / (1 - delta); the residual
+    b - A x is formed with double-double sums (Dot2). A column rounded to complex128 after
+    x = A^* y adds at most 2^-53 ||x||, included. Returns (bounds, delta); a bound is +inf when
+    delta >= 1/2 (no certificate)."""
+    A = _z(A)
+    X = np.asarray(X, dtype=np.complex128)
+    cols = X[:, None] if X.ndim == 1 else X
+    B = np.asarray(b, dtype=np.complex128)
+    B = B[:, None] if B.ndim == 1 else B
+    m, n = A.shape
+    l = min(4 * m, n) if l is None else l
+    P = draw_params(n, l, seed)
+    Y = np.ascontiguousarray(sketch(P, A))
+    R = np.linalg.qr(Y, mode="r")
+    Rinv_f = np.linalg.norm(np.linalg.solve(R, np.eye(m)))          # ||R^{-1}||_F
+    u = 2.0 ** -53
+    delta = 8.0 * (n + np.log2(n) + 2 * m) * u * np.linalg.norm(A) * Rinv_f
+    bounds = []
+    for j in range(cols.shape[1]):
+        x = np.ascontiguousarray(cols[:, j])
+        vh, vl = matvec_dd(A, x)
+        r = (B[:, j] - vh) - vl
+        g = np.linalg.solve(R.conj().T, r)                            # R^{-*} r
+        xn = np.linalg.norm(x)
+        if delta >= 0.5 or xn == 0.0:
+            bounds.append(np.inf)
+        else:
+            bounds.append(np.linalg.norm(g) / (1.0 - delta) / xn + u)
+    return np.array(bounds), float(delta)

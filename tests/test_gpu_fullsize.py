@@ -1,13 +1,14 @@
-"""Full-size solves of the two large workloads, built on the GPU (their oracle
-solutions would take hours on the host): 2048 x 262144 complex64 with singular
-values 1 .. 1e-5 (mixed precision), and 4096 x 131072 complex64 with singular
-values 1 .. 1e-6 and 64 right-hand sides (block entry point), both to eps = 1e-10.
-
-Every solve must return OK with its a-posteriori bound <= eps, and its residual
-b - A x, formed by torch in complex128 independently of the library, must be
-within eps ||x|| (since sigma_max(A) = 1 and x - p is bounded by eps ||p||) plus
-the rounding bound of torch's own product, 2 n 2^-53 || |A| |x| ||. The solution
-lies in range(A^*) by construction (Step 5 forms x = A^* y)."""
+"""Full-size solves of the two large workloads, built on the GPU: 2048 x 262144
+complex64 with singular values 1 .. 1e-5 (mixed precision), and 4096 x 131072
+complex64 with singular values 1 .. 1e-6 and 64 right-hand sides (block entry
+point), both to eps = 1e-10. The oracle's O1 solution would take tens of minutes
+on the host, so each x is checked by the oracle's own a-posteriori certificate
+(oracle.error_certificate: the oracle's FP64 sketch of A with its own T, a LAPACK
+QR of it, and the double-double residual b - A x), a rigorous bound on
+||x - p|| / ||x|| computed without the library: it must be within eps. (A plain
+residual check is not enough: ||b - A x|| / sigma_min(A) is looser than the error by
+up to the condition number, 1e5 .. 1e6 here.)"""
+import numpy as np
 import pytest
 
 import synth
@@ -26,13 +27,12 @@ def mn():
     return minnorm
 
 
-def _check_residual(A64, b, x, eps):
-    import torch
-    r = b - A64 @ x
-    n = A64.shape[1]
-    bound = 2.0 * n * 2.0 ** -53 * torch.linalg.norm(A64.abs() @ x.abs(), dim=0)
-    ok = torch.linalg.norm(r, dim=0) <= 1.01 * eps * torch.linalg.norm(x, dim=0) + bound
-    return bool(ok.all())
+def _certified(A, b, X, eps):
+    """The oracle's certificate for the columns of X (numpy, host), against eps."""
+    import oracle
+    bounds, delta = oracle.error_certificate(A, b, X, seed=17)
+    assert delta < 0.1, delta
+    return bounds
 
 
 def test_precision_workload_2048x262144(mn):
@@ -50,8 +50,10 @@ def test_precision_workload_2048x262144(mn):
     finally:
         mn.minnorm_plan_destroy(plan)
     assert st == mn.OK and info["err_bound"] <= w["eps"], info
-    A64 = s.A.to(torch.complex128)
-    assert _check_residual(A64, s.b[:, None], x[:, None], w["eps"])
+    A_np, b_np, x_np = s.A.cpu().numpy(), s.b.cpu().numpy(), x.cpu().numpy()
+    del s
+    bounds = _certified(A_np, b_np, x_np, w["eps"])
+    assert bounds[0] <= w["eps"], (bounds, info)
 
 
 def test_block_rhs_workload_4096x131072x64(mn):
@@ -71,5 +73,9 @@ def test_block_rhs_workload_4096x131072x64(mn):
         mn.minnorm_plan_destroy(plan)
     assert st == mn.OK
     assert all(i["status"] == mn.OK and i["err_bound"] <= w["eps"] for i in infos)
-    A64 = s.A.to(torch.complex128)
-    assert _check_residual(A64, B, X, w["eps"])
+    cols = [0, 31, 32, 63]                 # both ends of both 32-column chunks
+    A_np = s.A.cpu().numpy()
+    B_np, X_np = B[:, cols].cpu().numpy(), X[:, cols].cpu().numpy()
+    del s
+    bounds = _certified(A_np, B_np, X_np, w["eps"])
+    assert np.all(bounds <= w["eps"]), (bounds, [infos[j] for j in cols])
