@@ -84,13 +84,22 @@ typedef struct {
   int32_t exact_passes;      /* passes over A in exact fixed-point arithmetic (x = A^* y, b - A x) */
   int32_t status;            /* this solve's minnorm_status (per column / per system in the
                                 block and batch entry points) */
-  double err_bound;          /* a-posteriori bound on ||x - p|| / ||x|| (uses sigma_min(A^* P R^{-1}) >= 1) */
+  double err_bound;          /* rigorous a-posteriori bound on ||x - p|| / ||x||:
+                                ||R^{-*} P^T (b - A x)|| / ((1 - cert_delta) ||x||), rounding of
+                                the certificate itself included; +inf when cert_delta >= 1/2 */
   double resid_rel;          /* ||b - A x|| / ||b|| from the last residual */
   double rdiag_max;          /* |R_11| */
   double rdiag_min;          /* |R_mm| */
+  double sigma_min_R;        /* lower bound of sigma_min(R): 1 / ||R^{-1}||_F */
+  double sigma_max_R;        /* upper bound of sigma_max(R): ||R||_F */
+  double cert_delta;         /* sigma_min(A^* P R^{-1}) >= 1 - cert_delta: the a priori bounds of
+                                the sketch's and the QR's rounding times ||A||_F ||R^{-1}||_F (1 when
+                                they certify nothing) */
   float ms_sketch;           /* with MINNORM_FLAG_TIMING: Step 1 (sketch) of the last minnorm_sketch */
   float ms_qr;               /* with MINNORM_FLAG_TIMING: Step 2 (QR + R^{-1}) of the last minnorm_sketch */
-  float ms_solve;            /* with MINNORM_FLAG_TIMING: Steps 3-5 of the last minnorm_solve */
+  float ms_solve;            /* with MINNORM_FLAG_TIMING: Steps 3-5 of this solve */
+  float ms_cg;               /* with MINNORM_FLAG_TIMING: this solve's CG products (Step 4) */
+  float ms_refine;           /* with MINNORM_FLAG_TIMING: this solve's exact residuals (refinement, Step 5) */
   float reserved;
 } minnorm_info;
 

@@ -19,8 +19,13 @@ void note_launch();
 long long launches_so_far();
 
 // ---- sketch.cu ------------------------------------------------------------
+// arithmetic of the sketch: complex FP64, or complex double-word (pairs of
+// floats on the FP32 pipe, dw.cuh); element kinds of a chain's source rows
+constexpr int kArithF64 = 0, kArithDW = 2;
+constexpr int kSrcC128 = 0, kSrcC64 = 1, kSrcDW = 2;
+
 struct ChainArgs {
-  const void *src;       // rows x n, complex128 (src_c64 = 0) or complex64
+  const void *src;       // rows x n, of kind src_kind (complex128, complex64 or complex double-word)
   int64_t ld_src;
   void *dst;             // rows x n complex of the compute precision
   int64_t ld_dst;
@@ -30,7 +35,9 @@ struct ChainArgs {
   const void *post;      // n phases applied to the output, or nullptr
   const int32_t *halo;   // per-segment right halo
   int n, seg, cap, rows;
-  bool src_c64, conj, real_fp32;
+  int src_kind;          // kSrcC128, kSrcC64 or kSrcDW
+  bool conj;
+  int arith;             // kArithF64 or kArithDW (dst, phase, cs and post in that arithmetic)
 };
 cudaError_t launch_chain(const ChainArgs &a, cudaStream_t st);
 
@@ -47,7 +54,7 @@ struct FftArgs {
   void *Y;                // l x m complex128, column-major
   int64_t ldy;
   int row_offset;
-  bool real_fp32;
+  int arith;              // kArithF64 or kArithDW (src, work, tw, chirp, full, bh in that arithmetic)
   // Bluestein stages (n not a power of two; see params.h):
   const void *chirp;      // if set: the input is x_j chirp_j for j < nin and 0 for nin <= j < L
   int nin;
@@ -129,8 +136,10 @@ struct XprodArgs {
   void *xfix;             // xfix_bytes(cols): x in 128-bit fixed point for the forward product
   int xsplit;             // row splits of x = A^* y (0: xadj_splits); at most xadj_max_splits(rows)
 };
+// The fixed-point copy of A (and its complex64 copy when A32 is set); with rown2 set, also an
+// upper bound of ||A[i, :]||^2 per row (rigorous: the rounding of the float sums is added).
 cudaError_t launch_fix_prep(const void *A, int64_t lda, bool c64, int64_t rows, int64_t cols, void *afix,
-                            int32_t *E, void *A32, cudaStream_t st);
+                            int32_t *E, void *A32, cudaStream_t st, double *rown2 = nullptr);
 cudaError_t launch_xresidual(const XprodArgs &a, cudaStream_t st);
 size_t xprod_partial_bytes(int64_t rows, int nchunk);
 int xadj_splits(int64_t rows, int64_t cols);

@@ -23,10 +23,15 @@
 // with real coefficients. Inside a CTA it is evaluated exactly as a parallel
 // scan of the affine maps C -> s C + c v. Segments are independent: a segment
 // is extended to the right by a precomputed halo over which the product of
-// |sin t_k| falls below 2^-72 / sqrt(n) (FP64) or 2^-42 / sqrt(n) (FP32), so
-// starting the recurrence at the halo's end with a zero carry changes the
+// |sin t_k| falls below 2^-72 / sqrt(n) (FP64) or 2^-60 / sqrt(n) (double-word),
+// so starting the recurrence at the halo's end with a zero carry changes the
 // segment's outputs by less than that fraction of the row norm.
+//
+// Every kernel is instantiated for complex FP64 and for complex double-word
+// arithmetic (dw.cuh: pairs of floats on the FP32 pipe, ~2^-46 per operation),
+// the sketch of the mixed-precision path.
 #include "common.cuh"
+#include "dw.cuh"
 #include "kernels.h"
 
 namespace mn {
@@ -401,16 +406,22 @@ static cudaError_t launch_chain_t(const ChainArgs &a, cudaStream_t st) {
 }
 
 cudaError_t launch_chain(const ChainArgs &a, cudaStream_t st) {
-  // src kinds: 0 = complex128, 1 = complex64; real: 0 = double, 1 = float
-  if (a.real_fp32) {
-    if (a.src_c64) {
-      if (a.conj) return a.post ? launch_chain_t<float, zf, true, true>(a, st) : launch_chain_t<float, zf, true, false>(a, st);
-      return a.post ? launch_chain_t<float, zf, false, true>(a, st) : launch_chain_t<float, zf, false, false>(a, st);
+  // arithmetic: complex FP64 or complex double-word; sources: complex128, complex64, or the
+  // previous chain's double-word output
+  if (a.arith == kArithDW) {
+    if (a.src_kind == kSrcDW) {
+      if (a.conj) return a.post ? launch_chain_t<df, zw, true, true>(a, st) : launch_chain_t<df, zw, true, false>(a, st);
+      return a.post ? launch_chain_t<df, zw, false, true>(a, st) : launch_chain_t<df, zw, false, false>(a, st);
     }
-    if (a.conj) return a.post ? launch_chain_t<float, zd, true, true>(a, st) : launch_chain_t<float, zd, true, false>(a, st);
-    return a.post ? launch_chain_t<float, zd, false, true>(a, st) : launch_chain_t<float, zd, false, false>(a, st);
+    if (a.src_kind == kSrcC64) {
+      if (a.conj) return a.post ? launch_chain_t<df, zf, true, true>(a, st) : launch_chain_t<df, zf, true, false>(a, st);
+      return a.post ? launch_chain_t<df, zf, false, true>(a, st) : launch_chain_t<df, zf, false, false>(a, st);
+    }
+    if (a.conj) return a.post ? launch_chain_t<df, zd, true, true>(a, st) : launch_chain_t<df, zd, true, false>(a, st);
+    return a.post ? launch_chain_t<df, zd, false, true>(a, st) : launch_chain_t<df, zd, false, false>(a, st);
   }
-  if (a.src_c64) {
+  if (a.arith != kArithF64 || a.src_kind == kSrcDW) return cudaErrorInvalidValue;
+  if (a.src_kind == kSrcC64) {
     if (a.conj) return a.post ? launch_chain_t<double, zf, true, true>(a, st) : launch_chain_t<double, zf, true, false>(a, st);
     return a.post ? launch_chain_t<double, zf, false, true>(a, st) : launch_chain_t<double, zf, false, false>(a, st);
   }
@@ -456,7 +467,9 @@ static cudaError_t launch_fft_t(const FftArgs &a, cudaStream_t st) {
 }
 
 cudaError_t launch_fft(const FftArgs &a, cudaStream_t st) {
-  return a.real_fp32 ? launch_fft_t<float>(a, st) : launch_fft_t<double>(a, st);
+  if (a.arith == kArithDW) return launch_fft_t<df>(a, st);
+  if (a.arith == kArithF64) return launch_fft_t<double>(a, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_to_c64(const void *A, int64_t lda, void *B, int64_t ldb, int64_t rows, int64_t cols,

@@ -30,6 +30,7 @@
 
 #include "../../include/minnorm.h"
 #include "common.cuh"
+#include "dw.cuh"
 #include "kernels.h"
 #include "params.h"
 #include "vec.h"
@@ -45,6 +46,7 @@ long long launches_so_far() { return g_launches.load(std::memory_order_relaxed);
 namespace {
 
 constexpr int kSeg = 2048;                 // chain segment (outputs per CTA)
+constexpr int kChainScanThreads = 256;     // threads of a chain CTA (sketch.cu)
 constexpr int kChainCap = 4096;            // loaded elements per chain CTA
 constexpr int kMaxOuter = 12;
 
@@ -69,7 +71,8 @@ struct minnorm_plan_s {
   uint32_t flags = 0;
   cudaStream_t st = nullptr;
   int device = 0, sms = 152;
-  bool fp32 = false;        // sketch and CG products in FP32
+  bool fp32 = false;        // CG products in FP32
+  int sk_arith = kArithF64;  // sketch arithmetic: FP64, or double-word (mixed precision)
   bool sketched = false;
   bool failed = false;
   SrftParams P;
@@ -80,7 +83,14 @@ struct minnorm_plan_s {
   void *d_chirp = nullptr, *d_bhat = nullptr;  // Bluestein tables (compute precision)
   double *d_fac = nullptr;                   // l complex128: c_{s_t} / sqrt(n)
   cudaEvent_t ev_sk0 = nullptr, ev_sk1 = nullptr, ev_sk2 = nullptr;  // sketch / QR timing events
-  double *h_qr = nullptr;                    // pinned: QR error word, |R_11|, |R_mm| of the last sketch
+  double *h_qr = nullptr;                    // pinned: QR error word, |R_11|, |R_mm| of the last sketch,
+                                             // ||R||_F^2, ||P R^{-1}||_F^2, ||A||_F^2 (upper bound)
+  // the certificate sigma_min(A^* P R^{-1}) >= 1 - delta (see cert_delta)
+  double eps_sk = 0.0;   // a priori bound of the sketch's rounding, relative to each row's norm
+  double eps_qr = 0.0;   // a priori bound of the QR's backward error, relative to ||Y||_F
+  double cert_delta = 1.0, inv_eta = 0.0, r_fro = 0.0, rinv_fro = 0.0, a_fro = 0.0;
+  double *d_rown2 = nullptr;  // per row of A: an upper bound of ||A[i, :]||^2
+  double *d_cert = nullptr;   // ||R||_F^2, ||P R^{-1}||_F^2, sum of d_rown2
   // block right-hand sides (allocated by the first multi-column mixed solve)
   bool blk_ready = false;
   void *d_bG = nullptr, *d_bR = nullptr, *d_bU = nullptr, *d_bS = nullptr, *d_bP = nullptr, *d_bT = nullptr,
@@ -204,8 +214,8 @@ int64_t fft_length(int64_t n) {
 void scratch_sizes(int64_t m, int64_t n, minnorm_precision prec, minnorm_dtype dtype, size_t &s_bytes,
                    size_t &afix_bytes, size_t &a32_bytes) {
   const bool fp32 = prec == MINNORM_MIXED;
-  const size_t rc = fp32 ? sizeof(zf) : sizeof(zd);
-  s_bytes = rc * (size_t)m * (size_t)fft_length(n);
+  // the sketch's transform buffers: complex FP64 or complex double-word, 16 bytes either way
+  s_bytes = sizeof(zd) * (size_t)m * (size_t)fft_length(n);
   afix_bytes = sizeof(int64_t) * 2 * (size_t)m * (size_t)n;
   a32_bytes = (fp32 && dtype == MINNORM_C128) ? sizeof(zf) * (size_t)m * (size_t)n : 0;
 }
@@ -261,17 +271,100 @@ void collect_timers(minnorm_plan_t plan) {
   plan->event_next = 0;
 }
 
+// ---- the certificate --------------------------------------------------------
+// The refinement stops on ||x - p|| <= ||R^{-*} P^T (b - A x)|| / sigma_min(M), M = A^* P R^{-1}.
+// For the exact sketch Y = T A^* and an exact QR, T M = Q has orthonormal columns and T has
+// orthonormal rows (Section 3), so sigma_min(M) >= 1. With the computed sketch Y' = T A^* + E and
+// the computed R (Y' P + dY = Q R, Q orthonormal), T M = Q - (dY + E P) R^{-1}, hence
+//   sigma_min(M) >= 1 - delta,  delta = (||E||_F + ||dY||_F) ||R^{-1}||_F
+//                               <= (eps_sk + eps_qr (1 + eps_sk)) ||A||_F ||R^{-1}||_F,
+// with a priori bounds of the rounding of both (relative to each row of A, and to ||Y||_F). The
+// bound also pays for the rounding of P R^{-1} itself (back substitution: relative error within
+// 4 m 2^-53 ||R||_F ||R^{-1}||_F) and for the final rounding of x to complex128.
+
+// Weight of a Givens chain's recurrence C_k = cos_k v_k + sin_k C_{k+1}: C_k is a sum over j >= k
+// of v_j times products of |sin| over k..j-1; the largest row sum T_k = 1 + |sin_k| T_{k+1} and
+// column sum U_j = 1 + |sin_{j-1}| U_{j-1} bound the 2-norm of the weight matrix by
+// sqrt(max T max U) (Schur's test), so a rounding of relative size u in every term of every sum
+// moves the chain's outputs by at most u sqrt(max T max U) ||v|| per rounding level.
+static double chain_weight(const std::vector<double> &theta, int64_t n) {
+  double t = 1.0, tmax = 1.0, u = 1.0, umax = 1.0;
+  for (int64_t k = n - 2; k >= 0; --k) {
+    t = 1.0 + std::fabs(std::sin(theta[k])) * t;
+    tmax = std::max(tmax, t);
+  }
+  for (int64_t j = 1; j < n; ++j) {
+    u = 1.0 + std::fabs(std::sin(theta[j - 1])) * u;
+    umax = std::max(umax, u);
+  }
+  return std::sqrt(tmax * umax);
+}
+
+// A priori bound of ||y'_i - T conj(a_i)|| / ||a_i|| for the sketch's arithmetic (unit ua per
+// operation: 2^-46 for double-word products and sums, 2^-53 for FP64). T is a product of unitary
+// stages (phases, Givens chains, the DFT) and a row selection, so the stages' errors add:
+//   input rounding (complex128 to double-word): 2^-48
+//   each of the three phase products (the table entry rounded, four products, two sums): 8 ua
+//   each chain: (depth + 2) ua sqrt(max T max U) + the halo truncation (2^-60 or 2^-72)
+//     with depth 6 per + 40 roundings along a term's path through the block scan (per: elements
+//     per thread, both serial passes) plus the warp and block levels
+//   the FFT: 6 ua per radix-2 stage (twiddle product and the butterfly's sum) + 8 ua for the
+//     four-step twiddle pass; Bluestein: two FFTs of length L and two chirp products, amplified
+//     by amp = L max|bh| / sqrt(n) (the intermediate vectors' norm relative to ||a_i||)
+//   the output rounding to complex128: 2^-53.
+double sketch_error_bound(minnorm_plan_t plan, double chain_w, int per, double halo_tol, double amp) {
+  const bool dw = plan->sk_arith == kArithDW;
+  const double ua = dw ? 0x1.0p-46 : 0x1.0p-53;
+  const double e_in = (dw && plan->dtype == MINNORM_C128) ? 0x1.0p-48 : 0.0;
+  const double e_ph = 8.0 * ua;
+  const double e_ch = (6.0 * per + 42.0) * ua * chain_w + halo_tol * std::sqrt((double)plan->n);
+  const double e_fft1 = (6.0 * plan->logn + (plan->logN1 ? 8.0 : 0.0)) * ua;
+  const double e_fft = plan->bluestein ? (2.0 * e_fft1 + 16.0 * ua) * std::max(1.0, amp) : e_fft1;
+  return e_in + 3.0 * e_ph + 2.0 * e_ch + e_fft + 0x1.0p-53;
+}
+
+// delta from the norms of the last sketch (see above); a delta >= 1/2 certifies nothing
+void certificate_delta(minnorm_plan_t plan, double r2, double rinv2, double a2) {
+  const double slack = 1.0 + 1e-12;  // the FP64 sums of the squares
+  plan->r_fro = std::sqrt(r2 * slack);
+  plan->rinv_fro = std::sqrt(rinv2 * slack);
+  plan->a_fro = std::sqrt(a2 * slack);
+  const double e = plan->eps_sk + plan->eps_qr * (1.0 + plan->eps_sk);
+  plan->cert_delta = e * plan->a_fro * plan->rinv_fro;
+  plan->inv_eta = 4.0 * (double)plan->m * 0x1.0p-53 * plan->r_fro * plan->rinv_fro;
+  if (!(plan->cert_delta < 0.5)) plan->cert_delta = 1.0;
+}
+
+// the factor-related fields of minnorm_info (the rest is zeroed)
+void fill_factor_info(minnorm_plan_t plan, minnorm_info *info) {
+  info->rdiag_max = plan->rdiag_max;
+  info->rdiag_min = plan->rdiag_min;
+  info->sigma_min_R = plan->rinv_fro > 0.0 ? 1.0 / plan->rinv_fro : 0.0;
+  info->sigma_max_R = plan->r_fro;
+  info->cert_delta = plan->cert_delta;
+  info->ms_sketch = plan->ms_sketch;
+  info->ms_qr = plan->ms_qr;
+  info->ms_solve = info->ms_cg = info->ms_refine = info->reserved = 0.0f;
+}
+
+// ||x - p|| / ||x|| <= certified(||R^{-*} P^T r||, ||x||)
+double certified(minnorm_plan_t plan, double gnorm, double xnorm) {
+  if (!(xnorm > 0.0) || !(plan->cert_delta < 0.5)) return INFINITY;
+  return gnorm * (1.0 + plan->inv_eta + 4.0 * (double)plan->m * 0x1.0p-53) / ((1.0 - plan->cert_delta) * xnorm) +
+         0x1.0p-52;
+}
+
 // Upload the derived tables of the current parameters.
 minnorm_status upload_params(minnorm_plan_t plan) {
   const int64_t n = plan->n, l = plan->l;
   const SrftParams &P = plan->P;
-  const bool f32 = plan->fp32;
-  const size_t csz = f32 ? sizeof(zf) : sizeof(zd);
+  const bool dw = plan->sk_arith == kArithDW;
+  const size_t csz = sizeof(zd);  // complex FP64 or complex double-word: 16 bytes
   auto put_complex = [&](void *dst, const std::vector<std::complex<double>> &v) -> cudaError_t {
     std::vector<unsigned char> buf(v.size() * csz);
     for (size_t i = 0; i < v.size(); ++i) {
-      if (f32) {
-        zf z{(float)v[i].real(), (float)v[i].imag()};
+      if (dw) {
+        zw z{df(v[i].real()), df(v[i].imag())};  // nearest double-words (2^-48 relative)
         memcpy(&buf[i * csz], &z, csz);
       } else {
         zd z{v[i].real(), v[i].imag()};
@@ -298,7 +391,7 @@ minnorm_status upload_params(minnorm_plan_t plan) {
   CK(put_complex(plan->d_cs2, tmp));
   CK(put_complex(plan->d_post, P.d));
   // halos
-  const double tol = (f32 ? 0x1.0p-42 : 0x1.0p-72) / std::sqrt((double)n);
+  const double tol = (dw ? 0x1.0p-60 : 0x1.0p-72) / std::sqrt((double)n);
   int h1 = 0, h2 = 0;
   std::vector<int32_t> halo1 = chain_halos(P.theta_t, n, kSeg, tol, &h1);
   std::vector<int32_t> halo2 = chain_halos(P.theta, n, kSeg, tol, &h2);
@@ -307,6 +400,8 @@ minnorm_status upload_params(minnorm_plan_t plan) {
   plan->cap2 = (int)std::min<int64_t>(kSeg, n) + h2 + 1;
   CK(cudaMemcpy(plan->d_halo1, halo1.data(), sizeof(int32_t) * halo1.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(plan->d_halo2, halo2.data(), sizeof(int32_t) * halo2.size(), cudaMemcpyHostToDevice));
+  const double chain_w = std::max(chain_weight(P.theta_t, n), chain_weight(P.theta, n));
+  const int per = (std::max(plan->cap1, plan->cap2) + kChainScanThreads - 1) / kChainScanThreads;
   // samples: for each output t, where X[s_t] sits in the pass that produces it
   const int logn = plan->logn, logN1 = plan->logN1;
   std::vector<int32_t> off, st_t(l), st_loc(l);
@@ -352,7 +447,15 @@ minnorm_status upload_params(minnorm_plan_t plan) {
       fac[2 * t + 1] = chirp[P.s[t]].imag() * sc;
     }
     CK(cudaMemcpy(plan->d_fac, fac.data(), sizeof(double) * 2 * l, cudaMemcpyHostToDevice));
+    double bmax = 0.0;
+    for (const auto &z : bh) bmax = std::max(bmax, std::abs(z));
+    plan->eps_sk = sketch_error_bound(plan, chain_w, per, tol, (double)L * bmax / std::sqrt((double)n));
+  } else {
+    plan->eps_sk = sketch_error_bound(plan, chain_w, per, tol, 0.0);
   }
+  // Householder QR (FP64): backward error within 8 m (d + 4) 2^-53 ||Y||_F, d the depth of its
+  // dot products' sums (a thread's run of rows plus the warp, block and grid trees)
+  plan->eps_qr = 8.0 * (double)plan->m * (double)((l + 127) / 128 + 20) * 0x1.0p-53;
   plan->sketched = false;
   return MINNORM_OK;
 }
@@ -367,13 +470,14 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   plan->flags = flags;
   plan->st = (cudaStream_t)stream;
   plan->fp32 = (prec == MINNORM_MIXED);
+  plan->sk_arith = (prec == MINNORM_MIXED) ? kArithDW : kArithF64;
   CK(cudaGetDevice(&plan->device));
   CK(cudaDeviceGetAttribute(&plan->sms, cudaDevAttrMultiProcessorCount, plan->device));
   // FFT geometry: length L = n for a power of two, else the Bluestein length 2^ceil(log2(2n - 1))
   plan->bluestein = (n & (n - 1)) != 0;
   const int64_t L = fft_length(n);
   plan->logn = ilog2(L);
-  const int cap = plan->fp32 ? 8192 : 4096;
+  const int cap = 4096;  // complex elements of 16 bytes per FFT tile in shared memory
   if (L <= cap) {
     plan->logN1 = 0;
   } else {
@@ -383,21 +487,22 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
     plan->tj = (int)std::min<int64_t>(N1, cap / N2);
     plan->tk = (int)std::min<int64_t>(N2, cap / N1);
   }
-  const size_t rc = plan->fp32 ? sizeof(zf) : sizeof(zd);  // compute complex size
+  const size_t rc = plan->fp32 ? sizeof(zf) : sizeof(zd);  // complex size of the CG products
+  const size_t rs = sizeof(zd);  // complex size of the sketch (FP64 or double-word)
   const int64_t nseg = (n + kSeg - 1) / kSeg;
   ALLOC(plan->d_idx1, sizeof(int32_t) * n);
   ALLOC(plan->d_idx2, sizeof(int32_t) * n);
   ALLOC(plan->d_halo1, sizeof(int32_t) * nseg);
   ALLOC(plan->d_halo2, sizeof(int32_t) * nseg);
-  ALLOC(plan->d_ph1, rc * n);
-  ALLOC(plan->d_ph2, rc * n);
-  ALLOC(plan->d_cs1, rc * n);
-  ALLOC(plan->d_cs2, rc * n);
-  ALLOC(plan->d_post, rc * n);
-  ALLOC(plan->d_tw, rc * L);
+  ALLOC(plan->d_ph1, rs * n);
+  ALLOC(plan->d_ph2, rs * n);
+  ALLOC(plan->d_cs1, rs * n);
+  ALLOC(plan->d_cs2, rs * n);
+  ALLOC(plan->d_post, rs * n);
+  ALLOC(plan->d_tw, rs * L);
   if (plan->bluestein) {
-    ALLOC(plan->d_chirp, rc * n);
-    ALLOC(plan->d_bhat, rc * L);
+    ALLOC(plan->d_chirp, rs * n);
+    ALLOC(plan->d_bhat, rs * L);
     ALLOC(plan->d_fac, 2 * sizeof(double) * l);
   }
   const int64_t nbB = plan->logN1 ? ((L >> plan->logN1) / plan->tk) : 1;
@@ -412,8 +517,8 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
     plan->d_S1 = plan->pool->S1;
     plan->d_S2 = plan->pool->S2;
   } else {
-    ALLOC(plan->d_S1, rc * (size_t)m * L);
-    ALLOC(plan->d_S2, rc * (size_t)m * L);
+    ALLOC(plan->d_S1, rs * (size_t)m * L);
+    ALLOC(plan->d_S2, rs * (size_t)m * L);
   }
   ALLOC(plan->d_Y, sizeof(zd) * (size_t)l * m);
   if (flags & MINNORM_FLAG_KEEP_SKETCH) ALLOC(plan->d_Ykeep, sizeof(zd) * (size_t)l * m);
@@ -446,6 +551,8 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   ALLOC(plan->d_qq, sizeof(double) * 1024);
   ALLOC(plan->d_red, sizeof(double) * 2048);
   ALLOC(plan->d_norms, sizeof(double) * 4);
+  ALLOC(plan->d_rown2, sizeof(double) * m);
+  ALLOC(plan->d_cert, sizeof(double) * 4);
   ALLOC(plan->d_cg, sizeof(CgScalars));
   zd **mvecs[] = {&plan->d_r, &plan->d_g, &plan->d_u, &plan->d_s, &plan->d_p, &plan->d_w, &plan->d_t,
                   &plan->d_np, &plan->d_dy, &plan->d_yh, &plan->d_yl, &plan->d_vh, &plan->d_vl};
@@ -479,7 +586,7 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   }
   if (cudaMallocHost(&plan->h_norms, sizeof(double) * 4) != cudaSuccess) return MINNORM_ENOMEM;
   if (cudaMallocHost(&plan->h_cg, sizeof(CgScalars)) != cudaSuccess) return MINNORM_ENOMEM;
-  if (cudaMallocHost(&plan->h_qr, sizeof(double) * 3) != cudaSuccess) return MINNORM_ENOMEM;
+  if (cudaMallocHost(&plan->h_qr, sizeof(double) * 6) != cudaSuccess) return MINNORM_ENOMEM;
   draw_srft_params(seed, n, l, plan->P);
   return upload_params(plan);
 }
@@ -496,23 +603,19 @@ minnorm_status sketch_transform(minnorm_plan_t plan, const void *A, int64_t lda)
     plan->ev_sk1 = next_event(plan);
     CK(cudaEventRecord(plan->ev_sk0, st));
   }
-  const void *src = A;
-  int64_t lds = lda;
-  bool src_c64 = plan->dtype == MINNORM_C64;
+  const bool src_c64 = plan->dtype == MINNORM_C64;
   // fixed-point copy of A for the exact residuals (and the complex64 copy in mixed mode)
-  CK(launch_fix_prep(A, lda, src_c64, m, n, plan->d_afix, plan->d_E, plan->d_A32, st));
-  if (plan->fp32 && plan->dtype == MINNORM_C128) {
-    src = plan->d_A32;
-    lds = n;
-    src_c64 = true;
-  }
+  CK(launch_fix_prep(A, lda, src_c64, m, n, plan->d_afix, plan->d_E, plan->d_A32, st, plan->d_rown2));
   {
+    // the sketch reads A as stored (FP64 or double-word arithmetic: the R the error bound uses
+    // is that of an FP64-class sketch of A itself)
     Timed tm(plan, 4);
-    ChainArgs c1{src, lds, plan->d_S1, n, plan->d_idx1, plan->d_ph1, plan->d_cs1, nullptr, plan->d_halo1,
-                 (int)n, kSeg, plan->cap1, (int)m, src_c64, true, plan->fp32};
+    const int ar = plan->sk_arith;
+    ChainArgs c1{A, lda, plan->d_S1, n, plan->d_idx1, plan->d_ph1, plan->d_cs1, nullptr, plan->d_halo1,
+                 (int)n, kSeg, plan->cap1, (int)m, src_c64 ? kSrcC64 : kSrcC128, true, ar};
     CK(launch_chain(c1, st));
     ChainArgs c2{plan->d_S1, n, plan->d_S2, n, plan->d_idx2, plan->d_ph2, plan->d_cs2, plan->d_post,
-                 plan->d_halo2, (int)n, kSeg, plan->cap2, (int)m, plan->fp32, false, plan->fp32};
+                 plan->d_halo2, (int)n, kSeg, plan->cap2, (int)m, ar == kArithDW ? kSrcDW : kSrcC128, false, ar};
     CK(launch_chain(c2, st));
     const int64_t L = int64_t(1) << plan->logn;
     FftArgs f{};
@@ -528,7 +631,7 @@ minnorm_status sketch_transform(minnorm_plan_t plan, const void *A, int64_t lda)
     f.rows = (int)m;
     f.Y = plan->d_Y;
     f.ldy = l;
-    f.real_fp32 = plan->fp32;
+    f.arith = ar;
     if (!plan->bluestein) {
       f.src = plan->d_S2;
       f.ld = n;
@@ -575,6 +678,10 @@ minnorm_status sketch_factor(minnorm_plan_t plan) {
              plan->d_qrmail, plan->d_err, kBarrierLimitNs};
     CK(launch_qrp(q, st));
     CK(launch_prinv(plan->d_R, plan->d_piv, (int)m, plan->d_Wp, plan->d_WpH, st));
+    // ||R||_F, ||P R^{-1}||_F and ||A||_F for the certificate's delta
+    CK(launch_sumsq(m * m, plan->d_R, plan->d_red, plan->d_cert, st));
+    CK(launch_sumsq(m * m, plan->d_Wp, plan->d_red + 1024, plan->d_cert + 1, st));
+    CK(launch_sum((int)m, plan->d_rown2, plan->d_cert + 2, st));
   }
   if (plan->flags & MINNORM_FLAG_TIMING) {
     plan->ev_sk2 = next_event(plan);
@@ -583,6 +690,7 @@ minnorm_status sketch_factor(minnorm_plan_t plan) {
   CK(cudaMemcpyAsync(&plan->h_qr[0], plan->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&plan->h_qr[1], plan->d_beta, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&plan->h_qr[2], plan->d_beta + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&plan->h_qr[3], plan->d_cert, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   return MINNORM_OK;
 }
 
@@ -605,6 +713,7 @@ minnorm_status sketch_finish(minnorm_plan_t plan) {
   }
   plan->rdiag_max = std::fabs(b0);
   plan->rdiag_min = std::fabs(bm);
+  certificate_delta(plan, plan->h_qr[3], plan->h_qr[4], plan->h_qr[5]);
   plan->sketched = true;
   if (!(plan->rdiag_min > 64.0 * (double)plan->m * 0x1.0p-53 * plan->rdiag_max)) return MINNORM_ERANK;
   return MINNORM_OK;
@@ -631,7 +740,7 @@ minnorm_status sketch_from_host(minnorm_plan_t plan, const void *A_host, int64_t
   cudaStream_t st = plan->st;
   const int64_t m = plan->m, n = plan->n;
   const size_t es = plan->dtype == MINNORM_C128 ? sizeof(zd) : sizeof(zf);
-  const size_t rc = plan->fp32 ? sizeof(zf) : sizeof(zd);
+  const size_t rs = sizeof(zd);  // sketch buffers: complex FP64 or complex double-word
   const bool timing = plan->flags & MINNORM_FLAG_TIMING;
   if (!plan->st_copy) {
     CK(cudaStreamCreateWithFlags(&plan->st_copy, cudaStreamNonBlocking));
@@ -650,7 +759,7 @@ minnorm_status sketch_from_host(minnorm_plan_t plan, const void *A_host, int64_t
   CK(cudaEventRecord(plan->ev_host[kHostBlocks], st));
   CK(cudaStreamWaitEvent(plan->st_copy, plan->ev_host[kHostBlocks], 0));
   const int K = (int)std::min<int64_t>(kHostBlocks, m);
-  const bool via32 = plan->fp32 && plan->dtype == MINNORM_C128;
+  const int ar = plan->sk_arith;
   for (int k = 0; k < K; ++k) {
     const int64_t r0 = m * k / K, r1 = m * (k + 1) / K, rows = r1 - r0;
     char *Ab = static_cast<char *>(plan->d_Ah) + (size_t)r0 * n * es;
@@ -661,17 +770,16 @@ minnorm_status sketch_from_host(minnorm_plan_t plan, const void *A_host, int64_t
     zf *A32 = plan->d_A32 ? plan->d_A32 + r0 * n : nullptr;
     CK(launch_fix_prep(Ab, n, plan->dtype == MINNORM_C64, rows, n,
                        reinterpret_cast<char *>(plan->d_afix) + (size_t)r0 * n * 2 * sizeof(int64_t), plan->d_E + r0,
-                       A32, st));
-    const void *src = via32 ? (const void *)A32 : (const void *)Ab;
-    const bool src_c64 = via32 || plan->dtype == MINNORM_C64;
-    char *S1 = reinterpret_cast<char *>(plan->d_S1) + (size_t)r0 * n * rc;
-    char *S2 = reinterpret_cast<char *>(plan->d_S2) + (size_t)r0 * n * rc;
+                       A32, st, plan->d_rown2 + r0));
+    const bool src_c64 = plan->dtype == MINNORM_C64;
+    char *S1 = reinterpret_cast<char *>(plan->d_S1) + (size_t)r0 * n * rs;
+    char *S2 = reinterpret_cast<char *>(plan->d_S2) + (size_t)r0 * n * rs;
     Timed tm(plan, 4);
-    ChainArgs c1{src, n, S1, n, plan->d_idx1, plan->d_ph1, plan->d_cs1, nullptr, plan->d_halo1,
-                 (int)n, kSeg, plan->cap1, (int)rows, src_c64, true, plan->fp32};
+    ChainArgs c1{Ab, n, S1, n, plan->d_idx1, plan->d_ph1, plan->d_cs1, nullptr, plan->d_halo1,
+                 (int)n, kSeg, plan->cap1, (int)rows, src_c64 ? kSrcC64 : kSrcC128, true, ar};
     CK(launch_chain(c1, st));
     ChainArgs c2{S1, n, S2, n, plan->d_idx2, plan->d_ph2, plan->d_cs2, plan->d_post,
-                 plan->d_halo2, (int)n, kSeg, plan->cap2, (int)rows, plan->fp32, false, plan->fp32};
+                 plan->d_halo2, (int)n, kSeg, plan->cap2, (int)rows, ar == kArithDW ? kSrcDW : kSrcC128, false, ar};
     CK(launch_chain(c2, st));
     FftArgs f{};
     f.tw = plan->d_tw;
@@ -687,7 +795,7 @@ minnorm_status sketch_from_host(minnorm_plan_t plan, const void *A_host, int64_t
     f.Y = plan->d_Y;
     f.ldy = plan->l;
     f.row_offset = (int)r0;
-    f.real_fp32 = plan->fp32;
+    f.arith = ar;
     f.src = S2;
     f.ld = n;
     f.work = S1;
@@ -974,6 +1082,8 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
   (void)lda;
   const bool timing = plan->flags & MINNORM_FLAG_TIMING;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double ms0[6];
+  memcpy(ms0, plan->stat_ms, sizeof(ms0));
   if (timing) { e0 = next_event(plan); e1 = next_event(plan); CK(cudaEventRecord(e0, st)); }
   const void *Acg = plan->d_A32 ? (const void *)plan->d_A32 : A;
   // y = 0, x = 0, r = b
@@ -995,7 +1105,7 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
     minnorm_status s = norms(plan, outer > 0, &gnorm, &xnorm);
     if (s != MINNORM_OK) return s;
     if (outer > 0) {
-      err = xnorm > 0 ? gnorm / xnorm : INFINITY;
+      err = certified(plan, gnorm, xnorm);
       if (err <= eps) { status = MINNORM_OK; break; }
       if (err < best) best = err;
       stagnant = (err > 0.5 * prev) ? stagnant + 1 : 0;
@@ -1023,7 +1133,7 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
     double gnorm = 0, xnorm = 0;
     minnorm_status s = norms(plan, true, &gnorm, &xnorm);
     if (s != MINNORM_OK) return s;
-    err = xnorm > 0 ? gnorm / xnorm : INFINITY;
+    err = certified(plan, gnorm, xnorm);
     if (err <= eps) status = MINNORM_OK;
   }
   CK(cudaMemcpyAsync(x, plan->d_xh, sizeof(zd) * n, cudaMemcpyDeviceToDevice, st));
@@ -1046,12 +1156,10 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
     info->err_bound = err;
     const double bn = std::sqrt(plan->h_norms[3]);
     info->resid_rel = bn > 0 ? std::sqrt(plan->h_norms[2]) / bn : 0.0;
-    info->rdiag_max = plan->rdiag_max;
-    info->rdiag_min = plan->rdiag_min;
-    info->ms_sketch = plan->ms_sketch;
-    info->ms_qr = plan->ms_qr;
+    fill_factor_info(plan, info);
     info->ms_solve = plan->ms_solve;
-    info->reserved = 0;
+    info->ms_cg = (float)(plan->stat_ms[0] + plan->stat_ms[1] + plan->stat_ms[5] - ms0[0] - ms0[1] - ms0[5]);
+    info->ms_refine = (float)(plan->stat_ms[2] - ms0[2]);
   }
   return status;
 }
@@ -1229,7 +1337,7 @@ minnorm_status solve_block_chunk(minnorm_plan_t plan, const void *A, int64_t lda
       Col &q = col[c];
       if (outer > 0) {
         const double xn = std::sqrt(plan->h_bx[c]);
-        q.err = xn > 0 ? gn[c] / xn : INFINITY;
+        q.err = certified(plan, gn[c], xn);
         if (q.err <= eps) { q.status = MINNORM_OK; q.done = true; continue; }
         if (q.err < q.best) q.best = q.err;
         q.stagnant = (q.err > 0.5 * q.prev) ? q.stagnant + 1 : 0;
@@ -1280,6 +1388,7 @@ minnorm_status solve_block_chunk(minnorm_plan_t plan, const void *A, int64_t lda
       CK(cudaMemcpyAsync(plan->h_norms, plan->d_norms, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       minnorm_info &f = infos[c];
+      fill_factor_info(plan, &f);
       f.outer_steps = col[c].outer;
       f.cg_iters = col[c].cg;
       f.exact_passes = col[c].passes;
@@ -1287,12 +1396,6 @@ minnorm_status solve_block_chunk(minnorm_plan_t plan, const void *A, int64_t lda
       f.err_bound = col[c].err;
       const double bn = std::sqrt(plan->h_norms[3]);
       f.resid_rel = bn > 0 ? std::sqrt(plan->h_norms[2]) / bn : 0.0;
-      f.rdiag_max = plan->rdiag_max;
-      f.rdiag_min = plan->rdiag_min;
-      f.ms_sketch = plan->ms_sketch;
-      f.ms_qr = plan->ms_qr;
-      f.ms_solve = 0.0f;
-      f.reserved = 0;
     }
   } else {
     CK(cudaStreamSynchronize(st));

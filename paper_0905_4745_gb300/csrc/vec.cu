@@ -183,4 +183,10 @@ cudaError_t launch_sumsq(int64_t len, const void *v, double *part, double *out, 
 
 int sumsq_partials(int64_t len) { return blocks_for(len); }
 
+cudaError_t launch_sum(int len, const double *v, double *out, cudaStream_t st) {
+  note_launch();
+  finish_sum_kernel<<<1, 256, 0, st>>>(v, len, out);
+  return cudaGetLastError();
+}
+
 }  // namespace mn

@@ -22,5 +22,7 @@ cudaError_t launch_resid_finish(int64_t len, const void *b, const void *vh, cons
 cudaError_t launch_sub(int64_t len, void *r, const void *t, cudaStream_t st);
 cudaError_t launch_sumsq(int64_t len, const void *v, double *part, double *out, cudaStream_t st);
 int sumsq_partials(int64_t len);
+// *out = sum of the len doubles of v (one block)
+cudaError_t launch_sum(int len, const double *v, double *out, cudaStream_t st);
 
 }  // namespace mn

@@ -93,25 +93,45 @@ struct alignas(16) i128c {
 template <typename T>
 __global__ void __launch_bounds__(512)
 fix_prep_kernel(const T *__restrict__ A, int64_t lda, int64_t cols, fixc *__restrict__ afix,
-                int32_t *__restrict__ E, zf *__restrict__ A32) {
+                int32_t *__restrict__ E, zf *__restrict__ A32, double *__restrict__ rown2) {
   __shared__ int red[16];
+  __shared__ double red2[16];
   const int64_t i = blockIdx.x;
   const T *a = A + i * lda;
   int mx = -100000;
+  float ss = 0.0f;  // this thread's sum of |a_ij|^2 over its <= k = ceil(cols / blockDim) entries
   for (int64_t j = threadIdx.x; j < cols; j += blockDim.x) {
     const T v = a[j];
     const double re = (double)v.re, im = (double)v.im;
     if (re != 0.0) mx = max(mx, expo(re));
     if (im != 0.0) mx = max(mx, expo(im));
+    const float fr = (float)v.re, fi = (float)v.im;
+    ss = __fmaf_rn(fr, fr, __fmaf_rn(fi, fi, ss));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  double ssd = (double)ss;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ssd += __shfl_xor_sync(0xffffffffu, ssd, o);
+  if ((threadIdx.x & 31) == 0) red2[threadIdx.x >> 5] = ssd;
   __syncthreads();
   int e = red[0];
   for (int w = 1; w < (int)(blockDim.x >> 5); ++w) e = max(e, red[w]);
   if (e < -99999) e = 0;  // a zero row
-  if (threadIdx.x == 0) E[i] = e;
+  if (threadIdx.x == 0) {
+    E[i] = e;
+    if (rown2) {
+      // an upper bound of ||a_i||^2: each float term carries at most one rounding of 2^-24 from
+      // the FMA that adds it and, for complex128 entries, 2^-23 from squaring the rounded
+      // components; a float sum of k nonnegative terms exceeds none of them by more than
+      // (1 + 2^-24)^k; the double sums of the partials add 2^-40 at most
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red2[w];
+      const double k = (double)((cols + blockDim.x - 1) / blockDim.x);
+      rown2[i] = t * (1.0 + (k + 4.0) * 0x1.0p-23 + 0x1.0p-40) + (double)cols * 0x1.0p-140;  // + underflow
+    }
+  }
   const int k = 62 - e;
   fixc *o = afix + i * cols;
   for (int64_t j = threadIdx.x; j < cols; j += blockDim.x) {
@@ -349,12 +369,14 @@ int xprod_wy(int64_t m) { return 126 - ceil_log2(m) - 2; }
 int xprod_wx(int64_t n) { return 126 - ceil_log2(n) - 2; }
 
 cudaError_t launch_fix_prep(const void *A, int64_t lda, bool c64, int64_t rows, int64_t cols, void *afix,
-                            int32_t *E, void *A32, cudaStream_t st) {
+                            int32_t *E, void *A32, cudaStream_t st, double *rown2) {
   note_launch();
   if (c64)
-    fix_prep_kernel<zf><<<(unsigned)rows, 512, 0, st>>>((const zf *)A, lda, cols, (fixc *)afix, E, (zf *)A32);
+    fix_prep_kernel<zf><<<(unsigned)rows, 512, 0, st>>>((const zf *)A, lda, cols, (fixc *)afix, E, (zf *)A32,
+                                                         rown2);
   else
-    fix_prep_kernel<zd><<<(unsigned)rows, 512, 0, st>>>((const zd *)A, lda, cols, (fixc *)afix, E, (zf *)A32);
+    fix_prep_kernel<zd><<<(unsigned)rows, 512, 0, st>>>((const zd *)A, lda, cols, (fixc *)afix, E, (zf *)A32,
+                                                         rown2);
   return cudaGetLastError();
 }
 

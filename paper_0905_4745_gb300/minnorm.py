@@ -36,8 +36,10 @@ class MinnormError(RuntimeError):
 class Info(C.Structure):
     _fields_ = [("outer_steps", C.c_int32), ("cg_iters", C.c_int32), ("exact_passes", C.c_int32),
                 ("status", C.c_int32), ("err_bound", C.c_double), ("resid_rel", C.c_double),
-                ("rdiag_max", C.c_double), ("rdiag_min", C.c_double), ("ms_sketch", C.c_float),
-                ("ms_qr", C.c_float), ("ms_solve", C.c_float), ("reserved", C.c_float)]
+                ("rdiag_max", C.c_double), ("rdiag_min", C.c_double), ("sigma_min_R", C.c_double),
+                ("sigma_max_R", C.c_double), ("cert_delta", C.c_double), ("ms_sketch", C.c_float),
+                ("ms_qr", C.c_float), ("ms_solve", C.c_float), ("ms_cg", C.c_float), ("ms_refine", C.c_float),
+                ("reserved", C.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}

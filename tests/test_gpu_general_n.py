@@ -3,9 +3,9 @@ Bluestein's chirp convolution (two FFTs of the power-of-two length L >= 2n - 1),
 against the oracle's transform (which takes Bluestein's identity too, but with its own
 radix-2 code, in FP64) and, through full solves, against the oracle's p.
 
-Tolerances: FP64 sketches 1e-12 relative, as for powers of two. FP32 sketches 8e-6:
-twice the power-of-two bound, since each element now passes two FFTs of length L and
-two chirp products (~2 log2 L + 20 roundings of 2^-24 instead of log2 n + 16)."""
+Tolerances: FP64 sketches 1e-12 relative, as for powers of two. Double-word sketches
+(mixed precision) (40 + 12 log2 L) 2^-46: twice the power-of-two bound, since each
+element now passes two FFTs of length L and two chirp products."""
 import numpy as np
 import pytest
 
@@ -67,11 +67,14 @@ def test_sketch_fp64_general_n(mn, m, n):
 
 
 @pytest.mark.parametrize("m,n", [(5, 100), (8, 3000), (6, 5000), (4, 40000)])
-def test_sketch_fp32_general_n(mn, m, n):
+def test_sketch_dw_general_n(mn, m, n):
     s = synth.make_system(m, n, exponent=2, seed=600 + n)
     Y = _sketch(mn, m, n, mn.MIXED, 23, s.A)
     Yref = oracle.sketch(oracle.draw_params(n, 4 * m, 23), s.A)
-    assert _rel(Y, Yref) <= 8e-6
+    L = 1 << int(np.ceil(np.log2(2 * n - 1)))
+    tol = (40 + 12 * np.log2(L)) * 2.0 ** -46
+    assert _rel(Y, Yref) <= tol
+    assert np.abs(Y - Yref).max() <= tol * np.abs(Yref).max()
 
 
 @pytest.mark.parametrize("m,k,prec", [(48, 21, 0), (48, 21, 1), (100, 37, 1), (37, 9, 0)])

@@ -32,8 +32,12 @@ def _check(x, p, eps, info):
     rel = np.linalg.norm(d) / np.linalg.norm(p)
     assert rel <= eps, (rel, info)
     assert np.max(np.abs(d)) <= eps * np.max(np.abs(p)), (np.max(np.abs(d)), info)
-    # the bound the library reports is a true bound (relative to ||x||)
-    assert rel * np.linalg.norm(p) <= 1.01 * info["err_bound"] * np.linalg.norm(x) + 1e-300, (rel, info)
+    # the bound the library reports is a true bound (relative to ||x||), and its ingredients are
+    # consistent: sigma_min(R) >= 1 / ||R^{-1}||_F <= |R_mm|, ||R||_F >= |R_11|, delta small
+    assert rel * np.linalg.norm(p) <= info["err_bound"] * np.linalg.norm(x), (rel, info)
+    assert info["cert_delta"] < 0.1, info
+    assert info["sigma_min_R"] <= info["rdiag_min"] * (1 + 1e-12), info
+    assert info["sigma_max_R"] >= info["rdiag_max"] * (1 - 1e-12), info
 
 
 def _solve(mn, A, b, prec, eps, seed):
