@@ -48,8 +48,8 @@ typedef struct minnorm_plan_s *minnorm_plan_t;
 typedef struct minnorm_batch_s *minnorm_batch_t;
 
 typedef enum {
-  MINNORM_C128 = 0,          /* A stored as complex128 */
-  MINNORM_C64 = 1            /* A stored as complex64  */
+  MINNORM_C64 = 1,           /* A stored as complex64  */
+  MINNORM_C128 = 2           /* A stored as complex128 */
 } minnorm_dtype;
 
 typedef enum {
@@ -135,6 +135,17 @@ minnorm_status minnorm_plan_set_params(minnorm_plan_t plan,
                                        const double *zeta_t, const int64_t *pi_t, const double *theta_t,
                                        const double *zeta, const int64_t *pi, const double *theta,
                                        const double *d, const int64_t *s);
+
+/*
+ * Copy the plan's SRFT realization (Section 3) into host arrays of the layout
+ * minnorm_plan_set_params takes: zeta_t, zeta, d: n complex128 (2n doubles);
+ * pi_t, pi: n int64; theta_t, theta: n-1 doubles; s: l int64. Any pointer may
+ * be NULL to skip that array. Exporting then setting the same arrays leaves the
+ * plan's transform unchanged (the oracle can also ingest them). No device
+ * access. Errors: EINVAL (null plan).
+ */
+minnorm_status minnorm_plan_export_params(minnorm_plan_t plan, double *zeta_t, int64_t *pi_t, double *theta_t,
+                                          double *zeta, int64_t *pi, double *theta, double *d, int64_t *s);
 
 /*
  * Steps 1-2 for the matrix A (device, row-major m x n, dtype of the plan):

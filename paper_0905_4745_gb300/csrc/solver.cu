@@ -1468,6 +1468,26 @@ minnorm_status minnorm_plan_set_params(minnorm_plan_t plan, const double *zeta_t
   return st;
 }
 
+minnorm_status minnorm_plan_export_params(minnorm_plan_t plan, double *zeta_t, int64_t *pi_t, double *theta_t,
+                                          double *zeta, int64_t *pi, double *theta, double *d, int64_t *s) {
+  if (!plan) return MINNORM_EINVAL;
+  const SrftParams &P = plan->P;
+  const int64_t n = plan->n, l = plan->l;
+  auto cplx = [&](const std::vector<std::complex<double>> &src, double *dst) {
+    if (!dst) return;
+    for (int64_t j = 0; j < n; ++j) { dst[2 * j] = src[j].real(); dst[2 * j + 1] = src[j].imag(); }
+  };
+  cplx(P.zeta_t, zeta_t);
+  cplx(P.zeta, zeta);
+  cplx(P.d, d);
+  if (pi_t) std::copy(P.pi_t.begin(), P.pi_t.end(), pi_t);
+  if (pi) std::copy(P.pi.begin(), P.pi.end(), pi);
+  if (theta_t) std::copy(P.theta_t.begin(), P.theta_t.begin() + (n - 1), theta_t);
+  if (theta) std::copy(P.theta.begin(), P.theta.begin() + (n - 1), theta);
+  if (s) std::copy(P.s.begin(), P.s.begin() + l, s);
+  return MINNORM_OK;
+}
+
 minnorm_status minnorm_sketch(minnorm_plan_t plan, const void *A, int64_t lda) {
   if (!plan || !A) return MINNORM_EINVAL;
   if (plan->failed) return MINNORM_ESTATE;

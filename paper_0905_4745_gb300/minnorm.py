@@ -15,12 +15,12 @@ LIB_PATH = os.path.join(HERE, "libminnorm.so")
 OK, EINVAL, ESTATE, ENOMEM, ECUDA, ERANK, ENOCONV, EFLOOR, ETIMEOUT, ENOTSUP = range(10)
 STATUS_NAMES = ["OK", "EINVAL", "ESTATE", "ENOMEM", "ECUDA", "ERANK", "ENOCONV", "EFLOOR",
                 "ETIMEOUT", "ENOTSUP"]
-C128, C64 = 0, 1
+C64, C128 = 1, 2
 FP64, MIXED = 0, 1
 FLAG_TIMING, FLAG_KEEP_SKETCH = 1, 2
 
 # every symbol include/minnorm.h declares
-EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_sketch", "minnorm_solve",
+EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_plan_export_params", "minnorm_sketch", "minnorm_solve",
            "minnorm_solve_host", "minnorm_plan_destroy", "minnorm_status_string", "minnorm_get_sketch",
            "minnorm_get_factor", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats",
            "minnorm_launch_count", "minnorm_qr_noalloc", "minnorm_solve_many", "minnorm_batch_create",
@@ -58,6 +58,7 @@ def lib():
         p, i64, u64, u32, i32, d = C.c_void_p, C.c_int64, C.c_uint64, C.c_uint32, C.c_int32, C.c_double
         L.minnorm_plan_create.argtypes = [C.POINTER(p), i64, i64, i64, C.c_int, C.c_int, u64, u32, p]
         L.minnorm_plan_set_params.argtypes = [p] * 9
+        L.minnorm_plan_export_params.argtypes = [p] * 9
         L.minnorm_sketch.argtypes = [p, p, i64]
         L.minnorm_solve.argtypes = [p, p, i64, p, d, p, C.POINTER(Info)]
         L.minnorm_solve_host.argtypes = [p, p, i64, p, d, p, C.POINTER(Info)]
@@ -136,6 +137,17 @@ def minnorm_plan_set_params(plan, zeta_t, pi_t, theta_t, zeta, pi, theta, d, s):
             np.ascontiguousarray(d, np.complex128), np.ascontiguousarray(s, np.int64)]
     st = lib().minnorm_plan_set_params(plan, *[a.ctypes.data for a in arrs])
     return _check(st, "minnorm_plan_set_params")
+
+
+def minnorm_plan_export_params(plan, n, l):
+    """The plan's SRFT realization as host numpy arrays (zeta_t, pi_t, theta_t, zeta, pi, theta, d, s),
+    in the form minnorm_plan_set_params and the oracle's parameter set take."""
+    import numpy as np
+    arrs = [np.empty(n, np.complex128), np.empty(n, np.int64), np.empty(n - 1, np.float64),
+            np.empty(n, np.complex128), np.empty(n, np.int64), np.empty(n - 1, np.float64),
+            np.empty(n, np.complex128), np.empty(l, np.int64)]
+    _check(lib().minnorm_plan_export_params(plan, *[a.ctypes.data for a in arrs]), "minnorm_plan_export_params")
+    return tuple(arrs)
 
 
 def minnorm_sketch(plan, A, lda=None, allow=(OK,)):

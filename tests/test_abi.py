@@ -57,15 +57,20 @@ def test_plan_create_validates_before_touching_the_device(libpath):
     from paper_0905_4745_gb300 import minnorm
     L = minnorm.lib()
     h = ctypes.c_void_p()
+    c128 = minnorm.C128
     bad = [(5, 5, 0), (0, 8, 0), (8, 4, 0), (4, 64, 4), (4, 64, 65)]
     for m, n, l in bad:
-        st = L.minnorm_plan_create(ctypes.byref(h), m, n, l, 0, 0, 1, 0, None)
+        st = L.minnorm_plan_create(ctypes.byref(h), m, n, l, c128, 0, 1, 0, None)
         assert st == minnorm.EINVAL, (m, n, l, st)
-    assert L.minnorm_plan_create(ctypes.byref(h), 4, 64, 0, 7, 0, 1, 0, None) == minnorm.EINVAL
-    assert L.minnorm_plan_create(ctypes.byref(h), 4, 64, 0, 0, 9, 1, 0, None) == minnorm.EINVAL
+    # storage kinds: MINNORM_C64 = 1, MINNORM_C128 = 2 (0 and others are invalid)
+    assert (minnorm.C64, minnorm.C128) == (1, 2)
+    for dt in (0, 3, 7):
+        assert L.minnorm_plan_create(ctypes.byref(h), 4, 64, 0, dt, 0, 1, 0, None) == minnorm.EINVAL
+    assert L.minnorm_plan_create(ctypes.byref(h), 4, 64, 0, c128, 9, 1, 0, None) == minnorm.EINVAL
     # n above 2^30 is beyond the transform's tables (any other n >= 2, power of two or not, is planned)
-    assert L.minnorm_plan_create(ctypes.byref(h), 4, (1 << 30) + 1, 0, 0, 0, 1, 0, None) == minnorm.ENOTSUP
-    assert L.minnorm_plan_create(None, 4, 64, 0, 0, 0, 1, 0, None) == minnorm.EINVAL
+    assert L.minnorm_plan_create(ctypes.byref(h), 4, (1 << 30) + 1, 0, c128, 0, 1, 0, None) == minnorm.ENOTSUP
+    assert L.minnorm_plan_create(None, 4, 64, 0, c128, 0, 1, 0, None) == minnorm.EINVAL
+    assert L.minnorm_plan_export_params(None, *([None] * 8)) == minnorm.EINVAL
     # null plan handles
     assert L.minnorm_sketch(None, None, 64) == minnorm.EINVAL
     assert L.minnorm_solve(None, None, 64, None, 1e-3, None, None) == minnorm.EINVAL

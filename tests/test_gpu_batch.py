@@ -84,8 +84,8 @@ def test_batch_statuses_and_errors(mn):
     h = ctypes.c_void_p()
     ms = (ctypes.c_int64 * 2)(8, 16)
     bad = (ctypes.c_int64 * 2)(64, 16)                   # m >= n for the second system
-    assert L.minnorm_batch_create(ctypes.byref(h), 2, ms, bad, 0, 0, 1, 0, None) == mn.EINVAL
-    assert L.minnorm_batch_create(ctypes.byref(h), 0, ms, bad, 0, 0, 1, 0, None) == mn.EINVAL
+    assert L.minnorm_batch_create(ctypes.byref(h), 2, ms, bad, mn.C128, 0, 1, 0, None) == mn.EINVAL
+    assert L.minnorm_batch_create(ctypes.byref(h), 0, ms, bad, mn.C128, 0, 1, 0, None) == mn.EINVAL
     # a rank-deficient system is reported in its own info and does not stop the others
     shapes = [(8, 100), (6, 90), (10, 120)]
     systems = [synth.make_system(m, n, exponent=2, seed=4200 + i) for i, (m, n) in enumerate(shapes)]

@@ -118,6 +118,31 @@ def test_sketch_dw_matches_oracle(mn, m, n):
     assert np.abs(Y - Yref).max() <= dw_sketch_tol(n) * np.abs(Yref).max()
 
 
+def test_export_params_round_trip(mn):
+    # the exported realization is the one the plan drew (the oracle's streams for the same seed),
+    # setting it back leaves the sketch bit for bit unchanged, and the oracle ingests it
+    m, n = 5, 2048
+    l = 4 * m
+    s = synth.make_system(m, n, exponent=1, seed=5)
+    plan = _plan(mn, m, n, mn.FP64, seed=29, flags=mn.FLAG_KEEP_SKETCH)
+    try:
+        E = mn.minnorm_plan_export_params(plan, n, l)
+        P = oracle.draw_params(n, l, 29)
+        for got, want in zip(E, (P.zeta_t, P.pi_t, P.theta_t, P.zeta, P.pi, P.theta, P.d, P.s)):
+            assert got.shape == want.shape
+            if got.dtype == np.int64:
+                assert np.array_equal(got, want)
+            else:      # phases and angles: libm on either side, within an ulp or two
+                assert np.max(np.abs(got - want)) <= 1e-15 * max(1.0, np.max(np.abs(want)))
+        Y0 = _sketch(mn, plan, _t(s.A), m, l)
+        mn.minnorm_plan_set_params(plan, *E)
+        Y1 = _sketch(mn, plan, _t(s.A), m, l)
+        assert np.array_equal(Y0, Y1)
+        assert _rel(Y1, oracle.sketch(oracle.Params(n, l, *E), s.A)) <= 1e-12
+    finally:
+        mn.minnorm_plan_destroy(plan)
+
+
 def test_sketch_with_injected_parameters(mn):
     # the same plan with parameters set from the oracle's streams of another seed,
     # and with a degenerate transform (no H): both must match the oracle's T
