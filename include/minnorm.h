@@ -162,12 +162,30 @@ minnorm_status minnorm_sketch(minnorm_plan_t plan, const void *A, int64_t lda);
  * ||x - p|| <= eps ||p|| when it returns MINNORM_OK. A must hold the same
  * values as at minnorm_sketch.
  *   eps:  in (0, 1); the refinement stops once its a-posteriori bound is <= eps.
- *   info: host pointer or NULL.
- * Errors: EINVAL, ESTATE (no sketch), ENOCONV, EFLOOR (x still written),
- * ECUDA. Synchronizes the stream once per refinement step.
+ *   info: host pointer, or NULL for the asynchronous form.
+ * With info != NULL the call synchronizes the stream once per refinement step
+ * (the stopping test is read on the host) and returns the solve's status:
+ * EINVAL, ESTATE (no sketch), ENOCONV, EFLOOR (x still written), ETIMEOUT, ECUDA.
+ * With info == NULL the call makes no host round trip: it enqueues the whole
+ * refinement loop (at most 12 steps; the stopping test runs on the device and the
+ * steps after it return at once) and the copy of x, and returns MINNORM_OK once
+ * they are enqueued (argument errors are still returned at once). The solve's
+ * status then sits in a device word of the plan; read it with
+ * minnorm_solve_wait. Until then x, b and A must stay valid and unchanged. A
+ * plan that has not yet run a synchronous solve uses its default work splits
+ * (the autotuner runs only in the synchronous form).
  */
 minnorm_status minnorm_solve(minnorm_plan_t plan, const void *A, int64_t lda, const void *b,
                              double eps, void *x, minnorm_info *info);
+
+/*
+ * Waits for the plan's last asynchronous minnorm_solve (synchronizes the plan's
+ * stream) and returns that solve's status (OK, ENOCONV, EFLOOR, or ETIMEOUT when
+ * a bounded device-side wait expired). info (host, nullable) receives its step
+ * counts, bound and residual; with MINNORM_FLAG_TIMING also its times.
+ * Errors: EINVAL (null plan), ESTATE (no asynchronous solve pending), ECUDA.
+ */
+minnorm_status minnorm_solve_wait(minnorm_plan_t plan, minnorm_info *info);
 
 /*
  * Steps 3-5 for nrhs right-hand sides sharing the A, T and R of the last
@@ -235,6 +253,16 @@ minnorm_status minnorm_batch_destroy(minnorm_batch_t batch);
 
 /* Free the plan and its workspace (synchronizes its stream). NULL is accepted. */
 minnorm_status minnorm_plan_destroy(minnorm_plan_t plan);
+
+/* Limit of the plan's bounded device-side waits (grid barriers, the QR's pivot
+ * exchange, mbarrier phases): limit_ns in [1 ms, 2 s], 2 s by default. A wait
+ * that runs out makes its kernel record the failure, wait (bounded) for its own
+ * copies in flight, release what it holds and return; the call then reports
+ * MINNORM_ETIMEOUT and the plan is left usable only for destroy. withhold = 1
+ * (tests of that path) makes one CTA of the plan's next fused CG launch (mixed
+ * precision, m <= 512) leave at once without arriving at the grid barrier, so
+ * the wait runs out for certain. The paper has no counterpart. Errors: EINVAL. */
+minnorm_status minnorm_plan_set_wait_limit(minnorm_plan_t plan, uint64_t limit_ns, int32_t withhold);
 
 /* Static string naming a status. */
 const char *minnorm_status_string(minnorm_status status);

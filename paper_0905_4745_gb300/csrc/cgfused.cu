@@ -50,6 +50,8 @@ struct CgFusedParams {
   GridBarrier *bar;
   int *err;
   uint64_t limit_ns;
+  const int *skip;
+  int withhold;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -178,6 +180,12 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
   __shared__ double s_scal[4];
   __shared__ double s_qq[kCgThreads / 32];
   __shared__ float s_red[kCgThreads / 32][32];
+  // an asynchronous solve that has stopped: every CTA reads the same word (written by an
+  // earlier kernel of the stream), so all return before the first grid barrier
+  if (P.skip && *P.skip) return;
+  // a test of the bounded waits: CTA 0 leaves before it issues any copy or arrives anywhere,
+  // so the others' first grid barrier runs out after limit_ns and they report ETIMEOUT
+  if (P.withhold && blockIdx.x == 0) return;
 
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
@@ -529,6 +537,8 @@ cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st) {
   P.bar = a.bar;
   P.err = a.err;
   P.limit_ns = a.limit_ns;
+  P.skip = a.skip;
+  P.withhold = a.withhold;
   const size_t smem = cg_fused_smem(a.m);
   cudaError_t e = cudaFuncSetAttribute(cg_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

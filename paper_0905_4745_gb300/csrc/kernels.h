@@ -135,6 +135,7 @@ struct XprodArgs {
   void *xpart;            // xadj_partial_bytes(rows, cols): row-split partial sums of A^* y
   void *xfix;             // xfix_bytes(cols): x in 128-bit fixed point for the forward product
   int xsplit;             // row splits of x = A^* y (0: xadj_splits); at most xadj_max_splits(rows)
+  const int *skip;        // if set and nonzero on the device, every kernel returns at once
 };
 // The fixed-point copy of A (and its complex64 copy when A32 is set); with rown2 set, also an
 // upper bound of ||A[i, :]||^2 per row (rigorous: the rounding of the float sums is added).
@@ -165,6 +166,9 @@ struct CgFusedArgs {
   int grid;                // CTAs (one per SM)
   double keep_frac;        // share of L2 the tail of each sweep is loaded into with an evict-last hint
                            // (negative: the default); a cache hint only, results do not depend on it
+  const int *skip;         // if set and nonzero on the device, the kernel returns at once
+  int withhold;            // 1: CTA 0 returns at once without arriving at the grid barrier (tests of
+                           // the bounded wait: the others time out and report it)
 };
 bool cg_fused_supported(int64_t m, int64_t n, int64_t lda, const void *A);
 cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st);

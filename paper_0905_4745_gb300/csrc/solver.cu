@@ -161,6 +161,14 @@ struct minnorm_plan_s {
   // host pinned scalars
   double *h_norms = nullptr;
   CgScalars *h_cg = nullptr;
+  // asynchronous solve (minnorm_solve with info == NULL): device state, pinned copy, pending flag
+  SolveState *d_ss = nullptr, *h_ss = nullptr;
+  bool async_pending = false;
+  // bounded device-side waits: their limit, and (tests) a CTA of the next fused CG launch that
+  // withholds its arrival at the grid barrier
+  uint64_t wait_limit_ns = kBarrierLimitNs;
+  int withhold = 0;
+  cudaEvent_t ev_as0 = nullptr, ev_as1 = nullptr;
   // timing
   std::vector<KernelTimer> timers;
   std::vector<cudaEvent_t> event_pool;
@@ -586,6 +594,8 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   }
   if (cudaMallocHost(&plan->h_norms, sizeof(double) * 4) != cudaSuccess) return MINNORM_ENOMEM;
   if (cudaMallocHost(&plan->h_cg, sizeof(CgScalars)) != cudaSuccess) return MINNORM_ENOMEM;
+  if (cudaMallocHost(&plan->h_ss, sizeof(SolveState)) != cudaSuccess) return MINNORM_ENOMEM;
+  ALLOC(plan->d_ss, sizeof(SolveState));
   if (cudaMallocHost(&plan->h_qr, sizeof(double) * 6) != cudaSuccess) return MINNORM_ENOMEM;
   draw_srft_params(seed, n, l, plan->P);
   return upload_params(plan);
@@ -675,7 +685,7 @@ minnorm_status sketch_factor(minnorm_plan_t plan) {
     Timed tm(plan, 3);
     CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
     QrArgs q{plan->d_Y, (int)l, (int)m, plan->d_vn1, plan->d_vn2, plan->d_beta, plan->d_piv, plan->d_R,
-             plan->d_qrmail, plan->d_err, kBarrierLimitNs};
+             plan->d_qrmail, plan->d_err, plan->wait_limit_ns};
     CK(launch_qrp(q, st));
     CK(launch_prinv(plan->d_R, plan->d_piv, (int)m, plan->d_Wp, plan->d_WpH, st));
     // ||R||_F, ||P R^{-1}||_F and ||A||_F for the certificate's delta
@@ -912,13 +922,15 @@ minnorm_status inner_cg(minnorm_plan_t plan, const void *Acg, double tol, int ma
     a.maxit = maxit;
     a.bar = plan->d_bar;
     a.err = plan->d_err;
-    a.limit_ns = kBarrierLimitNs;
+    a.limit_ns = plan->wait_limit_ns;
     a.grid = plan->sms;
     if (!plan->cg_tuned) {
       minnorm_status ts = tune_cg_keep(plan, a);
       if (ts != MINNORM_OK) return ts;
     }
     a.keep_frac = plan->cg_keep;
+    a.withhold = plan->withhold;
+    plan->withhold = 0;
     {
       Timed tm(plan, 5);
       CK(launch_cg_fused(a, st));
@@ -1066,12 +1078,14 @@ minnorm_status tune_xresidual(minnorm_plan_t plan, const void *b) {
 }
 
 // one exact residual with the plan's (tuned) split
-minnorm_status xresidual(minnorm_plan_t plan, const void *b) {
-  if (!plan->x_tuned) {
+minnorm_status xresidual(minnorm_plan_t plan, const void *b, const int *skip = nullptr) {
+  if (!plan->x_tuned && !skip) {  // an asynchronous solve keeps the current split (no host round trip)
     minnorm_status s = tune_xresidual(plan, b);
     if (s != MINNORM_OK) return s;
   }
-  CK(launch_xresidual(xargs(plan, b), plan->st));
+  XprodArgs a = xargs(plan, b);
+  a.skip = skip;
+  CK(launch_xresidual(a, plan->st));
   return MINNORM_OK;
 }
 
@@ -1162,6 +1176,111 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
     info->ms_refine = (float)(plan->stat_ms[2] - ms0[2]);
   }
   return status;
+}
+
+// ---- Steps 3-5 without host round trips (minnorm_solve with info == NULL) -----------
+// The refinement loop of solve_impl, enqueued whole: kMaxOuter steps, each opened by the
+// stopping test on the device (solve_stop_kernel, the same rule and certificate as the host
+// loop). Once the test fires it sets SolveState::done, and every kernel of the later steps
+// (the small products, the CG kernels through their `done` word, the accumulation of y and the
+// exact residual) returns at once. The inner CG of the two-pass form enqueues its maxit
+// iterations (each kernel returns once the CG's own test has fired). Nothing is tuned here: a
+// plan that has not yet run a synchronous solve uses the default work splits. The status, the
+// step counts and the bound stay on the device until minnorm_solve_wait.
+minnorm_status solve_async(minnorm_plan_t plan, const void *A, const void *b, double eps, void *x) {
+  cudaStream_t st = plan->st;
+  const int64_t m = plan->m, n = plan->n;
+  const bool timing = plan->flags & MINNORM_FLAG_TIMING;
+  if (!plan->ev_as0) {
+    CK(cudaEventCreate(&plan->ev_as0));
+    CK(cudaEventCreate(&plan->ev_as1));
+  }
+  if (timing) CK(cudaEventRecord(plan->ev_as0, st));
+  const void *Acg = plan->d_A32 ? (const void *)plan->d_A32 : A;
+  const int *skip = &plan->d_ss->done;
+  CK(cudaMemsetAsync(plan->d_yh, 0, sizeof(zd) * m, st));
+  CK(cudaMemsetAsync(plan->d_yl, 0, sizeof(zd) * m, st));
+  CK(cudaMemsetAsync(plan->d_xh, 0, sizeof(zd) * n, st));
+  CK(cudaMemsetAsync(plan->d_xl, 0, sizeof(zd) * n, st));
+  CK(cudaMemcpyAsync(plan->d_r, b, sizeof(zd) * m, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
+  CK(launch_solve_state_init(plan->d_ss, st));
+  const CertConsts cc{plan->cert_delta, 1.0 + plan->inv_eta + 4.0 * (double)m * 0x1.0p-53, eps};
+  const double tol_inner = plan->fp32 ? 1e-3 : 1e-11;
+  const int maxit = plan->fp32 ? 40 : 300;
+  const bool fused = plan->fused_ok && cg_fused_supported(plan->m, plan->n, plan->g_cg.ld, Acg);
+  for (int outer = 0; outer <= kMaxOuter; ++outer) {
+    const bool final = outer == kMaxOuter;
+    CK(launch_small_gemv(plan->d_WpH, (int)m, plan->d_r, plan->d_g, nullptr, skip, st));
+    CK(launch_sumsq(m, plan->d_g, plan->d_red, plan->d_norms, st));
+    if (outer > 0) CK(launch_sumsq(n, plan->d_xh, plan->d_red + 1024, plan->d_norms + 1, st));
+    CK(launch_solve_stop(plan->d_ss, plan->d_norms, outer, final, cc, outer > 0 ? plan->d_cg : nullptr, st));
+    if (final) break;
+    if (fused) {
+      CK(cudaMemsetAsync(plan->d_bar, 0, sizeof(GridBarrier), st));
+      CgFusedArgs a{};
+      a.A = Acg;
+      a.m = plan->m;
+      a.n = plan->n;
+      a.lda = plan->g_cg.ld;
+      a.Wp = plan->d_Wp;
+      a.WpH = plan->d_WpH;
+      a.g = plan->d_g;
+      a.u = plan->d_u;
+      a.s = plan->d_s;
+      a.w = plan->d_w;
+      a.t = plan->d_t;
+      a.dy = plan->d_dy;
+      a.tpart = plan->d_tpart;
+      a.qq_part = plan->d_qqp;
+      a.gg_part = plan->d_ggp;
+      a.sc = plan->d_cg;
+      a.tol2 = tol_inner * tol_inner;
+      a.maxit = maxit;
+      a.bar = plan->d_bar;
+      a.err = plan->d_err;
+      a.limit_ns = plan->wait_limit_ns;
+      a.grid = plan->sms;
+      a.keep_frac = plan->cg_keep;
+      a.skip = skip;
+      a.withhold = plan->withhold;
+      plan->withhold = 0;
+      Timed tm(plan, 5);
+      CK(launch_cg_fused(a, st));
+    } else {
+      const int *done = &plan->d_cg->done;
+      const int mi = (int)m;
+      CK(launch_cg_init(mi, plan->d_g, plan->d_u, plan->d_s, plan->d_p, plan->d_cg, st, skip));
+      for (int k = 0; k < maxit; ++k) {
+        if (plan->fp32) {
+          CK(launch_small_gemv(plan->d_Wp, mi, plan->d_p, plan->d_w, plan->d_w32, done, st));
+          { Timed tm(plan, 0); CK(launch_gemv_adj_f32(plan->g_cg, Acg, plan->d_w32, plan->d_q, plan->d_part, plan->d_qq, done, st)); }
+          { Timed tm(plan, 1); CK(launch_gemv_fwd_f32(plan->g_cg, Acg, plan->d_q, plan->d_t, plan->d_part, done, st)); }
+        } else {
+          CK(launch_small_gemv(plan->d_Wp, mi, plan->d_p, plan->d_w, nullptr, done, st));
+          { Timed tm(plan, 0); CK(launch_gemv_adj(plan->g_cg, Acg, plan->d_w, plan->d_q, plan->d_part, plan->d_qq, done, st)); }
+          { Timed tm(plan, 1); CK(launch_gemv_fwd(plan->g_cg, Acg, plan->d_q, plan->d_t, plan->d_part, done, st)); }
+        }
+        CK(launch_small_gemv(plan->d_WpH, mi, plan->d_t, plan->d_np, nullptr, done, st));
+        CK(launch_cg_update(mi, plan->d_qq, plan->nqq, plan->d_np, plan->d_u, plan->d_s, plan->d_p, plan->d_cg,
+                            tol_inner * tol_inner, st));
+      }
+      CK(launch_small_gemv(plan->d_Wp, mi, plan->d_u, plan->d_dy, nullptr, skip, st));
+    }
+    CK(launch_dd_accumulate(m, plan->d_yh, plan->d_yl, plan->d_dy, st, skip));
+    {
+      Timed tm(plan, 2);
+      minnorm_status xs = xresidual(plan, b, skip);
+      if (xs != MINNORM_OK) return xs;
+    }
+  }
+  CK(cudaMemcpyAsync(x, plan->d_xh, sizeof(zd) * n, cudaMemcpyDeviceToDevice, st));
+  if (timing) CK(cudaEventRecord(plan->ev_as1, st));
+  // ||r||^2 and ||b||^2 for the report, kept on the device
+  CK(launch_sumsq(m, plan->d_r, plan->d_red, plan->d_norms + 2, st));
+  CK(launch_sumsq(m, (const zd *)b, plan->d_red + 1024, plan->d_norms + 3, st));
+  plan->async_pending = true;
+  return MINNORM_OK;
 }
 
 // argument checks of minnorm_plan_create (no device access)
@@ -1268,7 +1387,7 @@ minnorm_status block_inner_cg(minnorm_plan_t plan, const void *Acg, int64_t lda_
   pa.Bsplit2 = plan->d_bsplit2;
   pa.nsplit_tc = plan->blk_nsplit_tc;
   pa.err = plan->d_err;
-  pa.limit_ns = kBarrierLimitNs;
+  pa.limit_ns = plan->wait_limit_ns;
   pa.sms = plan->sms;
   CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
   int it = 0;
@@ -1508,7 +1627,55 @@ minnorm_status minnorm_solve(minnorm_plan_t plan, const void *A, int64_t lda, co
   if (!(eps > 0.0 && eps < 1.0)) return MINNORM_EINVAL;
   plan->g_hp.ld = lda;
   plan->g_cg.ld = plan->d_A32 ? plan->n : lda;
+  plan->async_pending = false;
+  if (!info) return solve_async(plan, A, b, eps, x);
   return solve_impl(plan, A, lda, b, eps, x, info);
+}
+
+minnorm_status minnorm_plan_set_wait_limit(minnorm_plan_t plan, uint64_t limit_ns, int32_t withhold) {
+  if (!plan || limit_ns < 1000000ull || limit_ns > kBarrierLimitNs || withhold < 0 || withhold > 1)
+    return MINNORM_EINVAL;
+  plan->wait_limit_ns = limit_ns;
+  plan->withhold = withhold;
+  return MINNORM_OK;
+}
+
+minnorm_status minnorm_solve_wait(minnorm_plan_t plan, minnorm_info *info) {
+  if (!plan) return MINNORM_EINVAL;
+  if (!plan->async_pending) return MINNORM_ESTATE;
+  plan->async_pending = false;
+  cudaStream_t st = plan->st;
+  int err = 0;
+  CK(cudaMemcpyAsync(plan->h_ss, plan->d_ss, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(plan->h_norms + 2, plan->d_norms + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (err) {
+    plan->failed = true;
+    return MINNORM_ETIMEOUT;
+  }
+  const SolveState ss = *plan->h_ss;
+  if (info) {
+    fill_factor_info(plan, info);
+    info->outer_steps = ss.outer;
+    info->cg_iters = ss.cg_total;
+    info->exact_passes = 2 * ss.outer;
+    info->status = ss.status;
+    info->err_bound = ss.err;
+    const double bn = std::sqrt(plan->h_norms[3]);
+    info->resid_rel = bn > 0 ? std::sqrt(plan->h_norms[2]) / bn : 0.0;
+    if (plan->flags & MINNORM_FLAG_TIMING) {
+      cudaEventElapsedTime(&info->ms_solve, plan->ev_as0, plan->ev_as1);
+      double ms0[6];
+      memcpy(ms0, plan->stat_ms, sizeof(ms0));
+      collect_timers(plan);
+      info->ms_cg = (float)(plan->stat_ms[0] + plan->stat_ms[1] + plan->stat_ms[5] - ms0[0] - ms0[1] - ms0[5]);
+      info->ms_refine = (float)(plan->stat_ms[2] - ms0[2]);
+    }
+  } else if (plan->flags & MINNORM_FLAG_TIMING) {
+    collect_timers(plan);
+  }
+  return (minnorm_status)ss.status;
 }
 
 minnorm_status minnorm_solve_many(minnorm_plan_t plan, const void *A, int64_t lda, const void *B, int64_t ldb,
@@ -1573,7 +1740,8 @@ minnorm_status minnorm_solve_host(minnorm_plan_t plan, const void *A_host, int64
     s = minnorm_sketch(plan, plan->d_Ah, n);
     if (s != MINNORM_OK) return s;
   }
-  minnorm_status r = minnorm_solve(plan, plan->d_Ah, n, plan->d_bh, eps, plan->d_xo, info);
+  minnorm_info local{};
+  minnorm_status r = minnorm_solve(plan, plan->d_Ah, n, plan->d_bh, eps, plan->d_xo, info ? info : &local);
   if (r != MINNORM_OK && r != MINNORM_ENOCONV && r != MINNORM_EFLOOR) return r;
   CK(cudaMemcpyAsync(x_host, plan->d_xo, sizeof(zd) * n, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -1593,6 +1761,9 @@ minnorm_status minnorm_plan_destroy(minnorm_plan_t plan) {
   for (cudaEvent_t e : plan->event_pool) cudaEventDestroy(e);
   if (plan->h_norms) cudaFreeHost(plan->h_norms);
   if (plan->h_cg) cudaFreeHost(plan->h_cg);
+  if (plan->h_ss) cudaFreeHost(plan->h_ss);
+  if (plan->ev_as0) cudaEventDestroy(plan->ev_as0);
+  if (plan->ev_as1) cudaEventDestroy(plan->ev_as1);
   if (plan->h_qr) cudaFreeHost(plan->h_qr);
   if (plan->h_bpart) cudaFreeHost(plan->h_bpart);
   if (plan->h_bint) cudaFreeHost(plan->h_bint);
@@ -1685,7 +1856,7 @@ minnorm_status minnorm_block_products(minnorm_plan_t plan, const void *A, int64_
   pa.Bsplit2 = plan->d_bsplit2;
   pa.nsplit_tc = plan->blk_nsplit_tc;
   pa.err = plan->d_err;
-  pa.limit_ns = kBarrierLimitNs;
+  pa.limit_ns = plan->wait_limit_ns;
   pa.sms = plan->sms;
   CK(launch_block_adj(pa, st));
   CK(launch_block_fwd(pa, st));
@@ -1890,7 +2061,8 @@ minnorm_status minnorm_batch_solve(minnorm_batch_t batch, const void *const *A, 
     minnorm_status s = st[i];
     if (s == MINNORM_OK) {
       BCK(launch_fix_prep(A[i], ld, p->dtype == MINNORM_C64, p->m, p->n, p->d_afix, p->d_E, p->d_A32, p->st));
-      s = minnorm_solve(p, A[i], ld, b[i], eps, x[i], infos ? infos + i : nullptr);
+      minnorm_info local{};
+      s = minnorm_solve(p, A[i], ld, b[i], eps, x[i], infos ? infos + i : &local);
     } else if (infos) {
       memset(infos + i, 0, sizeof(minnorm_info));
       infos[i].status = s;

@@ -12,8 +12,12 @@ namespace mn {
 
 __global__ void __launch_bounds__(1024)
 cg_init_kernel(int m, const zd *__restrict__ g, zd *__restrict__ u, zd *__restrict__ s, zd *__restrict__ p,
-               CgScalars *sc) {
+               CgScalars *sc, const int *__restrict__ skip) {
   __shared__ double red[32];
+  if (skip && *skip) {  // the solve has stopped: the inner loop's kernels return at once
+    if (threadIdx.x == 0) { sc->done = 1; sc->iters = 0; }
+    return;
+  }
   double loc = 0.0;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     const zd v = g[i];
@@ -73,7 +77,8 @@ cg_update_kernel(int m, const double *__restrict__ qq_part, int nqq, const zd *_
 
 // (yh, yl) += d   componentwise, double-double
 __global__ void dd_accumulate_kernel(int64_t len, zd *__restrict__ yh, zd *__restrict__ yl,
-                                     const zd *__restrict__ d) {
+                                     const zd *__restrict__ d, const int *__restrict__ skip) {
+  if (skip && *skip) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
     const zd h = yh[i], l = yl[i], v = d[i];
     double s1, e1, s2, e2;
@@ -137,9 +142,57 @@ static int blocks_for(int64_t len) {
   return (int)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
 }
 
-cudaError_t launch_cg_init(int m, const void *g, void *u, void *s, void *p, CgScalars *sc, cudaStream_t st) {
+cudaError_t launch_cg_init(int m, const void *g, void *u, void *s, void *p, CgScalars *sc, cudaStream_t st,
+                           const int *skip) {
   note_launch();
-  cg_init_kernel<<<1, 1024, 0, st>>>(m, (const zd *)g, (zd *)u, (zd *)s, (zd *)p, sc);
+  cg_init_kernel<<<1, 1024, 0, st>>>(m, (const zd *)g, (zd *)u, (zd *)s, (zd *)p, sc, skip);
+  return cudaGetLastError();
+}
+
+__global__ void solve_state_init_kernel(SolveState *ss) {
+  ss->done = 0;
+  ss->status = 6;  // MINNORM_ENOCONV until a test passes
+  ss->outer = 0;
+  ss->stagnant = 0;
+  ss->cg_total = 0;
+  ss->err = __longlong_as_double(0x7ff0000000000000LL);   // +inf
+  ss->prev = ss->err;
+}
+
+// The same stopping rule as the host loop of a synchronous solve: stop with OK once the
+// certified bound ||g|| factor / ((1 - delta) ||x||) + 2^-52 is within eps, with EFLOOR after two
+// steps in a row that did not halve it, with ENOCONV after the last step.
+__global__ void solve_stop_kernel(SolveState *ss, const double *norms, int outer, int final, CertConsts c,
+                                  const CgScalars *sc) {
+  if (ss->done) return;
+  if (sc && outer > 0) ss->cg_total += sc->iters;
+  const double gn = sqrt(norms[0]);
+  if (outer == 0 && !final) {
+    if (gn == 0.0) { ss->done = 1; ss->status = 0; ss->err = 0.0; }
+    return;
+  }
+  const double xn = sqrt(norms[1]);
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  const double err = (xn > 0.0 && c.delta < 0.5) ? gn * c.factor / ((1.0 - c.delta) * xn) + 0x1.0p-52 : inf;
+  ss->err = err;
+  ss->outer = outer;
+  if (err <= c.eps) { ss->done = 1; ss->status = 0; return; }
+  if (final) { ss->done = 1; ss->status = 6; return; }   // ENOCONV
+  ss->stagnant = (err > 0.5 * ss->prev) ? ss->stagnant + 1 : 0;
+  ss->prev = err;
+  if (ss->stagnant >= 2) { ss->done = 1; ss->status = 7; }  // EFLOOR
+}
+
+cudaError_t launch_solve_state_init(SolveState *ss, cudaStream_t st) {
+  note_launch();
+  solve_state_init_kernel<<<1, 1, 0, st>>>(ss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_stop(SolveState *ss, const double *norms, int outer, bool final, CertConsts c,
+                              const CgScalars *sc, cudaStream_t st) {
+  note_launch();
+  solve_stop_kernel<<<1, 1, 0, st>>>(ss, norms, outer, final ? 1 : 0, c, sc);
   return cudaGetLastError();
 }
 
@@ -150,9 +203,10 @@ cudaError_t launch_cg_update(int m, const double *qq, int nqq, const void *np, v
   return cudaGetLastError();
 }
 
-cudaError_t launch_dd_accumulate(int64_t len, void *yh, void *yl, const void *d, cudaStream_t st) {
+cudaError_t launch_dd_accumulate(int64_t len, void *yh, void *yl, const void *d, cudaStream_t st,
+                                 const int *skip) {
   note_launch();
-  dd_accumulate_kernel<<<blocks_for(len), 256, 0, st>>>(len, (zd *)yh, (zd *)yl, (const zd *)d);
+  dd_accumulate_kernel<<<blocks_for(len), 256, 0, st>>>(len, (zd *)yh, (zd *)yl, (const zd *)d, skip);
   return cudaGetLastError();
 }
 

@@ -144,8 +144,9 @@ fix_prep_kernel(const T *__restrict__ A, int64_t lda, int64_t cols, fixc *__rest
 // ---- y' = (yh + yl) 2^E_i as 128-bit fixed point ------------------------------
 __global__ void __launch_bounds__(1024)
 fix_y_kernel(int m, const zd *__restrict__ yh, const zd *__restrict__ yl, const int32_t *__restrict__ E,
-             int Wy, i128c *__restrict__ yfix, int *__restrict__ Fy_out) {
+             int Wy, i128c *__restrict__ yfix, int *__restrict__ Fy_out, const int *__restrict__ skip) {
   __shared__ int red[32];
+  if (skip && *skip) return;  // an asynchronous solve that has stopped
   int mx = -100000;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     const zd h = yh[i];
@@ -180,9 +181,10 @@ constexpr int kXadjUnroll = 8;
 // loads' latency); each writes its exact partial sums, added by xadj_finish.
 __global__ void __launch_bounds__(kXadjThreads)
 xadj_kernel(const fixc *__restrict__ afix, int64_t rows, int64_t cols, const i128c *__restrict__ yfix,
-            i128c *__restrict__ xpart) {
+            i128c *__restrict__ xpart, const int *__restrict__ skip) {
   __shared__ i128c sy[kXadjThreads];
   __shared__ i128 ss[kXadjThreads];
+  if (skip && *skip) return;  // an asynchronous solve that has stopped
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t per = (rows + gridDim.y - 1) / gridDim.y;
   const int64_t r0 = (int64_t)blockIdx.y * per, r1 = r0 + per < rows ? r0 + per : rows;
@@ -228,8 +230,9 @@ xadj_kernel(const fixc *__restrict__ afix, int64_t rows, int64_t cols, const i12
 // x_j = sum of the row splits' partials, as double-double; max exponent to Fx
 __global__ void __launch_bounds__(256)
 xadj_finish_kernel(const i128c *__restrict__ xpart, int nsplit, int64_t cols, const int *__restrict__ Fy, int Wy,
-                   zd *__restrict__ xh, zd *__restrict__ xl, int *__restrict__ Fx) {
+                   zd *__restrict__ xh, zd *__restrict__ xl, int *__restrict__ Fx, const int *__restrict__ skip) {
   __shared__ int red[8];
+  if (skip && *skip) return;  // an asynchronous solve that has stopped
   int mx = -100000;
   const int scale = 2 + *Fy - Wy;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols; j += (int64_t)gridDim.x * blockDim.x) {
@@ -261,7 +264,8 @@ xadj_finish_kernel(const i128c *__restrict__ xpart, int nsplit, int64_t cols, co
 // x' = (xh + xl) 2^(Wx - Fx) as 128-bit fixed point, once per column for the forward pass
 __global__ void __launch_bounds__(256)
 xfix_kernel(int64_t cols, const zd *__restrict__ xh, const zd *__restrict__ xl, const int *__restrict__ Fx, int Wx,
-            i128c *__restrict__ xfix) {
+            i128c *__restrict__ xfix, const int *__restrict__ skip) {
+  if (skip && *skip) return;  // an asynchronous solve that has stopped
   const int k = Wx - *Fx;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols; j += (int64_t)gridDim.x * blockDim.x) {
     const zd h = xh[j], l = xl[j];
@@ -281,8 +285,9 @@ __device__ __forceinline__ i128 shfl_xor_i128(i128 v, int o) {
 
 __global__ void __launch_bounds__(kXfwdThreads)
 xfwd_kernel(const fixc *__restrict__ afix, int64_t rows, int64_t cols, const i128c *__restrict__ xfix,
-            int64_t chunk, i128c *__restrict__ partial) {
+            int64_t chunk, i128c *__restrict__ partial, const int *__restrict__ skip) {
   __shared__ i128c sred[(kXfwdThreads / 32) * kXfwdRows];
+  if (skip && *skip) return;  // an asynchronous solve that has stopped
   const int64_t i0 = (int64_t)blockIdx.y * kXfwdRows;
   const int64_t c0 = (int64_t)blockIdx.x * chunk;
   const int64_t c1 = c0 + chunk < cols ? c0 + chunk : cols;
@@ -335,7 +340,8 @@ xfwd_kernel(const fixc *__restrict__ afix, int64_t rows, int64_t cols, const i12
 __global__ void xfwd_finish_kernel(const i128c *__restrict__ partial, int nchunk, int64_t rows,
                                    const int32_t *__restrict__ E, const int *__restrict__ Fx, int Wx,
                                    const zd *__restrict__ b, zd *__restrict__ r, zd *__restrict__ th,
-                                   zd *__restrict__ tl) {
+                                   zd *__restrict__ tl, const int *__restrict__ skip) {
+  if (skip && *skip) return;  // an asynchronous solve that has stopped
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
     i128 sr = 0, si = 0;
     for (int c = 0; c < nchunk; ++c) {
@@ -406,20 +412,20 @@ cudaError_t launch_xresidual(const XprodArgs &a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   note_launch();
   fix_y_kernel<<<1, 1024, 0, st>>>((int)a.rows, (const zd *)a.yh, (const zd *)a.yl, a.E, Wy, (i128c *)a.yfix,
-                                   a.Fy);
+                                   a.Fy, a.skip);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {
     const int64_t nbx = (a.cols + kXadjThreads - 1) / kXadjThreads;
     const int nsplit = a.xsplit > 0 ? a.xsplit : xadj_splits(a.rows, a.cols);
     note_launch();
     xadj_kernel<<<dim3((unsigned)nbx, (unsigned)nsplit), kXadjThreads, 0, st>>>(
-        (const fixc *)a.afix, a.rows, a.cols, (const i128c *)a.yfix, (i128c *)a.xpart);
+        (const fixc *)a.afix, a.rows, a.cols, (const i128c *)a.yfix, (i128c *)a.xpart, a.skip);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int64_t nb = (a.cols + 255) / 256;
     if (nb > 2048) nb = 2048;
     note_launch();
     xadj_finish_kernel<<<(unsigned)nb, 256, 0, st>>>((const i128c *)a.xpart, nsplit, a.cols, a.Fy, Wy,
-                                                     (zd *)a.xh, (zd *)a.xl, a.Fx);
+                                                     (zd *)a.xh, (zd *)a.xl, a.Fx, a.skip);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (!a.b) return cudaSuccess;  // x only
@@ -428,19 +434,19 @@ cudaError_t launch_xresidual(const XprodArgs &a, cudaStream_t st) {
     if (nb > 2048) nb = 2048;
     note_launch();
     xfix_kernel<<<(unsigned)nb, 256, 0, st>>>(a.cols, (const zd *)a.xh, (const zd *)a.xl, a.Fx, Wx,
-                                              (i128c *)a.xfix);
+                                              (i128c *)a.xfix, a.skip);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   dim3 grid(a.nchunk, (unsigned)((a.rows + kXfwdRows - 1) / kXfwdRows));
   note_launch();
   xfwd_kernel<<<grid, kXfwdThreads, 0, st>>>((const fixc *)a.afix, a.rows, a.cols, (const i128c *)a.xfix, a.chunk,
-                                             (i128c *)a.partial);
+                                             (i128c *)a.partial, a.skip);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int64_t nb = (a.rows + 255) / 256;
   if (nb > 1024) nb = 1024;
   note_launch();
   xfwd_finish_kernel<<<(unsigned)nb, 256, 0, st>>>((const i128c *)a.partial, a.nchunk, a.rows, a.E, a.Fx, Wx,
-                                                   (const zd *)a.b, (zd *)a.r, (zd *)a.th, (zd *)a.tl);
+                                                   (const zd *)a.b, (zd *)a.r, (zd *)a.th, (zd *)a.tl, a.skip);
   return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ FP64, MIXED = 0, 1
 FLAG_TIMING, FLAG_KEEP_SKETCH = 1, 2
 
 # every symbol include/minnorm.h declares
-EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_plan_export_params", "minnorm_sketch", "minnorm_solve",
+EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_plan_export_params", "minnorm_sketch", "minnorm_solve", "minnorm_solve_wait", "minnorm_plan_set_wait_limit",
            "minnorm_solve_host", "minnorm_plan_destroy", "minnorm_status_string", "minnorm_get_sketch",
            "minnorm_get_factor", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats",
            "minnorm_launch_count", "minnorm_qr_noalloc", "minnorm_solve_many", "minnorm_batch_create",
@@ -61,6 +61,8 @@ def lib():
         L.minnorm_plan_export_params.argtypes = [p] * 9
         L.minnorm_sketch.argtypes = [p, p, i64]
         L.minnorm_solve.argtypes = [p, p, i64, p, d, p, C.POINTER(Info)]
+        L.minnorm_solve_wait.argtypes = [p, C.POINTER(Info)]
+        L.minnorm_plan_set_wait_limit.argtypes = [p, u64, i32]
         L.minnorm_solve_host.argtypes = [p, p, i64, p, d, p, C.POINTER(Info)]
         L.minnorm_solve_many.argtypes = [p, p, i64, p, i64, i64, d, p, i64, C.POINTER(Info)]
         L.minnorm_batch_create.argtypes = [C.POINTER(p), i32, C.POINTER(i64), C.POINTER(i64), C.c_int, C.c_int,
@@ -161,6 +163,19 @@ def minnorm_solve(plan, A, b, eps, x, lda=None, info=True, allow=(OK,)):
     st = lib().minnorm_solve(plan, _ptr(A), int(lda), _ptr(b), float(eps), _ptr(x),
                              C.byref(inf) if inf is not None else None)
     _check(st, "minnorm_solve", allow)
+    return st, (inf.as_dict() if inf is not None else None)
+
+
+def minnorm_plan_set_wait_limit(plan, limit_ns, withhold=0):
+    return _check(lib().minnorm_plan_set_wait_limit(plan, int(limit_ns), int(withhold)),
+                  "minnorm_plan_set_wait_limit")
+
+
+def minnorm_solve_wait(plan, info=True, allow=(OK,)):
+    """Status (and info) of the plan's last asynchronous minnorm_solve (minnorm_solve(..., info=False))."""
+    inf = Info() if info else None
+    st = lib().minnorm_solve_wait(plan, C.byref(inf) if inf is not None else None)
+    _check(st, "minnorm_solve_wait", allow)
     return st, (inf.as_dict() if inf is not None else None)
 
 
