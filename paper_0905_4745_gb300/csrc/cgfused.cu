@@ -551,9 +551,20 @@ cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st) {
   const double stage_bytes = (double)P.nbox * kBoxRows * 128;
   const double frac = a.keep_frac >= 0.0 ? a.keep_frac : 0.8;
   P.keep = (int)(frac * (double)l2 / ((double)G * stage_bytes));
-  void *args[] = {(void *)&map, (void *)&P};
+  // a cooperative launch (every CTA resident: the grid barriers need it), made through
+  // cudaLaunchKernelEx so that it can also be captured into a CUDA graph
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kCgThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   note_launch();
-  return cudaLaunchCooperativeKernel((const void *)cg_fused_kernel, dim3(G), dim3(kCgThreads), args, smem, st);
+  return cudaLaunchKernelEx(&cfg, cg_fused_kernel, map, P);
 }
 
 }  // namespace mn

@@ -168,6 +168,16 @@ struct minnorm_plan_s {
   // withholds its arrival at the grid barrier
   uint64_t wait_limit_ns = kBarrierLimitNs;
   int withhold = 0;
+  // the asynchronous solve's CUDA graph (captured on st_cap for one (A, b, x, lda); the
+  // certificate's constants are read from d_cc, written before each launch)
+  cudaGraphExec_t ga_exec = nullptr;
+  const void *ga_A = nullptr, *ga_b = nullptr;
+  void *ga_x = nullptr;
+  int64_t ga_lda = 0;
+  int ga_withhold = 0;
+  cudaStream_t st_cap = nullptr, st_cap2 = nullptr;
+  CertConsts *d_cc = nullptr;
+  bool capturing = false;
   cudaEvent_t ev_as0 = nullptr, ev_as1 = nullptr;
   // timing
   std::vector<KernelTimer> timers;
@@ -249,7 +259,7 @@ struct Timed {
   int cls;
   cudaEvent_t b{};
   bool on;
-  Timed(minnorm_plan_t p, int c) : plan(p), cls(c), on((p->flags & MINNORM_FLAG_TIMING) != 0) {
+  Timed(minnorm_plan_t p, int c) : plan(p), cls(c), on((p->flags & MINNORM_FLAG_TIMING) != 0 && !p->capturing) {
     if (on) {
       cudaEvent_t a = next_event(plan);
       b = next_event(plan);
@@ -596,6 +606,7 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
   if (cudaMallocHost(&plan->h_cg, sizeof(CgScalars)) != cudaSuccess) return MINNORM_ENOMEM;
   if (cudaMallocHost(&plan->h_ss, sizeof(SolveState)) != cudaSuccess) return MINNORM_ENOMEM;
   ALLOC(plan->d_ss, sizeof(SolveState));
+  ALLOC(plan->d_cc, sizeof(CertConsts));
   if (cudaMallocHost(&plan->h_qr, sizeof(double) * 6) != cudaSuccess) return MINNORM_ENOMEM;
   draw_srft_params(seed, n, l, plan->P);
   return upload_params(plan);
@@ -894,6 +905,8 @@ minnorm_status tune_cg_keep(minnorm_plan_t plan, CgFusedArgs a) {
 
 // ---- Steps 3-5 --------------------------------------------------------------
 // Inner solve: CG on (Wp^* A A^* Wp) du = g, Wp = P R^{-1}; dy = Wp du.
+minnorm_status enqueue_cg_iters(minnorm_plan_t plan, const void *Acg, double tol, int k);
+
 minnorm_status inner_cg(minnorm_plan_t plan, const void *Acg, double tol, int maxit, int *iters) {
   cudaStream_t st = plan->st;
   const int m = (int)plan->m;
@@ -947,26 +960,13 @@ minnorm_status inner_cg(minnorm_plan_t plan, const void *Acg, double tol, int ma
     plan->fused_iters += *iters;
     return MINNORM_OK;
   }
-  const int *done = &plan->d_cg->done;
   CK(launch_cg_init(m, plan->d_g, plan->d_u, plan->d_s, plan->d_p, plan->d_cg, st));
   const int chunk = plan->fp32 ? 4 : 8;
   int it = 0;
   while (it < maxit) {
     const int todo = std::min(chunk, maxit - it);
-    for (int k = 0; k < todo; ++k) {
-      if (plan->fp32) {
-        CK(launch_small_gemv(plan->d_Wp, m, plan->d_p, plan->d_w, plan->d_w32, done, st));
-        { Timed tm(plan, 0); CK(launch_gemv_adj_f32(plan->g_cg, Acg, plan->d_w32, plan->d_q, plan->d_part, plan->d_qq, done, st)); }
-        { Timed tm(plan, 1); CK(launch_gemv_fwd_f32(plan->g_cg, Acg, plan->d_q, plan->d_t, plan->d_part, done, st)); }
-      } else {
-        CK(launch_small_gemv(plan->d_Wp, m, plan->d_p, plan->d_w, nullptr, done, st));
-        { Timed tm(plan, 0); CK(launch_gemv_adj(plan->g_cg, Acg, plan->d_w, plan->d_q, plan->d_part, plan->d_qq, done, st)); }
-        { Timed tm(plan, 1); CK(launch_gemv_fwd(plan->g_cg, Acg, plan->d_q, plan->d_t, plan->d_part, done, st)); }
-      }
-      CK(launch_small_gemv(plan->d_WpH, m, plan->d_t, plan->d_np, nullptr, done, st));
-      CK(launch_cg_update(m, plan->d_qq, plan->nqq, plan->d_np, plan->d_u, plan->d_s, plan->d_p, plan->d_cg,
-                          tol * tol, st));
-    }
+    minnorm_status cs = enqueue_cg_iters(plan, Acg, tol, todo);
+    if (cs != MINNORM_OK) return cs;
     it += todo;
     CK(cudaMemcpyAsync(plan->h_cg, plan->d_cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1187,15 +1187,70 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
 // iterations (each kernel returns once the CG's own test has fired). Nothing is tuned here: a
 // plan that has not yet run a synchronous solve uses the default work splits. The status, the
 // step counts and the bound stay on the device until minnorm_solve_wait.
-minnorm_status solve_async(minnorm_plan_t plan, const void *A, const void *b, double eps, void *x) {
+// k iterations of the two-pass CG (each kernel returns once the CG's test has fired)
+minnorm_status enqueue_cg_iters(minnorm_plan_t plan, const void *Acg, double tol, int k) {
+  cudaStream_t st = plan->st;
+  const int *done = &plan->d_cg->done;
+  const int mi = (int)plan->m;
+  for (int i = 0; i < k; ++i) {
+    if (plan->fp32) {
+      CK(launch_small_gemv(plan->d_Wp, mi, plan->d_p, plan->d_w, plan->d_w32, done, st));
+      { Timed tm(plan, 0); CK(launch_gemv_adj_f32(plan->g_cg, Acg, plan->d_w32, plan->d_q, plan->d_part, plan->d_qq, done, st)); }
+      { Timed tm(plan, 1); CK(launch_gemv_fwd_f32(plan->g_cg, Acg, plan->d_q, plan->d_t, plan->d_part, done, st)); }
+    } else {
+      CK(launch_small_gemv(plan->d_Wp, mi, plan->d_p, plan->d_w, nullptr, done, st));
+      { Timed tm(plan, 0); CK(launch_gemv_adj(plan->g_cg, Acg, plan->d_w, plan->d_q, plan->d_part, plan->d_qq, done, st)); }
+      { Timed tm(plan, 1); CK(launch_gemv_fwd(plan->g_cg, Acg, plan->d_q, plan->d_t, plan->d_part, done, st)); }
+    }
+    CK(launch_small_gemv(plan->d_WpH, mi, plan->d_t, plan->d_np, nullptr, done, st));
+    CK(launch_cg_update(mi, plan->d_qq, plan->nqq, plan->d_np, plan->d_u, plan->d_s, plan->d_p, plan->d_cg, tol * tol,
+                        st));
+  }
+  return MINNORM_OK;
+}
+
+// Inside the capture of the asynchronous solve: the two-pass CG's iterations as a WHILE node of
+// the graph whose body is a chunk of kAsyncChunk iterations followed by a kernel that sets the
+// node's condition (cleared once the CG's test has fired or maxit iterations have run; maxit is
+// a multiple of the chunk, so the cap is the synchronous form's). The graph holds one copy of the
+// chunk however many iterations run.
+constexpr int kAsyncChunk = 4;
+minnorm_status capture_cg_while(minnorm_plan_t plan, const void *Acg, double tol, int maxit) {
+  cudaStream_t st = plan->st;
+  if (!plan->st_cap2) CK(cudaStreamCreateWithFlags(&plan->st_cap2, cudaStreamNonBlocking));
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *edges = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &edges, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return MINNORM_ECUDA;
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, edges, nd, &cp));
+  CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(plan->st_cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  plan->st = plan->st_cap2;
+  minnorm_status s = enqueue_cg_iters(plan, Acg, tol, kAsyncChunk);
+  if (s == MINNORM_OK && launch_cg_continue(h, plan->d_cg, maxit, plan->st_cap2) != cudaSuccess) s = MINNORM_ECUDA;
+  plan->st = st;
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(plan->st_cap2, &out);
+  if (s != MINNORM_OK) return s;
+  CK(e);
+  return MINNORM_OK;
+}
+
+minnorm_status solve_async_body(minnorm_plan_t plan, const void *A, const void *b, void *x) {
   cudaStream_t st = plan->st;
   const int64_t m = plan->m, n = plan->n;
-  const bool timing = plan->flags & MINNORM_FLAG_TIMING;
-  if (!plan->ev_as0) {
-    CK(cudaEventCreate(&plan->ev_as0));
-    CK(cudaEventCreate(&plan->ev_as1));
-  }
-  if (timing) CK(cudaEventRecord(plan->ev_as0, st));
   const void *Acg = plan->d_A32 ? (const void *)plan->d_A32 : A;
   const int *skip = &plan->d_ss->done;
   CK(cudaMemsetAsync(plan->d_yh, 0, sizeof(zd) * m, st));
@@ -1205,7 +1260,7 @@ minnorm_status solve_async(minnorm_plan_t plan, const void *A, const void *b, do
   CK(cudaMemcpyAsync(plan->d_r, b, sizeof(zd) * m, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
   CK(launch_solve_state_init(plan->d_ss, st));
-  const CertConsts cc{plan->cert_delta, 1.0 + plan->inv_eta + 4.0 * (double)m * 0x1.0p-53, eps};
+  const CertConsts *cc = plan->d_cc;
   const double tol_inner = plan->fp32 ? 1e-3 : 1e-11;
   const int maxit = plan->fp32 ? 40 : 300;
   const bool fused = plan->fused_ok && cg_fused_supported(plan->m, plan->n, plan->g_cg.ld, Acg);
@@ -1248,23 +1303,10 @@ minnorm_status solve_async(minnorm_plan_t plan, const void *A, const void *b, do
       Timed tm(plan, 5);
       CK(launch_cg_fused(a, st));
     } else {
-      const int *done = &plan->d_cg->done;
       const int mi = (int)m;
       CK(launch_cg_init(mi, plan->d_g, plan->d_u, plan->d_s, plan->d_p, plan->d_cg, st, skip));
-      for (int k = 0; k < maxit; ++k) {
-        if (plan->fp32) {
-          CK(launch_small_gemv(plan->d_Wp, mi, plan->d_p, plan->d_w, plan->d_w32, done, st));
-          { Timed tm(plan, 0); CK(launch_gemv_adj_f32(plan->g_cg, Acg, plan->d_w32, plan->d_q, plan->d_part, plan->d_qq, done, st)); }
-          { Timed tm(plan, 1); CK(launch_gemv_fwd_f32(plan->g_cg, Acg, plan->d_q, plan->d_t, plan->d_part, done, st)); }
-        } else {
-          CK(launch_small_gemv(plan->d_Wp, mi, plan->d_p, plan->d_w, nullptr, done, st));
-          { Timed tm(plan, 0); CK(launch_gemv_adj(plan->g_cg, Acg, plan->d_w, plan->d_q, plan->d_part, plan->d_qq, done, st)); }
-          { Timed tm(plan, 1); CK(launch_gemv_fwd(plan->g_cg, Acg, plan->d_q, plan->d_t, plan->d_part, done, st)); }
-        }
-        CK(launch_small_gemv(plan->d_WpH, mi, plan->d_t, plan->d_np, nullptr, done, st));
-        CK(launch_cg_update(mi, plan->d_qq, plan->nqq, plan->d_np, plan->d_u, plan->d_s, plan->d_p, plan->d_cg,
-                            tol_inner * tol_inner, st));
-      }
+      minnorm_status ws = capture_cg_while(plan, Acg, tol_inner, maxit);
+      if (ws != MINNORM_OK) return ws;
       CK(launch_small_gemv(plan->d_Wp, mi, plan->d_u, plan->d_dy, nullptr, skip, st));
     }
     CK(launch_dd_accumulate(m, plan->d_yh, plan->d_yl, plan->d_dy, st, skip));
@@ -1275,10 +1317,70 @@ minnorm_status solve_async(minnorm_plan_t plan, const void *A, const void *b, do
     }
   }
   CK(cudaMemcpyAsync(x, plan->d_xh, sizeof(zd) * n, cudaMemcpyDeviceToDevice, st));
-  if (timing) CK(cudaEventRecord(plan->ev_as1, st));
   // ||r||^2 and ||b||^2 for the report, kept on the device
   CK(launch_sumsq(m, plan->d_r, plan->d_red, plan->d_norms + 2, st));
   CK(launch_sumsq(m, (const zd *)b, plan->d_red + 1024, plan->d_norms + 3, st));
+  return MINNORM_OK;
+}
+
+// The loop above holds up to a few thousand kernels (the two-pass CG enqueues its iterations),
+// more than a stream's launch queue takes without blocking the host, so it is captured once into
+// a CUDA graph (on a private stream: the plan's may be the legacy default stream) and each
+// asynchronous solve is one graph launch. The graph is kept for the plan's (A, b, x, lda) and
+// captured again when they change; everything else it reads (the factors, the certificate's
+// constants in d_cc, eps) is read from device memory at run time.
+minnorm_status solve_async(minnorm_plan_t plan, const void *A, int64_t lda, const void *b, double eps, void *x) {
+  const bool timing = plan->flags & MINNORM_FLAG_TIMING;
+  if (!plan->ev_as0) {
+    CK(cudaEventCreate(&plan->ev_as0));
+    CK(cudaEventCreate(&plan->ev_as1));
+  }
+  if (!plan->st_cap) CK(cudaStreamCreateWithFlags(&plan->st_cap, cudaStreamNonBlocking));
+  const bool same = plan->ga_exec && plan->ga_A == A && plan->ga_b == b && plan->ga_x == x && plan->ga_lda == lda &&
+                    plan->withhold == 0 && plan->ga_withhold == 0;
+  if (!same) {
+    if (plan->ga_exec) {
+      cudaGraphExecDestroy(plan->ga_exec);
+      plan->ga_exec = nullptr;
+    }
+    cudaStream_t keep = plan->st;
+    plan->st = plan->st_cap;
+    plan->capturing = true;
+    plan->ga_withhold = plan->withhold;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(plan->st_cap, cudaStreamCaptureModeThreadLocal);
+    minnorm_status bs = MINNORM_OK;
+    if (e == cudaSuccess) {
+      bs = solve_async_body(plan, A, b, x);
+      e = cudaStreamEndCapture(plan->st_cap, &g);
+    }
+    plan->st = keep;
+    plan->capturing = false;
+    if (bs != MINNORM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return bs;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->ga_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      plan->ga_exec = nullptr;
+      plan->failed = true;
+      return MINNORM_ECUDA;
+    }
+    plan->ga_A = A;
+    plan->ga_b = b;
+    plan->ga_x = x;
+    plan->ga_lda = lda;
+  }
+  cudaStream_t st = plan->st;
+  // the certificate's constants for this sketch and eps (as kernel arguments: nothing on the
+  // host has to outlive the call, and no pageable copy waits for the stream)
+  const CertConsts cc{plan->cert_delta, 1.0 + plan->inv_eta + 4.0 * (double)plan->m * 0x1.0p-53, eps};
+  CK(launch_set_cert(plan->d_cc, cc, st));
+  if (timing) CK(cudaEventRecord(plan->ev_as0, st));
+  note_launch();
+  CK(cudaGraphLaunch(plan->ga_exec, st));
+  if (timing) CK(cudaEventRecord(plan->ev_as1, st));
   plan->async_pending = true;
   return MINNORM_OK;
 }
@@ -1628,7 +1730,7 @@ minnorm_status minnorm_solve(minnorm_plan_t plan, const void *A, int64_t lda, co
   plan->g_hp.ld = lda;
   plan->g_cg.ld = plan->d_A32 ? plan->n : lda;
   plan->async_pending = false;
-  if (!info) return solve_async(plan, A, b, eps, x);
+  if (!info) return solve_async(plan, A, lda, b, eps, x);
   return solve_impl(plan, A, lda, b, eps, x, info);
 }
 
@@ -1763,6 +1865,9 @@ minnorm_status minnorm_plan_destroy(minnorm_plan_t plan) {
   if (plan->h_cg) cudaFreeHost(plan->h_cg);
   if (plan->h_ss) cudaFreeHost(plan->h_ss);
   if (plan->ev_as0) cudaEventDestroy(plan->ev_as0);
+  if (plan->ga_exec) cudaGraphExecDestroy(plan->ga_exec);
+  if (plan->st_cap) cudaStreamDestroy(plan->st_cap);
+  if (plan->st_cap2) cudaStreamDestroy(plan->st_cap2);
   if (plan->ev_as1) cudaEventDestroy(plan->ev_as1);
   if (plan->h_qr) cudaFreeHost(plan->h_qr);
   if (plan->h_bpart) cudaFreeHost(plan->h_bpart);

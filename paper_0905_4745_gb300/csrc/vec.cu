@@ -162,8 +162,9 @@ __global__ void solve_state_init_kernel(SolveState *ss) {
 // The same stopping rule as the host loop of a synchronous solve: stop with OK once the
 // certified bound ||g|| factor / ((1 - delta) ||x||) + 2^-52 is within eps, with EFLOOR after two
 // steps in a row that did not halve it, with ENOCONV after the last step.
-__global__ void solve_stop_kernel(SolveState *ss, const double *norms, int outer, int final, CertConsts c,
+__global__ void solve_stop_kernel(SolveState *ss, const double *norms, int outer, int final, const CertConsts *cp,
                                   const CgScalars *sc) {
+  const CertConsts c = *cp;
   if (ss->done) return;
   if (sc && outer > 0) ss->cg_total += sc->iters;
   const double gn = sqrt(norms[0]);
@@ -183,13 +184,31 @@ __global__ void solve_stop_kernel(SolveState *ss, const double *norms, int outer
   if (ss->stagnant >= 2) { ss->done = 1; ss->status = 7; }  // EFLOOR
 }
 
+__global__ void set_cert_kernel(CertConsts *dst, CertConsts c) { *dst = c; }
+
+__global__ void cg_continue_kernel(cudaGraphConditionalHandle h, const CgScalars *sc, int maxit) {
+  cudaGraphSetConditional(h, (sc->done || sc->iters >= maxit) ? 0u : 1u);
+}
+
+cudaError_t launch_set_cert(CertConsts *dst, CertConsts c, cudaStream_t st) {
+  note_launch();
+  set_cert_kernel<<<1, 1, 0, st>>>(dst, c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_continue(cudaGraphConditionalHandle h, const CgScalars *sc, int maxit, cudaStream_t st) {
+  note_launch();
+  cg_continue_kernel<<<1, 1, 0, st>>>(h, sc, maxit);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_solve_state_init(SolveState *ss, cudaStream_t st) {
   note_launch();
   solve_state_init_kernel<<<1, 1, 0, st>>>(ss);
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve_stop(SolveState *ss, const double *norms, int outer, bool final, CertConsts c,
+cudaError_t launch_solve_stop(SolveState *ss, const double *norms, int outer, bool final, const CertConsts *c,
                               const CgScalars *sc, cudaStream_t st) {
   note_launch();
   solve_stop_kernel<<<1, 1, 0, st>>>(ss, norms, outer, final ? 1 : 0, c, sc);

@@ -36,10 +36,15 @@ struct CertConsts {
 cudaError_t launch_cg_init(int m, const void *g, void *u, void *s, void *p, CgScalars *sc, cudaStream_t st,
                            const int *skip = nullptr);
 cudaError_t launch_solve_state_init(SolveState *ss, cudaStream_t st);
+// *dst = c (by a kernel: no host buffer has to outlive the call)
+cudaError_t launch_set_cert(CertConsts *dst, CertConsts c, cudaStream_t st);
+// the condition of a CUDA graph's WHILE node around a chunk of CG iterations: keep looping
+// while the CG has neither met its test nor run maxit iterations
+cudaError_t launch_cg_continue(cudaGraphConditionalHandle h, const CgScalars *sc, int maxit, cudaStream_t st);
 // the refinement's stopping test on the device: norms[0] = ||g||^2, norms[1] = ||x||^2; step
 // `outer` (0: before any inner solve); final: the loop's last test (ENOCONV unless within eps);
-// sc: the CG scalars of the inner solve just finished (or NULL)
-cudaError_t launch_solve_stop(SolveState *ss, const double *norms, int outer, bool final, CertConsts c,
+// sc: the CG scalars of the inner solve just finished (or NULL); c: device copy of the constants
+cudaError_t launch_solve_stop(SolveState *ss, const double *norms, int outer, bool final, const CertConsts *c,
                               const CgScalars *sc, cudaStream_t st);
 cudaError_t launch_cg_update(int m, const double *qq, int nqq, const void *np, void *u, void *s, void *p,
                              CgScalars *sc, double tol2, cudaStream_t st);
