@@ -321,6 +321,18 @@ minnorm_status minnorm_residual_dd(minnorm_plan_t plan, const void *A, int64_t l
                                    const void *y_hi, const void *y_lo, const void *b,
                                    void *r, void *x_hi, void *x_lo);
 
+/* The trailing-update products of Step 2's blocked Householder QR, on the
+ * tensor cores with FP64 accuracy (exact BF16 slicing of both operands, the
+ * leading levels accumulated exactly; as accurate as an FP64 dot product):
+ *   W = V^H C      (when W is not NULL: W device, 32 x cols, column-major, ld 32)
+ *   C = C - V Z    (when Z is not NULL, after W: Z device, 32 x cols, ldz >= 32)
+ * V (device, rows x 32, ldv >= rows), C (device, rows x cols, ldc >= rows),
+ * all complex128 column-major; rows <= l and cols <= m of the plan. Allocates the
+ * plan's QR workspace on first use. Synchronizes the plan's stream.
+ * Errors: EINVAL, ESTATE, ENOMEM, ETIMEOUT, ECUDA. */
+minnorm_status minnorm_trailing_products(minnorm_plan_t plan, const void *V, int64_t ldv, void *C, int64_t ldc,
+                                         int64_t rows, int64_t cols, const void *Z, int64_t ldz, void *W);
+
 /* The schedule choices of the plan's autotuner: *x_chunks column chunks of
  * b - A x and *x_splits row splits of x = A^* y in the exact residual, and
  * *cg_l2_keep_pct, the share of L2 (percent) into which the fused CG loads the

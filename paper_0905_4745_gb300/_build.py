@@ -12,9 +12,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libminnorm.so")
-SOURCES = ["solver.cu", "sketch.cu", "qr.cu", "gemv.cu", "xprod.cu", "cgfused.cu", "blockcg.cu", "tcblock.cu", "noalloc.cu", "vec.cu",
+SOURCES = ["solver.cu", "sketch.cu", "qr.cu", "ozaki.cu", "qrblk.cu", "gemv.cu", "xprod.cu", "cgfused.cu", "blockcg.cu", "tcblock.cu", "noalloc.cu", "vec.cu",
            "params.cpp"]
-HEADERS = ["common.cuh", "dw.cuh", "kernels.h", "params.h", "vec.h"]
+HEADERS = ["common.cuh", "dw.cuh", "kernels.h", "params.h", "tc.cuh", "vec.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -173,6 +173,80 @@ struct CgFusedArgs {
 bool cg_fused_supported(int64_t m, int64_t n, int64_t lda, const void *A);
 cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st);
 
+// ---- ozaki.cu ----------------------------------------------------------------------
+// FP64-accurate complex products on the tensor cores (the trailing updates of the blocked
+// Householder QR, qrblk.cu). Every FP64 operand entry is split exactly into kOzSlices BF16
+// slices of 4-bit integers scaled by powers of two (one exponent per operand row); the pair
+// products of every slice level are accumulated EXACTLY in FP32 in tensor memory (one
+// accumulator per level: their integer sums fit in 24 bits) and combined in int64.
+constexpr int kOzSlices = 13;     // 13 x 4 bits: every bit of an FP64 significand
+constexpr int kOzN = 32;          // real output columns per tile
+constexpr int kOzM = 128;         // output rows per tile
+constexpr int kOzK = 64;          // K per block (one 128-byte row of BF16)
+constexpr int kOzKMax = 4096;     // real K per CTA: 13 x 225 x 4096 < 2^24 (every level exact)
+// Operand slices: [kOzSlices][rows_pad][k_pad] BF16, K contiguous (rows_pad a multiple of 128,
+// k_pad of 64, zero padded), with one int32 exponent per row.
+struct OzOperand {
+  void *slices;
+  int32_t *expo;
+  int64_t rows, rows_pad, k, k_pad;
+};
+size_t oz_slice_bytes(int64_t rows, int64_t k);
+// A rows from C's columns: row c = (Re C[r, c], Im C[r, c]) for r = 0..rows-1 interleaved along K
+cudaError_t launch_oz_slice_cols(const void *C, int64_t ldc, int64_t rows, int64_t cols, OzOperand &out,
+                                 cudaStream_t st);
+// B rows from the 32 reflectors V (rows x 32, column-major, ldv): row j < 32 = (Re V[:, j], Im V[:, j])
+// interleaved; row 32 + j = (Im V[:, j], -Re V[:, j])
+cudaError_t launch_oz_slice_v_adj(const void *V, int64_t ldv, int64_t rows, OzOperand &out, cudaStream_t st);
+// A rows for C -= V Z: row 2i = (Re V[i, j], -Im V[i, j]), row 2i + 1 = (Im V[i, j], Re V[i, j]) along j
+cudaError_t launch_oz_slice_v_fwd(const void *V, int64_t ldv, int64_t rows, OzOperand &out, cudaStream_t st);
+// B rows for C -= V Z: row c = (Re Z[j, c], Im Z[j, c]) along j (Z: 32 x cols complex, column-major, ldz)
+cudaError_t launch_oz_slice_z(const void *Z, int64_t ldz, int64_t cols, OzOperand &out, cudaStream_t st);
+// W^H = C^H V (the adjoint product): D[c][j] (cols x 64 real: Re then Im of (C^H V)[c, j]) into
+// FP64 partial sums over K splits, then W[j, c] = conj(...) (32 x cols complex, column-major, ldw)
+struct OzAdjArgs {
+  OzOperand a, b;
+  double *part;           // splits x cols_pad x 64
+  size_t part_bytes;      // its capacity (oz_adj_partial_bytes)
+  void *W;
+  int64_t ldw, cols;
+  int *err;
+  uint64_t limit_ns;
+};
+cudaError_t launch_oz_adj(const OzAdjArgs &a, cudaStream_t st);
+size_t oz_adj_partial_bytes(int64_t l, int64_t m, int sms);
+// C[i, c] -= (V Z)[i, c] for i < rows, c < cols (C complex column-major, ldc)
+struct OzFwdArgs {
+  OzOperand a, b;
+  void *C;
+  int64_t ldc, rows, cols;
+  int *err;
+  uint64_t limit_ns;
+};
+cudaError_t launch_oz_fwd(const OzFwdArgs &a, cudaStream_t st);
+
+// ---- qrblk.cu ----------------------------------------------------------------------
+// Workspace of the blocked Householder QR (sizes for l x m sketches): the operand slices and
+// exponents of both trailing products, their FP64 partial sums, W = V^H C and Z = T^H W.
+struct QrBlkWork {
+  int64_t l = 0, m = 0;
+  void *sA = nullptr, *sB = nullptr, *sV = nullptr, *sZ = nullptr;
+  int32_t *eA = nullptr, *eB = nullptr, *eV = nullptr, *eZ = nullptr;
+  double *part = nullptr;
+  size_t part_bytes = 0;
+  void *W = nullptr, *Z = nullptr, *T = nullptr;   // 32 x m, 32 x m, 32 x 32 complex, column-major
+  double *tau = nullptr;                           // 2 per panel column: tau (complex)
+  double *red = nullptr;                           // panel reduction scratch
+};
+// bytes of each buffer, in the order of the struct (for one allocation per buffer)
+void qrblk_sizes(int64_t l, int64_t m, int sms, size_t (&bytes)[13]);
+// W = V^H C (when W is set; 32 x cols, ldw 32) and then C -= V Z (when Z is set; Z 32 x cols,
+// column-major, ldz): V rows x 32 (ldv), C rows x cols (ldc), all complex FP64 column-major;
+// rows <= l, cols <= m of the workspace
+cudaError_t launch_trailing_products(QrBlkWork &w, const void *V, int64_t ldv, void *C, int64_t ldc, int64_t rows,
+                                     int64_t cols, const void *Z, int64_t ldz, void *W, int *err, uint64_t limit_ns,
+                                     cudaStream_t st);
+
 // ---- blockcg.cu -------------------------------------------------------------------
 // block CG over kBlockRhs right-hand sides (block vectors row-major m x kBlockRhs)
 constexpr int kBlockRhs = 32;

@@ -178,6 +178,9 @@ struct minnorm_plan_s {
   cudaStream_t st_cap = nullptr, st_cap2 = nullptr;
   CertConsts *d_cc = nullptr;
   bool capturing = false;
+  // blocked QR of the sketch (allocated on first use)
+  QrBlkWork qb;
+  bool qb_ready = false;
   cudaEvent_t ev_as0 = nullptr, ev_as1 = nullptr;
   // timing
   std::vector<KernelTimer> timers;
@@ -1385,6 +1388,32 @@ minnorm_status solve_async(minnorm_plan_t plan, const void *A, int64_t lda, cons
   return MINNORM_OK;
 }
 
+// workspace of the blocked QR (qrblk.cu), allocated on first use
+minnorm_status qrblk_alloc(minnorm_plan_t plan) {
+  if (plan->qb_ready) return MINNORM_OK;
+  size_t b[13];
+  qrblk_sizes(plan->l, plan->m, plan->sms, b);
+  QrBlkWork &w = plan->qb;
+  w.l = plan->l;
+  w.m = plan->m;
+  ALLOC(w.sA, b[0]);
+  ALLOC(w.sB, b[1]);
+  ALLOC(w.sV, b[2]);
+  ALLOC(w.sZ, b[3]);
+  ALLOC(w.eA, b[4]);
+  ALLOC(w.eB, b[5]);
+  ALLOC(w.eV, b[6]);
+  ALLOC(w.eZ, b[7]);
+  ALLOC(w.part, b[8]);
+  w.part_bytes = b[8];
+  ALLOC(w.W, b[9]);
+  ALLOC(w.Z, b[10]);
+  ALLOC(w.T, b[11]);
+  ALLOC(w.tau, b[12]);
+  plan->qb_ready = true;
+  return MINNORM_OK;
+}
+
 // argument checks of minnorm_plan_create (no device access)
 minnorm_status check_plan_args(int64_t m, int64_t n, int64_t &l, minnorm_dtype dtype, minnorm_precision prec,
                                uint32_t flags) {
@@ -1732,6 +1761,27 @@ minnorm_status minnorm_solve(minnorm_plan_t plan, const void *A, int64_t lda, co
   plan->async_pending = false;
   if (!info) return solve_async(plan, A, lda, b, eps, x);
   return solve_impl(plan, A, lda, b, eps, x, info);
+}
+
+minnorm_status minnorm_trailing_products(minnorm_plan_t plan, const void *V, int64_t ldv, void *C, int64_t ldc,
+                                         int64_t rows, int64_t cols, const void *Z, int64_t ldz, void *W) {
+  if (!plan || !V || !C) return MINNORM_EINVAL;
+  if (plan->failed) return MINNORM_ESTATE;
+  if (rows < 1 || cols < 1 || rows > plan->l || cols > plan->m || ldv < rows || ldc < rows || (Z && ldz < 32))
+    return MINNORM_EINVAL;
+  minnorm_status s = qrblk_alloc(plan);
+  if (s != MINNORM_OK) return s;
+  cudaStream_t st = plan->st;
+  CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
+  CK(launch_trailing_products(plan->qb, V, ldv, C, ldc, rows, cols, Z, ldz, W, plan->d_err, plan->wait_limit_ns, st));
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (err) {
+    plan->failed = true;
+    return MINNORM_ETIMEOUT;
+  }
+  return MINNORM_OK;
 }
 
 minnorm_status minnorm_plan_set_wait_limit(minnorm_plan_t plan, uint64_t limit_ns, int32_t withhold) {

@@ -20,7 +20,7 @@ FP64, MIXED = 0, 1
 FLAG_TIMING, FLAG_KEEP_SKETCH = 1, 2
 
 # every symbol include/minnorm.h declares
-EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_plan_export_params", "minnorm_sketch", "minnorm_solve", "minnorm_solve_wait", "minnorm_plan_set_wait_limit",
+EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_plan_export_params", "minnorm_sketch", "minnorm_solve", "minnorm_solve_wait", "minnorm_plan_set_wait_limit", "minnorm_trailing_products",
            "minnorm_solve_host", "minnorm_plan_destroy", "minnorm_status_string", "minnorm_get_sketch",
            "minnorm_get_factor", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats",
            "minnorm_launch_count", "minnorm_qr_noalloc", "minnorm_solve_many", "minnorm_batch_create",
@@ -63,6 +63,7 @@ def lib():
         L.minnorm_solve.argtypes = [p, p, i64, p, d, p, C.POINTER(Info)]
         L.minnorm_solve_wait.argtypes = [p, C.POINTER(Info)]
         L.minnorm_plan_set_wait_limit.argtypes = [p, u64, i32]
+        L.minnorm_trailing_products.argtypes = [p, p, i64, p, i64, i64, i64, p, i64, p]
         L.minnorm_solve_host.argtypes = [p, p, i64, p, d, p, C.POINTER(Info)]
         L.minnorm_solve_many.argtypes = [p, p, i64, p, i64, i64, d, p, i64, C.POINTER(Info)]
         L.minnorm_batch_create.argtypes = [C.POINTER(p), i32, C.POINTER(i64), C.POINTER(i64), C.c_int, C.c_int,
@@ -169,6 +170,16 @@ def minnorm_solve(plan, A, b, eps, x, lda=None, info=True, allow=(OK,)):
 def minnorm_plan_set_wait_limit(plan, limit_ns, withhold=0):
     return _check(lib().minnorm_plan_set_wait_limit(plan, int(limit_ns), int(withhold)),
                   "minnorm_plan_set_wait_limit")
+
+
+def minnorm_trailing_products(plan, V, C, Z=None, W=None):
+    """W = V^H C, then C -= V Z (complex128 column-major device tensors: V rows x 32, C rows x cols,
+    Z 32 x cols, W 32 x cols; pass the transposed-contiguous views, e.g. X.T.contiguous().T)."""
+    rows, cols = C.shape
+    return _check(lib().minnorm_trailing_products(plan, _ptr(V), int(V.stride(1)), _ptr(C), int(C.stride(1)),
+                                                  int(rows), int(cols), _ptr(Z),
+                                                  int(Z.stride(1)) if Z is not None else 0, _ptr(W)),
+                  "minnorm_trailing_products")
 
 
 def minnorm_solve_wait(plan, info=True, allow=(OK,)):
