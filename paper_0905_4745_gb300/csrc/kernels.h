@@ -179,11 +179,11 @@ cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st);
 // slices of 4-bit integers scaled by powers of two (one exponent per operand row); the pair
 // products of every slice level are accumulated EXACTLY in FP32 in tensor memory (one
 // accumulator per level: their integer sums fit in 24 bits) and combined in int64.
-constexpr int kOzSlices = 13;     // 13 x 4 bits: every bit of an FP64 significand
+constexpr int kOzSlices = 14;     // 14 x 4 bits: 56 bits below each row's scale
 constexpr int kOzN = 32;          // real output columns per tile
 constexpr int kOzM = 128;         // output rows per tile
 constexpr int kOzK = 64;          // K per block (one 128-byte row of BF16)
-constexpr int kOzKMax = 4096;     // real K per CTA: 13 x 225 x 4096 < 2^24 (every level exact)
+constexpr int kOzKMax = 4096;     // real K per CTA: 14 x 225 x 4096 < 2^24 (every level exact)
 // Operand slices: [kOzSlices][rows_pad][k_pad] BF16, K contiguous (rows_pad a multiple of 128,
 // k_pad of 64, zero padded), with one int32 exponent per row.
 struct OzOperand {
@@ -235,11 +235,19 @@ struct QrBlkWork {
   double *part = nullptr;
   size_t part_bytes = 0;
   void *W = nullptr, *Z = nullptr, *T = nullptr;   // 32 x m, 32 x m, 32 x 32 complex, column-major
-  double *tau = nullptr;                           // 2 per panel column: tau (complex)
-  double *red = nullptr;                           // panel reduction scratch
+  void *tau = nullptr;                             // m complex: the reflectors' tau
+  void *Vb = nullptr;                              // l x 32 complex: a panel's reflectors (unit diagonal)
+  void *R1 = nullptr;                              // m x m complex: the triangle of the unpivoted QR
+  void *dpart = nullptr;                           // sms x 32 complex: panel partial sums
+  double *npart = nullptr;                         // sms: panel partial norms
+  GridBarrier *bar = nullptr;
 };
-// bytes of each buffer, in the order of the struct (for one allocation per buffer)
-void qrblk_sizes(int64_t l, int64_t m, int sms, size_t (&bytes)[13]);
+// bytes of each buffer: sA, sB, sV, sZ, eA, eB, eV, eZ, part, W, Z, T, tau, Vb, R1, dpart, npart, bar
+void qrblk_sizes(int64_t l, int64_t m, int sms, size_t (&bytes)[18]);
+// Y P = Q R (Step 2) for l x m sketches, l >= m: blocked unpivoted QR, then the pivoted QR of
+// its m x m triangle (launch_qrp with the arguments of q); the pivots and R are those of the
+// pivoted QR of Y (R up to a unit diagonal)
+cudaError_t launch_qr_blocked(QrBlkWork &w, const QrArgs &q, int sms, cudaStream_t st);
 // W = V^H C (when W is set; 32 x cols, ldw 32) and then C -= V Z (when Z is set; Z 32 x cols,
 // column-major, ldz): V rows x 32 (ldv), C rows x cols (ldc), all complex FP64 column-major;
 // rows <= l, cols <= m of the workspace

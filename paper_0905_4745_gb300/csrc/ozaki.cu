@@ -8,23 +8,24 @@
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication and its applications", Numer. Algorithms 59, 2012), with
 // integer slices: every entry x of an operand row with exponent e (all of the
-// row's entries below 2^e in magnitude) is written exactly (to 2^-52 of 2^e) as
-//     x = 2^e / 16 * sum_{s=0}^{12} sigma_s,   sigma_s = +-d_s 16^-s,
-// d_s in 0..15 the base-16 digits of |x| 2^(52-e), read off the FP64 bit pattern
-// with integer shifts (no FP64 instruction). Each sigma_s is exact in BF16. A
-// product of two rows is then 2^(e + f) / 256 times the sum over the levels
-// L = s + t of sum_k sigma_s sigma_t. The levels L <= 13 are kept (105 pairs;
-// the dropped ones add at most 13 * 15 16^-13 16 of 2^(e+f)/256 per term, below
-// the 52-bit truncation of the entries themselves). A level's sum is an integer
-// multiple of 16^-L whose integer part stays below 13 * 225 * 4096 < 2^24 for
+// row's entries below 2^e in magnitude) is written exactly (to 2^-56 of 2^e) as
+//     x = 2^e / 16 * sum_{s=0}^{13} sigma_s,   sigma_s = +-d_s 16^-s,
+// d_s in 0..15 the base-16 digits of |x| 2^(56-e), read off the FP64 bit pattern
+// with integer shifts (no FP64 instruction; entries within 2^3 of the row's
+// scale keep every bit). Each sigma_s is exact in BF16. A product of two rows
+// is then 2^(e + f) / 256 times the sum over the levels L = s + t of
+// sum_k sigma_s sigma_t. The levels L <= 15 are kept (130 pairs; the dropped
+// ones add at most 14 * 15 * 16^-15 of 2^(e+f)/256 per term, the order of the
+// 56-bit truncation of the entries themselves). A level's sum is an integer
+// multiple of 16^-L whose integer part stays below 14 * 225 * 4096 < 2^24 for
 // K <= 4096 per CTA, so the tensor cores' FP32 accumulation of every kept level
-// (one accumulator each, 14 x 32 columns of tensor memory) is EXACT. (A shared FP32 accumulator for the trailing levels is not enough: its
+// (one accumulator each, 16 x 32 = all 512 columns of tensor memory) is EXACT. (A shared FP32 accumulator for the trailing levels is not enough: its
 // rounding grows with the number of terms, and the tensor cores' accumulation
 // truncates.) The levels are combined exactly in two int64 halves and rounded
 // once to FP64; K splits across CTAs are added in FP64. The only other errors
 // are the truncation of each entry to 52 bits below its row's scale: the
 // product is as accurate as an FP64 dot product, at the tensor cores' BF16 rate
-// divided by the 105 slice pairs.
+// divided by the 130 slice pairs.
 //
 // Real forms of the complex products (interleaved re/im along K):
 //   adjoint: A row c = (Re C[r,c], Im C[r,c])_r, B row j < 32 = (Re V[r,j], Im V[r,j])_r,
@@ -50,8 +51,8 @@ constexpr int kOzThreads = 256;
 constexpr int kOzRing = 6;                        // A slice tiles in flight
 constexpr int kOzATile = kOzM * kOzK * 2;         // 16 KB: 128 rows x 64 BF16
 constexpr int kOzBTile = kOzN * kOzK * 2;         // 4 KB: 32 rows x 64 BF16
-constexpr int kOzKept = kOzSlices + 1;            // levels 0..13 (pairs s + t <= 13), one accumulator each
-constexpr int kOzTmemCols = 512;                  // 14 x 32 = 448 used (a power of two is allocated)
+constexpr int kOzKept = kOzSlices + 2;            // levels 0..15 (pairs s + t <= 15), one accumulator each
+constexpr int kOzTmemCols = kOzKept * kOzN;       // 512
 constexpr int kOzOffB = kOzRing * kOzATile;       // 96 KB
 constexpr int kOzOffBar = kOzOffB + kOzSlices * kOzBTile;  // 148 KB
 constexpr int kOzSmem = kOzOffBar + 512 + 1024;   // barriers + alignment slack
@@ -64,7 +65,7 @@ __device__ __forceinline__ int oz_expo_of(double x) {
   return f == 0 ? -2000 : f - 1023 + 1;
 }
 
-// the 13 signed slices sigma_s = +-d_s 16^-s of x for row exponent e, as BF16
+// the 14 signed slices sigma_s = +-d_s 16^-s of x for row exponent e, as BF16
 __device__ __forceinline__ void oz_slices(double x, int e, __nv_bfloat16 (&q)[kOzSlices]) {
   const long long b = __double_as_longlong(x);
   const int f = (int)((b >> 52) & 0x7ff);
@@ -72,7 +73,8 @@ __device__ __forceinline__ void oz_slices(double x, int e, __nv_bfloat16 (&q)[kO
   if (f != 0 && e > -2000) {
     const unsigned long long mant = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
     const int sh = e - (f - 1023);  // >= 1: |x| < 2^e
-    N = sh < 64 ? (mant >> sh) : 0ull;  // floor(|x| 2^(52 - e)), 52 bits
+    // floor(|x| 2^(56 - e)) = mant 2^(4 - sh), 56 bits
+    N = sh <= 4 ? (mant << (4 - sh)) : (sh - 4 < 64 ? (mant >> (sh - 4)) : 0ull);
   }
   const float sgn = b < 0 ? -1.0f : 1.0f;
 #pragma unroll
@@ -306,9 +308,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
     s_a_issued = ai;
     s_b_issued = bi;
   } else if (nkb > 0 && wid == 1 && lane == 0) {
-    // products: pair (s, t), s + t <= 13, into accumulator s + t (exact); the first product
-    // into an accumulator (pair (0, t), or (1, 12) for level 13, of the first K-block)
-    // overwrites it. B_t has its last pair at s = 13 - t (B_0 and B_1 at s = 12).
+    // products: pair (s, t), s + t <= 15, into accumulator s + t (exact); the first product
+    // into an accumulator (pair (0, t), or (1, 13) and (2, 13) for levels 14 and 15, of the
+    // first K-block) overwrites it. B_t has its last pair at s = 15 - t (B_0 and B_1 at s = 13).
     int ai = 0, bu = 0;
     bool ok = true;
     const uint32_t id = idesc(kOzN);
@@ -326,7 +328,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
         for (int t = 0; t < kOzSlices && s + t < kOzKept; ++t) {
           const uint32_t d = tmem + (uint32_t)((s + t) * kOzN);
           const uint32_t b0 = sa(sB + t * kOzBTile);
-          const bool first = kk == 0 && (s == 0 || (s == 1 && t == kOzSlices - 1));
+          const bool first = kk == 0 && (s == 0 || (s <= 2 && t == kOzSlices - 1));
 #pragma unroll
           for (int k16 = 0; k16 < kOzK / 16; ++k16) {
             const uint32_t accum = (first && k16 == 0) ? 0u : 1u;
@@ -334,8 +336,11 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
           }
         }
         mma_commit(&a_empty[slot]);                   // A_s read
-        if (s >= 1) mma_commit(&b_empty[kOzSlices - s]);   // B_{13 - s} has had its last pair
-        if (s == kOzSlices - 1) mma_commit(&b_empty[0]);   // and B_0 at s = 12
+        if (s >= 2) mma_commit(&b_empty[kOzKept - 1 - s]);   // B_{15 - s} has had its last pair
+        if (s == kOzSlices - 1) {                             // and B_1, B_0 at s = 13
+          mma_commit(&b_empty[1]);
+          mma_commit(&b_empty[0]);
+        }
         ++ai;
       }
     }
@@ -363,8 +368,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
       const int ga = ma * kOzM + row;                   // A row
       const int ea = P.ea[ga];
       {
-        // levels 0..6 into Ih = sum I_L 16^(6-L), levels 7..13 into Il = sum I_L 16^(13-L), each
-        // level's sum an exact integer I_L times 16^-L below 2^24 (both halves below 2^49)
+        // levels 0..7 into Ih = sum I_L 16^(7-L), levels 8..15 into Il = sum I_L 16^(15-L), each
+        // level's sum an exact integer I_L times 16^-L below 2^24 (both halves below 2^53)
         long long Ih[32], Il[32];
         float v[32];
 #pragma unroll
@@ -374,12 +379,12 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
           for (int L = 0; L < kOzKept; ++L) {
             tmem_ld32(tmem + ((uint32_t)(32 * (wid & 3)) << 16) + (uint32_t)(L * kOzN), v);
             const float up = __int_as_float((127 + 4 * L) << 23);  // 16^L
-            if (L < 7) {
+            if (L < 8) {
 #pragma unroll
-              for (int k = 0; k < 32; ++k) Ih[k] += (long long)__float2int_rn(v[k] * up) << (4 * (6 - L));
+              for (int k = 0; k < 32; ++k) Ih[k] += (long long)__float2int_rn(v[k] * up) << (4 * (7 - L));
             } else {
 #pragma unroll
-              for (int k = 0; k < 32; ++k) Il[k] += (long long)__float2int_rn(v[k] * up) << (4 * (13 - L));
+              for (int k = 0; k < 32; ++k) Il[k] += (long long)__float2int_rn(v[k] * up) << (4 * (15 - L));
             }
           }
         }
@@ -387,8 +392,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
         for (int k = 0; k < 32; ++k) {
           const int col = k;
           const int eb = P.eb[nb * kOzN + col];
-          // the levels' sum Ih 16^-6 + Il 16^-13 (one rounding), times 2^(ea + eb) / 256
-          double r = fma((double)Il[k], 0x1.0p-52, (double)Ih[k] * 0x1.0p-24);
+          // the levels' sum Ih 16^-7 + Il 16^-15 (one rounding), times 2^(ea + eb) / 256
+          double r = fma((double)Il[k], 0x1.0p-60, (double)Ih[k] * 0x1.0p-28);
           const int sc = ea + eb - 8;
           if (ea <= -2000 || eb <= -2000) r = 0.0;
           else if (sc >= -1022 && sc <= 1023) r *= __longlong_as_double((long long)(sc + 1023) << 52);  // 2^sc

@@ -11,6 +11,8 @@
 // to a unit diagonal (the sign LAPACK's reflectors give each row). The costly
 // l x m part runs as products on the tensor cores; only the m x m part is
 // factored column by column.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -18,7 +20,166 @@ namespace mn {
 
 static int64_t qpad(int64_t v, int64_t q) { return (v + q - 1) / q * q; }
 
-void qrblk_sizes(int64_t l, int64_t m, int sms, size_t (&b)[13]) {
+constexpr int kPanel = 32;           // columns per panel (the reflectors of one compact WY block)
+constexpr int kPanelThreads = 256;   // 8 warps; lane = panel column
+
+// Householder QR without pivoting of the panel P (L rows x jb <= 32 columns, column-major,
+// ld), LAPACK's zgeqr2 conventions: for column j, beta = -sign(Re alpha) ||P[j:, j]||,
+// tau = (beta - alpha) / beta, v = P[j:, j] / (alpha - beta) with v_j = 1, and H_j^H =
+// I - conj(tau) v v^H applied to the columns right of j. The CTAs own contiguous row ranges;
+// warp w takes rows r0 + w, r0 + w + 8, ..., lane c column c. Per column two grid-wide sums
+// (deterministic: every CTA adds the posted partials in the same order), both behind bounded
+// barriers: ||P[j+1:, j]||^2 (posted during the previous column's update), then in one pass
+// d_c = v^H P[:, c] for c > j and e_i = v_i^H v for the earlier reflectors i < j. CTA 0
+// builds the compact WY factor T (Schreiber and Van Loan; LAPACK's zlarft, forward and
+// columnwise): T[j, j] = tau_j, T[:j, j] = -tau_j T[:j, :j] e. Outputs: R's entries and the
+// reflectors in P (beta on the diagonal), V (L x 32, unit diagonal, zeros above; the columns
+// past jb zero), T (32 x 32, column-major), tau.
+__global__ void __launch_bounds__(kPanelThreads)
+qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ldv, zd *__restrict__ T,
+                zd *__restrict__ tau, zd *__restrict__ dpart, double *__restrict__ npart, GridBarrier *bar, int *err,
+                uint64_t limit_ns) {
+  __shared__ zd s_acc[kPanelThreads / 32][kPanel];
+  __shared__ zd s_d[kPanel];
+  __shared__ zd s_T[kPanel * kPanel];
+  __shared__ double s_n[kPanelThreads / 32];
+  __shared__ double s_scal[6];   // beta, Re/Im tau, Re/Im scale, ||x||^2
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int r0 = (int)((int64_t)L * b / G), r1 = (int)((int64_t)L * (b + 1) / G);
+  unsigned int epoch = 0;
+  // V: zero the own rows; T: zero
+  for (int r = r0 + wid; r < r1; r += 8) V[(int64_t)lane * ldv + r] = {0.0, 0.0};
+  if (b == 0)
+    for (int e = tid; e < kPanel * kPanel; e += blockDim.x) s_T[e] = {0.0, 0.0};
+  // ||P[1:, 0]||^2
+  {
+    double n = 0.0;
+    if (lane == 0)
+      for (int r = max(r0, 1) + wid; r < r1; r += 8) n += abs2(P[r]);
+    if (lane == 0) s_n[wid] = n;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kPanelThreads / 32; ++w) t += s_n[w];
+      npart[b] = t;
+    }
+  }
+  for (int j = 0; j < jb; ++j) {
+    if (!grid_sync(bar, G, epoch, limit_ns)) { if (tid == 0) atomicExch(err, 1); return; }
+    // the reflector of column j, in every CTA
+    if (tid == 0) {
+      double xn2 = 0.0;
+      for (int q = 0; q < G; ++q) xn2 += ldcg(npart + q);
+      const zd alpha = ldcg(P + (int64_t)j * ld + j);
+      double bt = alpha.re;
+      zd tj = {0.0, 0.0}, sc = {0.0, 0.0};
+      if (!(xn2 == 0.0 && alpha.im == 0.0)) {
+        const double mag = sqrt(alpha.re * alpha.re + alpha.im * alpha.im + xn2);
+        bt = alpha.re >= 0.0 ? -mag : mag;
+        tj = {(bt - alpha.re) / bt, -alpha.im / bt};
+        const double dr = alpha.re - bt, di = alpha.im, iden = 1.0 / (dr * dr + di * di);
+        sc = {dr * iden, -di * iden};   // 1 / (alpha - beta)
+      }
+      s_scal[0] = bt;
+      s_scal[1] = tj.re;
+      s_scal[2] = tj.im;
+      s_scal[3] = sc.re;
+      s_scal[4] = sc.im;
+    }
+    __syncthreads();
+    const zd scale = {s_scal[3], s_scal[4]};
+    const zd tj = {s_scal[1], s_scal[2]};
+    // v on the own rows (v_j = 1 on row j), into P and V; the partial dots
+    zd acc = {0.0, 0.0};
+    for (int r = max(r0, j) + wid; r < r1; r += 8) {
+      zd v;
+      if (r == j) v = {1.0, 0.0};
+      else v = ldcg(P + (int64_t)j * ld + r) * scale;
+      if (lane > j) {
+        if (lane < jb) macc(acc, v, ldcg(P + (int64_t)lane * ld + r));   // conj(v) P[r, c]
+      } else if (lane < j) {
+        macc(acc, ldcg(V + (int64_t)lane * ldv + r), v);                 // conj(v_i[r]) v[r]
+      } else {
+        V[(int64_t)j * ldv + r] = v;
+      }
+    }
+    s_acc[wid][lane] = acc;
+    __syncthreads();
+    if (wid == 0) {
+      zd t = {0.0, 0.0};
+      for (int w = 0; w < kPanelThreads / 32; ++w) t = t + s_acc[w][lane];
+      dpart[(int64_t)b * kPanel + lane] = t;
+    }
+    if (!grid_sync(bar, G, epoch, limit_ns)) { if (tid == 0) atomicExch(err, 1); return; }
+    if (wid == 0) {
+      zd t = {0.0, 0.0};
+      for (int q = 0; q < G; ++q) t = t + ldcg(dpart + (int64_t)q * kPanel + lane);
+      s_d[lane] = t;
+    }
+    __syncthreads();
+    // T column j (CTA 0): T[j, j] = tau_j, T[i, j] = -tau_j sum_{k=i..j-1} T[i, k] e_k
+    if (b == 0 && tid < kPanel) {
+      const int i = tid;
+      if (i < j) {
+        zd sum = {0.0, 0.0};
+        for (int k = i; k < j; ++k) mac(sum, s_T[k * kPanel + i], s_d[k]);
+        s_T[j * kPanel + i] = {-(tj.re * sum.re - tj.im * sum.im), -(tj.re * sum.im + tj.im * sum.re)};
+      } else if (i == j) {
+        s_T[j * kPanel + j] = tj;
+        tau[j] = tj;
+      }
+    }
+    // update columns c > j on the own rows r >= j (H_j^H = I - conj(tau) v v^H), beta on the
+    // diagonal, and the partial ||P[j+2:, j+1]||^2 for the next column
+    const zd f = conjg(tj) * s_d[lane];   // conj(tau) d_c
+    double n = 0.0;
+    for (int r = max(r0, j) + wid; r < r1; r += 8) {
+      if (lane > j && lane < jb) {
+        const zd v = r == j ? zd{1.0, 0.0} : ldcg(V + (int64_t)j * ldv + r);
+        zd x = ldcg(P + (int64_t)lane * ld + r);
+        x = x - f * v;
+        P[(int64_t)lane * ld + r] = x;
+        if (lane == j + 1 && r > j + 1) n += abs2(x);
+      } else if (lane == j) {
+        if (r == j) P[(int64_t)j * ld + j] = {s_scal[0], 0.0};
+        else P[(int64_t)j * ld + r] = ldcg(V + (int64_t)j * ldv + r);
+      }
+    }
+    n = warp_sum(n);
+    if (lane == 0) s_n[wid] = n;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kPanelThreads / 32; ++w) t += s_n[w];
+      npart[b] = t;
+    }
+  }
+  if (b == 0) {
+    __syncthreads();
+    for (int e = tid; e < kPanel * kPanel; e += blockDim.x) T[e] = s_T[e];
+  }
+}
+
+// Z = T^H W: Z[:, c] = T^H W[:, c], T 32 x 32 upper triangular (one thread per (row k, column c))
+__global__ void qr_tw_kernel(const zd *__restrict__ T, const zd *__restrict__ W, zd *__restrict__ Z, int64_t cols) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= cols * kPanel) return;
+  const int64_t c = e / kPanel;
+  const int k = (int)(e % kPanel);
+  zd z = {0.0, 0.0};
+  for (int i = 0; i <= k; ++i) macc(z, T[k * kPanel + i], W[c * kPanel + i]);   // conj(T[i, k]) W[i, c]
+  Z[c * kPanel + k] = z;
+}
+
+// R1 = the upper triangle of Y[0:m, 0:m] (zeros below), m x m column-major
+__global__ void qr_copy_r1_kernel(const zd *__restrict__ Y, int64_t ldy, int m, zd *__restrict__ R1) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)m * m) return;
+  const int64_t j = e / m, i = e % m;
+  R1[e] = i <= j ? Y[j * ldy + i] : zd{0.0, 0.0};
+}
+
+void qrblk_sizes(int64_t l, int64_t m, int sms, size_t (&b)[18]) {
   b[0] = oz_slice_bytes(m, 2 * l);          // sA: A rows from C's columns
   b[1] = oz_slice_bytes(kOzN, 2 * l);       // sB: the reflectors, adjoint form
   b[2] = oz_slice_bytes(2 * l, kOzK);       // sV: the reflectors, update form
@@ -32,6 +193,11 @@ void qrblk_sizes(int64_t l, int64_t m, int sms, size_t (&b)[13]) {
   b[10] = sizeof(zd) * 32 * (size_t)m;      // Z
   b[11] = sizeof(zd) * 32 * 32;             // T
   b[12] = sizeof(double) * 2 * (size_t)m;   // tau
+  b[13] = sizeof(zd) * 32 * (size_t)l;      // Vb
+  b[14] = sizeof(zd) * (size_t)m * (size_t)m;  // R1
+  b[15] = sizeof(zd) * 32 * (size_t)sms;    // dpart
+  b[16] = sizeof(double) * (size_t)sms;     // npart
+  b[17] = sizeof(GridBarrier);
 }
 
 cudaError_t launch_trailing_products(QrBlkWork &w, const void *V, int64_t ldv, void *C, int64_t ldc, int64_t rows,
@@ -54,6 +220,53 @@ cudaError_t launch_trailing_products(QrBlkWork &w, const void *V, int64_t ldv, v
     if ((e = launch_oz_fwd(g, st)) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// Y P = Q R for the l x m sketch Y (column-major, ld l, overwritten): blocked Householder QR of
+// Y without pivoting (panels of 32 columns, trailing updates on the tensor cores), then the
+// pivoted QR of the m x m triangle R1 with the arguments of q (its Y replaced by R1).
+cudaError_t launch_qr_blocked(QrBlkWork &w, const QrArgs &q, int sms, cudaStream_t st) {
+  const int64_t l = q.l, m = q.m;
+  if (l > w.l || m > w.m || l < m) return cudaErrorInvalidValue;
+  zd *Y = static_cast<zd *>(q.Y);
+  cudaError_t e;
+  for (int64_t k0 = 0; k0 < m; k0 += kPanel) {
+    const int jb = (int)std::min<int64_t>(kPanel, m - k0);
+    const int L = (int)(l - k0);
+    zd *P = Y + k0 * l + k0;
+    if ((e = cudaMemsetAsync(w.bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return e;
+    int G = std::min<int>(sms, std::max(1, L / 16));
+    void *args[] = {(void *)&P, (void *)&l, (void *)&L, (void *)&jb, (void *)&w.Vb, (void *)&l, (void *)&w.T,
+                    (void *)&w.tau, (void *)&w.dpart, (void *)&w.npart, (void *)&w.bar, (void *)&q.err,
+                    (void *)&q.limit_ns};
+    zd *tau = static_cast<zd *>(w.tau) + k0;
+    args[7] = (void *)&tau;
+    note_launch();
+    if ((e = cudaLaunchCooperativeKernel((const void *)qr_panel_kernel, dim3(G), dim3(kPanelThreads), args, 0, st)) !=
+        cudaSuccess)
+      return e;
+    if (k0 + jb < m) {
+      const int64_t cols = m - k0 - jb;
+      zd *C = Y + (k0 + jb) * l + k0;
+      if ((e = launch_trailing_products(w, w.Vb, l, C, l, L, cols, nullptr, 0, w.W, q.err, q.limit_ns, st)) !=
+          cudaSuccess)
+        return e;
+      note_launch();
+      qr_tw_kernel<<<(unsigned)((cols * kPanel + 255) / 256), 256, 0, st>>>(
+          static_cast<const zd *>(w.T), static_cast<const zd *>(w.W), static_cast<zd *>(w.Z), cols);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = launch_trailing_products(w, w.Vb, l, C, l, L, cols, w.Z, kPanel, nullptr, q.err, q.limit_ns, st)) !=
+          cudaSuccess)
+        return e;
+    }
+  }
+  note_launch();
+  qr_copy_r1_kernel<<<(unsigned)((m * m + 255) / 256), 256, 0, st>>>(Y, l, (int)m, static_cast<zd *>(w.R1));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  QrArgs q2 = q;
+  q2.Y = w.R1;
+  q2.l = (int)m;
+  return launch_qrp(q2, st);
 }
 
 }  // namespace mn

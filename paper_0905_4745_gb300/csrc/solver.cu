@@ -181,6 +181,7 @@ struct minnorm_plan_s {
   // blocked QR of the sketch (allocated on first use)
   QrBlkWork qb;
   bool qb_ready = false;
+  bool qr_blocked = false;   // Step 2 by the blocked QR (qrblk.cu) rather than the column-by-column kernel
   cudaEvent_t ev_as0 = nullptr, ev_as1 = nullptr;
   // timing
   std::vector<KernelTimer> timers;
@@ -475,11 +476,23 @@ minnorm_status upload_params(minnorm_plan_t plan) {
     plan->eps_sk = sketch_error_bound(plan, chain_w, per, tol, 0.0);
   }
   // Householder QR (FP64): backward error within 8 m (d + 4) 2^-53 ||Y||_F, d the depth of its
-  // dot products' sums (a thread's run of rows plus the warp, block and grid trees)
-  plan->eps_qr = 8.0 * (double)plan->m * (double)((l + 127) / 128 + 20) * 0x1.0p-53;
+  // dot products' sums (a thread's run of rows plus the warp, block and grid trees). The blocked
+  // form adds its two QRs' bounds: the l x m one, whose panel sums have depth l / (8 G) + 8 + G
+  // and whose tensor-core products err by at most 2^-52 sqrt(K) ||v|| ||c|| (K = 2l: depth
+  // sqrt(2l) in this form), then the m x m pivoted one.
+  if (plan->qr_blocked) {
+    const double G = plan->sms;
+    const double d1 = (double)l / (8.0 * G) + 8.0 + G + 2.0 * std::sqrt(2.0 * (double)l);
+    const double d2 = (double)((plan->m + 127) / 128 + 20);
+    plan->eps_qr = 8.0 * (double)plan->m * (d1 + d2 + 8.0) * 0x1.0p-53;
+  } else {
+    plan->eps_qr = 8.0 * (double)plan->m * (double)((l + 127) / 128 + 20) * 0x1.0p-53;
+  }
   plan->sketched = false;
   return MINNORM_OK;
 }
+
+minnorm_status qrblk_alloc(minnorm_plan_t plan);
 
 minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l, minnorm_dtype dtype,
                            minnorm_precision prec, uint64_t seed, uint32_t flags, void *stream) {
@@ -605,6 +618,12 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
     ALLOC(plan->d_qqp, sizeof(double) * plan->sms);
     ALLOC(plan->d_ggp, sizeof(double) * plan->sms);
   }
+  // Step 2 for tall sketches: the blocked QR with tensor-core trailing updates (its workspace now)
+  plan->qr_blocked = l > 2048 && !plan->pool;
+  if (plan->qr_blocked) {
+    minnorm_status qs = qrblk_alloc(plan);
+    if (qs != MINNORM_OK) return qs;
+  }
   if (cudaMallocHost(&plan->h_norms, sizeof(double) * 4) != cudaSuccess) return MINNORM_ENOMEM;
   if (cudaMallocHost(&plan->h_cg, sizeof(CgScalars)) != cudaSuccess) return MINNORM_ENOMEM;
   if (cudaMallocHost(&plan->h_ss, sizeof(SolveState)) != cudaSuccess) return MINNORM_ENOMEM;
@@ -700,7 +719,8 @@ minnorm_status sketch_factor(minnorm_plan_t plan) {
     CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
     QrArgs q{plan->d_Y, (int)l, (int)m, plan->d_vn1, plan->d_vn2, plan->d_beta, plan->d_piv, plan->d_R,
              plan->d_qrmail, plan->d_err, plan->wait_limit_ns};
-    CK(launch_qrp(q, st));
+    if (plan->qr_blocked) CK(launch_qr_blocked(plan->qb, q, plan->sms, st));
+    else CK(launch_qrp(q, st));
     CK(launch_prinv(plan->d_R, plan->d_piv, (int)m, plan->d_Wp, plan->d_WpH, st));
     // ||R||_F, ||P R^{-1}||_F and ||A||_F for the certificate's delta
     CK(launch_sumsq(m * m, plan->d_R, plan->d_red, plan->d_cert, st));
@@ -1391,7 +1411,7 @@ minnorm_status solve_async(minnorm_plan_t plan, const void *A, int64_t lda, cons
 // workspace of the blocked QR (qrblk.cu), allocated on first use
 minnorm_status qrblk_alloc(minnorm_plan_t plan) {
   if (plan->qb_ready) return MINNORM_OK;
-  size_t b[13];
+  size_t b[18];
   qrblk_sizes(plan->l, plan->m, plan->sms, b);
   QrBlkWork &w = plan->qb;
   w.l = plan->l;
@@ -1410,6 +1430,11 @@ minnorm_status qrblk_alloc(minnorm_plan_t plan) {
   ALLOC(w.Z, b[10]);
   ALLOC(w.T, b[11]);
   ALLOC(w.tau, b[12]);
+  ALLOC(w.Vb, b[13]);
+  ALLOC(w.R1, b[14]);
+  ALLOC(w.dpart, b[15]);
+  ALLOC(w.npart, b[16]);
+  ALLOC(w.bar, b[17]);
   plan->qb_ready = true;
   return MINNORM_OK;
 }

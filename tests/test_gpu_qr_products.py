@@ -2,15 +2,17 @@
 W = V^H C and C - V Z, against double-double references from the oracle (Dot2 sums:
 oracle.adj_matvec_dd / matvec_dd), element by element.
 
-Tolerance, from the arithmetic: every operand entry is kept to 52 bits below its row's
+Tolerance, from the arithmetic: every operand entry is kept to 56 bits below its row's
 scale 2^e (the least power of two above the row's largest entry), an absolute error of at
-most 2^(e - 52) <= 2^-51 max|row| per real component, so at most 2^-50.5 per complex entry
-and, through the two real products of each complex one, 2^-50 max|row| in a complex result;
-the slice levels are summed exactly and rounded once to FP64, the K splits (at most 4096 real
-terms each) added in FP64. So
-  |W_jc - W_ref| <= 2^-50 (max|V_:j| sum|C_:c| + max|C_:c| sum|V_:j|) + 2^-53 (splits + 1) |V|^T |C|,
-checked with a factor 2 of slack; normwise this is within 2^-50 sqrt(K) ||v_j|| ||c_c||,
-the order of an FP64 dot product's own a-priori bound (K 2^-53 ||v|| ||c||). Cases: one K range and
+most 2^(e - 56) <= 2^-55 max|row| per real component, so 2^-54 max|row| in a complex result
+through the two real products of each complex one; the slice pairs beyond level 15 are
+dropped (at most 14 * 15 * 16^-15 * 2^(e+f)/256 <= 2^-56 max|v| max|c| per product term);
+the kept levels are summed exactly and rounded once to FP64, the K splits (at most 4096 real
+terms each) added in FP64. So, with K the real length,
+  |W_jc - W_ref| <= 2^-54 (max|V_:j| sum|C_:c| + max|C_:c| sum|V_:j|) + 2^-56 K max|V_:j| max|C_:c|
+                    + 2^-53 (splits + 1) |V|^T |C|,
+checked with a factor 2 of slack; normwise this is within 2^-52 sqrt(K) ||v_j|| ||c_c||, below
+an FP64 dot product's own a-priori bound (K 2^-53 ||v|| ||c||). Cases: one K range and
 several (more than 4096 real terms: split K, summed in FP64), ragged tile edges, rows and
 columns of very different scales, zero rows and columns."""
 import numpy as np
@@ -73,7 +75,8 @@ def test_trailing_products_against_double_double(mn, rows, cols, m, n):
         xh, xl = oracle.adj_matvec_dd(V, np.ascontiguousarray(C[:, c]))
         ref = xh + xl
         mC, sC = absC[:, c].max(), absC[:, c].sum()
-        tol = 2.0 * (2.0 ** -50 * (mV * sC + mC * sV) + 2.0 ** -53 * (splits + 1) * (absV.T @ absC[:, c]))
+        tol = 2.0 * (2.0 ** -54 * (mV * sC + mC * sV) + 2.0 ** -56 * (2 * rows) * mV * mC
+                     + 2.0 ** -53 * (splits + 1) * (absV.T @ absC[:, c]))
         err = np.abs(W[:, c] - ref)
         assert np.all(err <= tol), (c, np.max(err / np.maximum(tol, 1e-300)))
     # C - V Z against Dot2 sums
@@ -83,7 +86,8 @@ def test_trailing_products_against_double_double(mn, rows, cols, m, n):
         vh, vl = oracle.matvec_dd(V, np.ascontiguousarray(Z[:, c]))
         ref = (C[:, c] - vh) - vl
         mZ, sZ = absZ[:, c].max(), absZ[:, c].sum()
-        tol = 2.0 * (2.0 ** -50 * (mVr * sZ + mZ * sVr) + 2.0 ** -53 * ((absV @ absZ[:, c]) + np.abs(ref) + absC[:, c]))
+        tol = 2.0 * (2.0 ** -54 * (mVr * sZ + mZ * sVr) + 2.0 ** -56 * 64 * mVr * mZ
+                     + 2.0 ** -53 * ((absV @ absZ[:, c]) + np.abs(ref) + absC[:, c]))
         err = np.abs(Cn[:, c] - ref)
         assert np.all(err <= tol), (c, np.max(err / np.maximum(tol, 1e-300)))
 
