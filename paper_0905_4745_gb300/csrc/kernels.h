@@ -238,16 +238,19 @@ struct QrBlkWork {
   void *tau = nullptr;                             // m complex: the reflectors' tau
   void *Vb = nullptr;                              // l x 32 complex: a panel's reflectors (unit diagonal)
   void *R1 = nullptr;                              // m x m complex: the triangle of the unpivoted QR
-  void *dpart = nullptr;                           // sms x 32 complex: panel partial sums
-  double *npart = nullptr;                         // sms: panel partial norms
+  void *ppart = nullptr;                           // 2 x sms x 32 complex: a panel's posted slots
+  void *rowb = nullptr;                            // 2 x 32 complex: a panel's posted rows
   GridBarrier *bar = nullptr;
 };
-// bytes of each buffer: sA, sB, sV, sZ, eA, eB, eV, eZ, part, W, Z, T, tau, Vb, R1, dpart, npart, bar
+// bytes of each buffer: sA, sB, sV, sZ, eA, eB, eV, eZ, part, W, Z, T, tau, Vb, R1, ppart, rowb, bar
 void qrblk_sizes(int64_t l, int64_t m, int sms, size_t (&bytes)[18]);
 // Y P = Q R (Step 2) for l x m sketches, l >= m: blocked unpivoted QR, then the pivoted QR of
 // its m x m triangle (launch_qrp with the arguments of q); the pivots and R are those of the
 // pivoted QR of Y (R up to a unit diagonal)
 cudaError_t launch_qr_blocked(QrBlkWork &w, const QrArgs &q, int sms, cudaStream_t st);
+// rows of a panel one CTA may hold in shared memory; the blocked QR needs l <= kPanelMaxRows * sms
+constexpr int kPanelMaxRows = 384;
+int qrblk_panel_grid(int64_t L, int sms);
 // W = V^H C (when W is set; 32 x cols, ldw 32) and then C -= V Z (when Z is set; Z 32 x cols,
 // column-major, ldz): V rows x 32 (ldv), C rows x cols (ldc), all complex FP64 column-major;
 // rows <= l, cols <= m of the workspace

@@ -22,55 +22,95 @@ static int64_t qpad(int64_t v, int64_t q) { return (v + q - 1) / q * q; }
 
 constexpr int kPanel = 32;           // columns per panel (the reflectors of one compact WY block)
 constexpr int kPanelThreads = 256;   // 8 warps; lane = panel column
+constexpr int kPanelWarps = kPanelThreads / 32;
+constexpr int kPanelLd = kPanel + 1; // shared-memory row stride of the panel block (complex entries)
+
+__device__ __forceinline__ zd shfl_zd(zd v, int src) {
+  return {__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
+}
+__device__ __forceinline__ zd sel_zd(bool p, zd a, zd b) { return {p ? a.re : b.re, p ? a.im : b.im}; }
 
 // Householder QR without pivoting of the panel P (L rows x jb <= 32 columns, column-major,
 // ld), LAPACK's zgeqr2 conventions: for column j, beta = -sign(Re alpha) ||P[j:, j]||,
 // tau = (beta - alpha) / beta, v = P[j:, j] / (alpha - beta) with v_j = 1, and H_j^H =
-// I - conj(tau) v v^H applied to the columns right of j. The CTAs own contiguous row ranges;
-// warp w takes rows r0 + w, r0 + w + 8, ..., lane c column c. Per column two grid-wide sums
-// (deterministic: every CTA adds the posted partials in the same order), both behind bounded
-// barriers: ||P[j+1:, j]||^2 (posted during the previous column's update), then in one pass
-// d_c = v^H P[:, c] for c > j and e_i = v_i^H v for the earlier reflectors i < j. CTA 0
-// builds the compact WY factor T (Schreiber and Van Loan; LAPACK's zlarft, forward and
-// columnwise): T[j, j] = tau_j, T[:j, j] = -tau_j T[:j, :j] e. Outputs: R's entries and the
-// reflectors in P (beta on the diagonal), V (L x 32, unit diagonal, zeros above; the columns
-// past jb zero), T (32 x 32, column-major), tau.
+// I - conj(tau) v v^H applied to the columns right of j.
+//
+// The CTAs own contiguous row ranges, held in shared memory for the whole panel (warp w
+// takes the rows w, w + 8, ..., lane c column c). One grid-wide sum per column: with
+// x = P[j+1:, j] (the rows below the diagonal), each CTA posts over its own rows
+//     slot j:      ||x||^2,
+//     slot c > j:  g_c = x^H P[j+1:, c],
+//     slot i < j:  h_i = V[j+1:, i]^H x,
+// and the CTA that owns row j posts that row (alpha = P[j, j], P[j, c] for c > j, and
+// V[j, i] for i < j). Every CTA then forms, from the same sums in the same order, with
+// s = 1 / (alpha - beta) (v = (1, s x)):
+//     d_c = v^H P[j:, c] = P[j, c] + conj(s) g_c          (c > j),
+//     e_i = v_i^H v      = conj(V[j, i]) + s h_i          (i < j),
+// updates its rows, and in the same pass forms its slots for column j + 1. CTA 0 builds the
+// compact WY factor T (Schreiber and Van Loan; LAPACK's zlarft, forward and columnwise):
+// T[j, j] = tau_j, T[:j, j] = -tau_j T[:j, :j] e. The posted values are double-buffered
+// by the parity of j, so one barrier per column separates every write from its reads.
+// Outputs: R's entries and the reflectors in P (beta on the diagonal), V (L x 32, unit
+// diagonal, zeros above; the columns past jb zero), T (32 x 32, column-major), tau.
+// Dynamic shared memory: kPanelLd * ceil(L / G) complex entries.
 __global__ void __launch_bounds__(kPanelThreads)
 qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ldv, zd *__restrict__ T,
-                zd *__restrict__ tau, zd *__restrict__ dpart, double *__restrict__ npart, GridBarrier *bar, int *err,
+                zd *__restrict__ tau, zd *__restrict__ part, zd *__restrict__ rowb, GridBarrier *bar, int *err,
                 uint64_t limit_ns) {
-  __shared__ zd s_acc[kPanelThreads / 32][kPanel];
+  extern __shared__ zd s_P[];   // own rows, row-major with stride kPanelLd
+  __shared__ zd s_acc[kPanelWarps][kPanel];
+  __shared__ zd s_tot[kPanel];
+  __shared__ zd s_row[kPanel];
   __shared__ zd s_d[kPanel];
   __shared__ zd s_T[kPanel * kPanel];
-  __shared__ double s_n[kPanelThreads / 32];
-  __shared__ double s_scal[6];   // beta, Re/Im tau, Re/Im scale, ||x||^2
+  __shared__ double s_scal[5];   // beta, Re/Im tau, Re/Im s
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int r0 = (int)((int64_t)L * b / G), r1 = (int)((int64_t)L * (b + 1) / G);
+  const int nr = r1 - r0;
   unsigned int epoch = 0;
-  // V: zero the own rows; T: zero
-  for (int r = r0 + wid; r < r1; r += 8) V[(int64_t)lane * ldv + r] = {0.0, 0.0};
-  if (b == 0)
-    for (int e = tid; e < kPanel * kPanel; e += blockDim.x) s_T[e] = {0.0, 0.0};
-  // ||P[1:, 0]||^2
-  {
-    double n = 0.0;
-    if (lane == 0)
-      for (int r = max(r0, 1) + wid; r < r1; r += 8) n += abs2(P[r]);
-    if (lane == 0) s_n[wid] = n;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < kPanelThreads / 32; ++w) t += s_n[w];
-      npart[b] = t;
-    }
+  for (int e = tid; e < nr * kPanel; e += kPanelThreads) {
+    const int c = e / nr, r = e - c * nr;
+    s_P[r * kPanelLd + c] = c < jb ? ldcg(P + (int64_t)c * ld + r0 + r) : zd{0.0, 0.0};
   }
+  if (b == 0)
+    for (int e = tid; e < kPanel * kPanel; e += kPanelThreads) s_T[e] = {0.0, 0.0};
+  __syncthreads();
+  // the slots of column jn over the own rows r > jn, from the block as it stands; lane c
+  // forms its slot branch-free (conj(a) b with a, b chosen by the lane's side of jn)
+  auto post = [&](int jn) {
+    zd acc = {0.0, 0.0};
+    for (int rr = max(r0, jn + 1) - r0 + wid; rr < nr; rr += kPanelWarps) {
+      const zd p = s_P[rr * kPanelLd + lane];
+      const zd pj = s_P[rr * kPanelLd + jn];
+      macc(acc, sel_zd(lane >= jn, pj, p), sel_zd(lane > jn, p, pj));
+    }
+    s_acc[wid][lane] = acc;
+    __syncthreads();
+    if (wid == 0) {
+      zd t = {0.0, 0.0};
+      for (int w = 0; w < kPanelWarps; ++w) t = t + s_acc[w][lane];
+      part[((int64_t)(jn & 1) * G + b) * kPanel + lane] = t;
+      if (jn >= r0 && jn < r1) rowb[(jn & 1) * kPanel + lane] = s_P[(jn - r0) * kPanelLd + lane];
+    }
+  };
+  post(0);
   for (int j = 0; j < jb; ++j) {
+    const int par = j & 1;
     if (!grid_sync(bar, G, epoch, limit_ns)) { if (tid == 0) atomicExch(err, 1); return; }
-    // the reflector of column j, in every CTA
-    if (tid == 0) {
-      double xn2 = 0.0;
-      for (int q = 0; q < G; ++q) xn2 += ldcg(npart + q);
-      const zd alpha = ldcg(P + (int64_t)j * ld + j);
+    {
+      zd a = {0.0, 0.0};
+      for (int q = wid; q < G; q += kPanelWarps) a = a + ldcg(part + ((int64_t)par * G + q) * kPanel + lane);
+      s_acc[wid][lane] = a;
+      if (wid == 0) s_row[lane] = ldcg(rowb + par * kPanel + lane);
+    }
+    __syncthreads();
+    if (wid == 0) {
+      zd t = {0.0, 0.0};
+      for (int w = 0; w < kPanelWarps; ++w) t = t + s_acc[w][lane];
+      s_tot[lane] = t;
+      // the reflector of column j (the same arithmetic in every CTA)
+      const zd alpha = s_row[j];
+      const double xn2 = __shfl_sync(0xffffffffu, t.re, j);
       double bt = alpha.re;
       zd tj = {0.0, 0.0}, sc = {0.0, 0.0};
       if (!(xn2 == 0.0 && alpha.im == 0.0)) {
@@ -80,43 +120,21 @@ qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ld
         const double dr = alpha.re - bt, di = alpha.im, iden = 1.0 / (dr * dr + di * di);
         sc = {dr * iden, -di * iden};   // 1 / (alpha - beta)
       }
-      s_scal[0] = bt;
-      s_scal[1] = tj.re;
-      s_scal[2] = tj.im;
-      s_scal[3] = sc.re;
-      s_scal[4] = sc.im;
-    }
-    __syncthreads();
-    const zd scale = {s_scal[3], s_scal[4]};
-    const zd tj = {s_scal[1], s_scal[2]};
-    // v on the own rows (v_j = 1 on row j), into P and V; the partial dots
-    zd acc = {0.0, 0.0};
-    for (int r = max(r0, j) + wid; r < r1; r += 8) {
-      zd v;
-      if (r == j) v = {1.0, 0.0};
-      else v = ldcg(P + (int64_t)j * ld + r) * scale;
-      if (lane > j) {
-        if (lane < jb) macc(acc, v, ldcg(P + (int64_t)lane * ld + r));   // conj(v) P[r, c]
-      } else if (lane < j) {
-        macc(acc, ldcg(V + (int64_t)lane * ldv + r), v);                 // conj(v_i[r]) v[r]
-      } else {
-        V[(int64_t)j * ldv + r] = v;
+      zd dv = {0.0, 0.0};
+      if (lane > j && lane < jb) dv = s_row[lane] + conjg(sc) * t;
+      else if (lane < j) dv = conjg(s_row[lane]) + sc * t;
+      s_d[lane] = dv;
+      if (lane == 0) {
+        s_scal[0] = bt;
+        s_scal[1] = tj.re;
+        s_scal[2] = tj.im;
+        s_scal[3] = sc.re;
+        s_scal[4] = sc.im;
       }
     }
-    s_acc[wid][lane] = acc;
     __syncthreads();
-    if (wid == 0) {
-      zd t = {0.0, 0.0};
-      for (int w = 0; w < kPanelThreads / 32; ++w) t = t + s_acc[w][lane];
-      dpart[(int64_t)b * kPanel + lane] = t;
-    }
-    if (!grid_sync(bar, G, epoch, limit_ns)) { if (tid == 0) atomicExch(err, 1); return; }
-    if (wid == 0) {
-      zd t = {0.0, 0.0};
-      for (int q = 0; q < G; ++q) t = t + ldcg(dpart + (int64_t)q * kPanel + lane);
-      s_d[lane] = t;
-    }
-    __syncthreads();
+    const zd tj = {s_scal[1], s_scal[2]};
+    const zd sc = {s_scal[3], s_scal[4]};
     // T column j (CTA 0): T[j, j] = tau_j, T[i, j] = -tau_j sum_{k=i..j-1} T[i, k] e_k
     if (b == 0 && tid < kPanel) {
       const int i = tid;
@@ -129,35 +147,32 @@ qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ld
         tau[j] = tj;
       }
     }
-    // update columns c > j on the own rows r >= j (H_j^H = I - conj(tau) v v^H), beta on the
-    // diagonal, and the partial ||P[j+2:, j+1]||^2 for the next column
-    const zd f = conjg(tj) * s_d[lane];   // conj(tau) d_c
-    double n = 0.0;
-    for (int r = max(r0, j) + wid; r < r1; r += 8) {
-      if (lane > j && lane < jb) {
-        const zd v = r == j ? zd{1.0, 0.0} : ldcg(V + (int64_t)j * ldv + r);
-        zd x = ldcg(P + (int64_t)lane * ld + r);
-        x = x - f * v;
-        P[(int64_t)lane * ld + r] = x;
-        if (lane == j + 1 && r > j + 1) n += abs2(x);
-      } else if (lane == j) {
-        if (r == j) P[(int64_t)j * ld + j] = {s_scal[0], 0.0};
-        else P[(int64_t)j * ld + r] = ldcg(V + (int64_t)j * ldv + r);
-      }
+    // the own rows r >= j: P[r, c] -= conj(tau) d_c v_r (c > j; the lanes past jb have d = 0),
+    // column j becomes v (beta on the diagonal)
+    const zd f = lane > j ? conjg(tj) * s_d[lane] : zd{0.0, 0.0};
+    for (int rr = max(r0, j) - r0 + wid; rr < nr; rr += kPanelWarps) {
+      const int r = r0 + rr;
+      zd *row = s_P + rr * kPanelLd;
+      const zd x = row[j];
+      const zd v = r == j ? zd{1.0, 0.0} : x * sc;
+      zd p = row[lane];
+      p = p - f * v;
+      if (lane == j) p = r == j ? zd{s_scal[0], 0.0} : v;
+      __syncwarp();
+      row[lane] = p;
     }
-    n = warp_sum(n);
-    if (lane == 0) s_n[wid] = n;
     __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < kPanelThreads / 32; ++w) t += s_n[w];
-      npart[b] = t;
-    }
+    if (j + 1 < jb) post(j + 1);
   }
-  if (b == 0) {
-    __syncthreads();
-    for (int e = tid; e < kPanel * kPanel; e += blockDim.x) T[e] = s_T[e];
+  __syncthreads();
+  for (int e = tid; e < nr * kPanel; e += kPanelThreads) {
+    const int c = e / nr, r = e - c * nr, gr = r0 + r;
+    const zd p = s_P[r * kPanelLd + c];
+    if (c < jb) P[(int64_t)c * ld + gr] = p;
+    V[(int64_t)c * ldv + gr] = c >= jb ? zd{0.0, 0.0} : gr > c ? p : gr == c ? zd{1.0, 0.0} : zd{0.0, 0.0};
   }
+  if (b == 0)
+    for (int e = tid; e < kPanel * kPanel; e += kPanelThreads) T[e] = s_T[e];
 }
 
 // Z = T^H W: Z[:, c] = T^H W[:, c], T 32 x 32 upper triangular (one thread per (row k, column c))
@@ -195,8 +210,8 @@ void qrblk_sizes(int64_t l, int64_t m, int sms, size_t (&b)[18]) {
   b[12] = sizeof(double) * 2 * (size_t)m;   // tau
   b[13] = sizeof(zd) * 32 * (size_t)l;      // Vb
   b[14] = sizeof(zd) * (size_t)m * (size_t)m;  // R1
-  b[15] = sizeof(zd) * 32 * (size_t)sms;    // dpart
-  b[16] = sizeof(double) * (size_t)sms;     // npart
+  b[15] = sizeof(zd) * 32 * 2 * (size_t)sms;  // ppart: the panel's posted slots, two parities
+  b[16] = sizeof(zd) * 32 * 2;                // rowb: the posted rows, two parities
   b[17] = sizeof(GridBarrier);
 }
 
@@ -222,6 +237,13 @@ cudaError_t launch_trailing_products(QrBlkWork &w, const void *V, int64_t ldv, v
   return cudaSuccess;
 }
 
+// CTAs of a panel of L rows: at most one per SM, at least 16 rows each, at most
+// kPanelMaxRows rows each (the block held in shared memory); 0 when L needs more
+int qrblk_panel_grid(int64_t L, int sms) {
+  const int64_t g = std::min<int64_t>(sms, std::max<int64_t>(1, L / 16));
+  return (L + g - 1) / g <= kPanelMaxRows ? (int)g : 0;
+}
+
 // Y P = Q R for the l x m sketch Y (column-major, ld l, overwritten): blocked Householder QR of
 // Y without pivoting (panels of 32 columns, trailing updates on the tensor cores), then the
 // pivoted QR of the m x m triangle R1 with the arguments of q (its Y replaced by R1).
@@ -230,20 +252,24 @@ cudaError_t launch_qr_blocked(QrBlkWork &w, const QrArgs &q, int sms, cudaStream
   if (l > w.l || m > w.m || l < m) return cudaErrorInvalidValue;
   zd *Y = static_cast<zd *>(q.Y);
   cudaError_t e;
+  if ((e = cudaFuncSetAttribute(qr_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(zd) * kPanelLd * kPanelMaxRows))) != cudaSuccess)
+    return e;
   for (int64_t k0 = 0; k0 < m; k0 += kPanel) {
     const int jb = (int)std::min<int64_t>(kPanel, m - k0);
     const int L = (int)(l - k0);
     zd *P = Y + k0 * l + k0;
     if ((e = cudaMemsetAsync(w.bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return e;
-    int G = std::min<int>(sms, std::max(1, L / 16));
-    void *args[] = {(void *)&P, (void *)&l, (void *)&L, (void *)&jb, (void *)&w.Vb, (void *)&l, (void *)&w.T,
-                    (void *)&w.tau, (void *)&w.dpart, (void *)&w.npart, (void *)&w.bar, (void *)&q.err,
-                    (void *)&q.limit_ns};
+    const int G = qrblk_panel_grid(L, sms);
+    if (G <= 0) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(zd) * kPanelLd * (size_t)((L + G - 1) / G);
     zd *tau = static_cast<zd *>(w.tau) + k0;
-    args[7] = (void *)&tau;
+    void *args[] = {(void *)&P, (void *)&l, (void *)&L, (void *)&jb, (void *)&w.Vb, (void *)&l, (void *)&w.T,
+                    (void *)&tau, (void *)&w.ppart, (void *)&w.rowb, (void *)&w.bar, (void *)&q.err,
+                    (void *)&q.limit_ns};
     note_launch();
-    if ((e = cudaLaunchCooperativeKernel((const void *)qr_panel_kernel, dim3(G), dim3(kPanelThreads), args, 0, st)) !=
-        cudaSuccess)
+    if ((e = cudaLaunchCooperativeKernel((const void *)qr_panel_kernel, dim3(G), dim3(kPanelThreads), args, smem,
+                                         st)) != cudaSuccess)
       return e;
     if (k0 + jb < m) {
       const int64_t cols = m - k0 - jb;

@@ -619,7 +619,7 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
     ALLOC(plan->d_ggp, sizeof(double) * plan->sms);
   }
   // Step 2 for tall sketches: the blocked QR with tensor-core trailing updates (its workspace now)
-  plan->qr_blocked = l > 2048 && !plan->pool;
+  plan->qr_blocked = l > 2048 && !plan->pool && qrblk_panel_grid(l, plan->sms) > 0;
   if (plan->qr_blocked) {
     minnorm_status qs = qrblk_alloc(plan);
     if (qs != MINNORM_OK) return qs;
@@ -1432,8 +1432,8 @@ minnorm_status qrblk_alloc(minnorm_plan_t plan) {
   ALLOC(w.tau, b[12]);
   ALLOC(w.Vb, b[13]);
   ALLOC(w.R1, b[14]);
-  ALLOC(w.dpart, b[15]);
-  ALLOC(w.npart, b[16]);
+  ALLOC(w.ppart, b[15]);
+  ALLOC(w.rowb, b[16]);
   ALLOC(w.bar, b[17]);
   plan->qb_ready = true;
   return MINNORM_OK;
