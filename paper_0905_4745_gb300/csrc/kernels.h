@@ -175,15 +175,18 @@ cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st);
 
 // ---- ozaki.cu ----------------------------------------------------------------------
 // FP64-accurate complex products on the tensor cores (the trailing updates of the blocked
-// Householder QR, qrblk.cu). Every FP64 operand entry is split exactly into kOzSlices BF16
-// slices of 4-bit integers scaled by powers of two (one exponent per operand row); the pair
-// products of every slice level are accumulated EXACTLY in FP32 in tensor memory (one
-// accumulator per level: their integer sums fit in 24 bits) and combined in int64.
-constexpr int kOzSlices = 14;     // 14 x 4 bits: 56 bits below each row's scale
-constexpr int kOzN = 32;          // real output columns per tile
+// Householder QR, qrblk.cu). Every FP64 operand entry is truncated to 55 bits below its row's
+// scale (one exponent per operand row) and split exactly into kOzSlices BF16 slices of balanced
+// base-256 digits; the pair products of every kept slice level are accumulated EXACTLY in FP32
+// in tensor memory (one accumulator per level: their integer sums over kOzDrain K-blocks fit in
+// 24 bits) and moved into int64 sums every kOzDrain K-blocks.
+constexpr int kOzSlices = 7;      // 7 x 8 bits: 55 bits below each row's scale
+constexpr int kOzLevels = 8;      // levels s + t <= 7 kept (34 slice pairs)
+constexpr int kOzN = 64;          // real output columns per tile
 constexpr int kOzM = 128;         // output rows per tile
 constexpr int kOzK = 64;          // K per block (one 128-byte row of BF16)
-constexpr int kOzKMax = 4096;     // real K per CTA: 14 x 225 x 4096 < 2^24 (every level exact)
+constexpr int kOzDrain = 2;       // K-blocks per exact accumulation: 7 x 128 x 2^14 < 2^24
+constexpr int kOzKbMax = 480;     // K-blocks per CTA: the int64 level sums stay below 2^53
 // Operand slices: [kOzSlices][rows_pad][k_pad] BF16, K contiguous (rows_pad a multiple of 128,
 // k_pad of 64, zero padded), with one int32 exponent per row.
 struct OzOperand {

@@ -8,24 +8,23 @@
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication and its applications", Numer. Algorithms 59, 2012), with
 // integer slices: every entry x of an operand row with exponent e (all of the
-// row's entries below 2^e in magnitude) is written exactly (to 2^-56 of 2^e) as
-//     x = 2^e / 16 * sum_{s=0}^{13} sigma_s,   sigma_s = +-d_s 16^-s,
-// d_s in 0..15 the base-16 digits of |x| 2^(56-e), read off the FP64 bit pattern
-// with integer shifts (no FP64 instruction; entries within 2^3 of the row's
-// scale keep every bit). Each sigma_s is exact in BF16. A product of two rows
-// is then 2^(e + f) / 256 times the sum over the levels L = s + t of
-// sum_k sigma_s sigma_t. The levels L <= 15 are kept (130 pairs; the dropped
-// ones add at most 14 * 15 * 16^-15 of 2^(e+f)/256 per term, the order of the
-// 56-bit truncation of the entries themselves). A level's sum is an integer
-// multiple of 16^-L whose integer part stays below 14 * 225 * 4096 < 2^24 for
-// K <= 4096 per CTA, so the tensor cores' FP32 accumulation of every kept level
-// (one accumulator each, 16 x 32 = all 512 columns of tensor memory) is EXACT. (A shared FP32 accumulator for the trailing levels is not enough: its
-// rounding grows with the number of terms, and the tensor cores' accumulation
-// truncates.) The levels are combined exactly in two int64 halves and rounded
-// once to FP64; K splits across CTAs are added in FP64. The only other errors
-// are the truncation of each entry to 52 bits below its row's scale: the
-// product is as accurate as an FP64 dot product, at the tensor cores' BF16 rate
-// divided by the 130 slice pairs.
+// row's entries below 2^e in magnitude) is truncated to N = floor(|x| 2^(55-e))
+// < 2^55 (read off the FP64 bit pattern with integer shifts; no FP64
+// instruction) and written in balanced base 256,
+//     x ~ sign(x) 2^(e-7) sum_{s=0}^{6} d_s 256^-s,   d_0 in [0, 128], d_s in [-128, 127],
+// an error below 2^(e-55) <= 2^-54 max|row|. Each d_s is an integer of at most
+// 8 bits, exact in BF16. A product of two rows is then 2^(e+f-14) times the sum
+// over the levels L = s + t of 256^-L I_L, I_L = sum_k sum_{s+t=L} d_s d'_t. The
+// levels L <= 7 are kept (34 pairs; the dropped ones add at most K 2^(e+f) 5.02
+// 2^-64 <= K 2^-59.3 max|a| max|b|). A level has at most 7 pairs and every
+// product is an integer of magnitude <= 2^14, so over 128 real terms (two
+// K-blocks) a level's sum is an integer below 7 2^21 < 2^24 and the tensor
+// cores' FP32 accumulation of it is EXACT (one accumulator per level: 8 x 64 =
+// all 512 columns of tensor memory). Every two K-blocks the epilogue warps move
+// the levels into exact int64 sums, Ih = sum_{L<=3} I_L 256^(3-L) and Il =
+// sum_{L>=4} I_L 256^(7-L); at the end Ih + Il 2^-32 is rounded once to FP64.
+// K splits across CTAs are added in FP64. The product is as accurate as an FP64
+// dot product (normwise), at the tensor cores' BF16 rate divided by 34.
 //
 // Real forms of the complex products (interleaved re/im along K):
 //   adjoint: A row c = (Re C[r,c], Im C[r,c])_r, B row j < 32 = (Re V[r,j], Im V[r,j])_r,
@@ -47,14 +46,14 @@ namespace mn {
 
 namespace {
 
-constexpr int kOzThreads = 256;
+constexpr int kOzEpiWarps = 16;                   // epilogue: 4 lane quarters x 4 column quarters
+constexpr int kOzThreads = 32 * (4 + kOzEpiWarps);
 constexpr int kOzRing = 6;                        // A slice tiles in flight
 constexpr int kOzATile = kOzM * kOzK * 2;         // 16 KB: 128 rows x 64 BF16
-constexpr int kOzBTile = kOzN * kOzK * 2;         // 4 KB: 32 rows x 64 BF16
-constexpr int kOzKept = kOzSlices + 2;            // levels 0..15 (pairs s + t <= 15), one accumulator each
-constexpr int kOzTmemCols = kOzKept * kOzN;       // 512
+constexpr int kOzBTile = kOzN * kOzK * 2;         // 8 KB: 64 rows x 64 BF16
+constexpr int kOzTmemCols = kOzLevels * kOzN;     // 512
 constexpr int kOzOffB = kOzRing * kOzATile;       // 96 KB
-constexpr int kOzOffBar = kOzOffB + kOzSlices * kOzBTile;  // 148 KB
+constexpr int kOzOffBar = kOzOffB + 2 * kOzSlices * kOzBTile;  // + 112 KB: two sets of B slices
 constexpr int kOzSmem = kOzOffBar + 512 + 1024;   // barriers + alignment slack
 
 // exponent of a row: the least e with every |x| < 2^e (the FP64 exponent field of the
@@ -65,7 +64,7 @@ __device__ __forceinline__ int oz_expo_of(double x) {
   return f == 0 ? -2000 : f - 1023 + 1;
 }
 
-// the 14 signed slices sigma_s = +-d_s 16^-s of x for row exponent e, as BF16
+// the 7 balanced base-256 digits of x for row exponent e, signed, as BF16
 __device__ __forceinline__ void oz_slices(double x, int e, __nv_bfloat16 (&q)[kOzSlices]) {
   const long long b = __double_as_longlong(x);
   const int f = (int)((b >> 52) & 0x7ff);
@@ -73,15 +72,18 @@ __device__ __forceinline__ void oz_slices(double x, int e, __nv_bfloat16 (&q)[kO
   if (f != 0 && e > -2000) {
     const unsigned long long mant = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
     const int sh = e - (f - 1023);  // >= 1: |x| < 2^e
-    // floor(|x| 2^(56 - e)) = mant 2^(4 - sh), 56 bits
-    N = sh <= 4 ? (mant << (4 - sh)) : (sh - 4 < 64 ? (mant >> (sh - 4)) : 0ull);
+    // floor(|x| 2^(55 - e)) = floor(mant 2^(3 - sh)) < 2^55
+    N = sh <= 3 ? (mant << (3 - sh)) : (sh - 3 < 64 ? (mant >> (sh - 3)) : 0ull);
   }
   const float sgn = b < 0 ? -1.0f : 1.0f;
+  int carry = 0;
 #pragma unroll
-  for (int s = 0; s < kOzSlices; ++s) {
-    const int d = (int)((N >> (4 * (kOzSlices - 1 - s))) & 15ull);
-    q[s] = __float2bfloat16_rn(sgn * (float)d * __int_as_float((127 - 4 * s) << 23));  // d 16^-s, exact
+  for (int s = kOzSlices - 1; s >= 1; --s) {
+    const int r = (int)((N >> (8 * (kOzSlices - 1 - s))) & 255ull) + carry;   // 0..256
+    carry = r >= 128 ? 1 : 0;
+    q[s] = __float2bfloat16_rn(sgn * (float)(r - (carry << 8)));            // -128..127, exact
   }
+  q[0] = __float2bfloat16_rn(sgn * (float)((int)(N >> 48) + carry));        // 0..128, exact
 }
 
 __device__ __forceinline__ int oz_block_max(int v, int *red) {
@@ -228,12 +230,35 @@ struct OzParams {
   uint64_t limit_ns;
 };
 
+__device__ __forceinline__ bool elect_one() {
+  uint32_t p = 0;
+  asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n selp.u32 %0, 1, 0, e;\n}\n" : "=r"(p));
+  return p != 0;
+}
+__device__ __forceinline__ void bar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
+}
+// 16 consecutive 32-bit columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
 // Tile: A rows [128 ma, +128), B rows [64 nb, +64), K-blocks [kb0, kb1). Adjoint: grid
 // (A tiles, K splits), nb = 0; update: grid (A tiles, B tiles), one K-block.
-// Roles: warp 0 lane 0 issues the TMA loads (the 13 B slice tiles of a K-block stay resident;
-// the A slice tiles stream through a 4-deep ring), warp 1 lane 0 issues the MMAs and commits
-// them to the barriers that free the tiles, warp 2 owns the tensor memory, warps 4-7 read the
-// eight accumulators (TMEM lanes 32 (w & 3) + lane = tile rows) and write the result.
+// Roles: warp 0 lane 0 issues the TMA loads (the 7 B slice tiles of a K-block into one of two
+// sets, the A slice tiles through a 6-deep ring); warp 1 runs the product loop converged, one
+// elected lane issuing the MMAs and the commits that free the tiles; warp 2 owns the tensor
+// memory; warps 4-19 drain the 8 level accumulators every kOzDrain K-blocks (warp w reads TMEM
+// lanes 32 (w & 3) + lane = tile rows, columns 16 ((w - 4) >> 2) + 0..15) and write the result.
 template <bool FWD>
 __global__ void __launch_bounds__(kOzThreads, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
@@ -241,28 +266,31 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
   extern __shared__ unsigned char oz_smem_raw[];
   unsigned char *base = (unsigned char *)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char *sA = base;
-  unsigned char *sB = base + kOzOffB;
+  unsigned char *sB = base + kOzOffB;              // [2][kOzSlices] tiles
   uint64_t *bars = reinterpret_cast<uint64_t *>(base + kOzOffBar);
-  uint64_t *a_full = bars;                     // kOzRing
-  uint64_t *a_empty = bars + kOzRing;          // kOzRing
-  uint64_t *b_full = bars + 2 * kOzRing;       // kOzSlices
-  uint64_t *b_empty = b_full + kOzSlices;      // kOzSlices
-  uint64_t *acc_full = b_empty + kOzSlices;    // 1
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_full + 1);
+  uint64_t *a_full = bars;                         // kOzRing
+  uint64_t *a_empty = bars + kOzRing;              // kOzRing
+  uint64_t *b_full = bars + 2 * kOzRing;           // 2 x kOzSlices
+  uint64_t *b_empty = b_full + 2 * kOzSlices;      // 2 x kOzSlices
+  uint64_t *acc_full = b_empty + 2 * kOzSlices;    // 1
+  uint64_t *acc_empty = acc_full + 1;              // 1
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 1);
   __shared__ int s_abort;
   __shared__ int s_a_issued, s_a_used, s_b_issued, s_b_used;
 
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const int ma = blockIdx.x;
-  const int nb = FWD ? blockIdx.y : blockIdx.z;
+  const int nb = FWD ? blockIdx.y : 0;
   const int kb0 = FWD ? 0 : blockIdx.y * P.kb0_stride;
   const int kb1 = FWD ? 1 : min(P.nkb, kb0 + P.kb0_stride);
   const int nkb = kb1 - kb0;
+  const int ndrain = (nkb + kOzDrain - 1) / kOzDrain;
 
   if (tid == 0) {
     for (int q = 0; q < kOzRing; ++q) { bar_init(&a_full[q], 1); bar_init(&a_empty[q], 1); }
-    for (int t = 0; t < kOzSlices; ++t) { bar_init(&b_full[t], 1); bar_init(&b_empty[t], 1); }
+    for (int t = 0; t < 2 * kOzSlices; ++t) { bar_init(&b_full[t], 1); bar_init(&b_empty[t], 1); }
     bar_init(acc_full, 1);
+    bar_init(acc_empty, kOzEpiWarps);
     s_abort = 0;
     s_a_issued = s_a_used = s_b_issued = s_b_used = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -279,148 +307,160 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
   const uint32_t tmem = *tmem_slot;
 
   if (nkb > 0 && wid == 0 && lane == 0) {
-    // producer: per K-block A_0..A_3, then B_12..B_0 (freed in that order by the previous
-    // K-block's products), then A_4..A_12; every wait for a free tile is bounded
+    // producer: per K-block its 7 B tiles (set kk & 1, free once K-block kk - 2's products
+    // are done with it), then its 7 A tiles through the ring; every wait is bounded
     int ai = 0, bi = 0;
     bool ok = true;
-    auto load_a = [&](int kb, int s) -> bool {
-      const int slot = ai % kOzRing;
-      if (ai >= kOzRing && !bar_wait(&a_empty[slot], (uint32_t)(((ai / kOzRing) - 1) & 1), P.limit_ns)) return false;
-      bar_expect(&a_full[slot], kOzATile);
-      tma2d(sA + slot * kOzATile, &amap, kb * kOzK, s * P.a_rows_pad + ma * kOzM, &a_full[slot]);
-      ++ai;
-      return true;
-    };
-    auto load_b = [&](int kb, int t, int kk) -> bool {
-      if (kk > 0 && !bar_wait(&b_empty[t], (uint32_t)((kk - 1) & 1), P.limit_ns)) return false;
-      bar_expect(&b_full[t], kOzBTile);
-      tma2d(sB + t * kOzBTile, &bmap, kb * kOzK, t * P.b_rows_pad + nb * kOzN, &b_full[t]);
-      ++bi;
-      return true;
-    };
     for (int kk = 0; kk < nkb && ok; ++kk) {
-      const int kb = kb0 + kk;
-      for (int s = 0; s < kOzRing && ok; ++s) ok = load_a(kb, s) && !*(volatile int *)&s_abort;
-      for (int t = kOzSlices - 1; t >= 0 && ok; --t) ok = load_b(kb, t, kk) && !*(volatile int *)&s_abort;
-      for (int s = kOzRing; s < kOzSlices && ok; ++s) ok = load_a(kb, s) && !*(volatile int *)&s_abort;
+      const int kb = kb0 + kk, set = kk & 1, use = kk >> 1;
+      for (int t = 0; t < kOzSlices && ok; ++t) {
+        uint64_t *fb = &b_full[set * kOzSlices + t];
+        if (use > 0 && !bar_wait(&b_empty[set * kOzSlices + t], (uint32_t)((use - 1) & 1), P.limit_ns)) ok = false;
+        if (!ok || *(volatile int *)&s_abort) { ok = false; break; }
+        bar_expect(fb, kOzBTile);
+        tma2d(sB + (set * kOzSlices + t) * kOzBTile, &bmap, kb * kOzK, t * P.b_rows_pad + nb * kOzN, fb);
+        ++bi;
+      }
+      for (int s = 0; s < kOzSlices && ok; ++s) {
+        const int slot = ai % kOzRing;
+        if (ai >= kOzRing && !bar_wait(&a_empty[slot], (uint32_t)(((ai / kOzRing) - 1) & 1), P.limit_ns)) ok = false;
+        if (!ok || *(volatile int *)&s_abort) { ok = false; break; }
+        bar_expect(&a_full[slot], kOzATile);
+        tma2d(sA + slot * kOzATile, &amap, kb * kOzK, s * P.a_rows_pad + ma * kOzM, &a_full[slot]);
+        ++ai;
+      }
     }
     if (!ok) atomicExch(&s_abort, 1);
     s_a_issued = ai;
     s_b_issued = bi;
-  } else if (nkb > 0 && wid == 1 && lane == 0) {
-    // products: pair (s, t), s + t <= 15, into accumulator s + t (exact); the first product
-    // into an accumulator (pair (0, t), or (1, 13) and (2, 13) for levels 14 and 15, of the
-    // first K-block) overwrites it. B_t has its last pair at s = 15 - t (B_0 and B_1 at s = 13).
+  } else if (nkb > 0 && wid == 1) {
+    // products: pair (s, t), s + t <= 7, t <= 6, into the accumulator of level s + t; the first
+    // pair of a level in an accumulation period ((0, L), or (1, 6) for level 7) overwrites it.
+    // B_t has its last pair at s = 7 - t (B_1 and B_0 at s = 6).
     int ai = 0, bu = 0;
     bool ok = true;
-    const uint32_t id = idesc(kOzN);
+    constexpr uint32_t id = idesc(kOzN);
+    const uint64_t a_desc0 = sdesc(sa(sA)), b_desc0 = sdesc(sa(sB));
     for (int kk = 0; kk < nkb && ok; ++kk) {
-      for (int s = 0; s < kOzSlices && ok; ++s) {
-        const int slot = ai % kOzRing;
-        ok = bar_wait(&a_full[slot], (uint32_t)((ai / kOzRing) & 1), P.limit_ns);
-        if (ok && s == 0) {
-          for (int t = 0; t < kOzSlices && ok; ++t) ok = bar_wait(&b_full[t], (uint32_t)(kk & 1), P.limit_ns);
-          bu += ok ? kOzSlices : 0;
-        }
-        if (!ok || *(volatile int *)&s_abort) { ok = false; break; }
-        tc_fence_after();
-        const uint32_t a0 = sa(sA + slot * kOzATile);
-        for (int t = 0; t < kOzSlices && s + t < kOzKept; ++t) {
-          const uint32_t d = tmem + (uint32_t)((s + t) * kOzN);
-          const uint32_t b0 = sa(sB + t * kOzBTile);
-          const bool first = kk == 0 && (s == 0 || (s <= 2 && t == kOzSlices - 1));
+      const int set = kk & 1, use = kk >> 1, per = kk % kOzDrain;
+      // every wait's outcome is made warp-uniform: the lanes stay converged for elect.sync
+      if (per == 0 && kk > 0)
+        ok = __all_sync(0xffffffffu, bar_wait(acc_empty, (uint32_t)(((kk / kOzDrain) - 1) & 1), P.limit_ns));
+      for (int t = 0; t < kOzSlices && ok; ++t)
+        ok = __all_sync(0xffffffffu, bar_wait(&b_full[set * kOzSlices + t], (uint32_t)(use & 1), P.limit_ns));
+      if (ok) bu += kOzSlices;
+      const uint64_t bset = b_desc0 + (uint64_t)((set * kOzSlices * kOzBTile) >> 4);
 #pragma unroll
-          for (int k16 = 0; k16 < kOzK / 16; ++k16) {
-            const uint32_t accum = (first && k16 == 0) ? 0u : 1u;
-            mma_bf16(d, sdesc(a0 + k16 * 32), sdesc(b0 + k16 * 32), id, accum);
+      for (int s = 0; s < kOzSlices; ++s) {
+        const int slot = ai % kOzRing;
+        if (ok) ok = __all_sync(0xffffffffu, bar_wait(&a_full[slot], (uint32_t)((ai / kOzRing) & 1), P.limit_ns));
+        if (!ok || __any_sync(0xffffffffu, *(volatile int *)&s_abort != 0)) { ok = false; break; }
+        tc_fence_after();
+        const uint64_t ad = a_desc0 + (uint64_t)((slot * kOzATile) >> 4);
+        if (elect_one()) {
+#pragma unroll
+          for (int t = 0; t < kOzSlices; ++t) {
+            if (s + t < kOzLevels) {
+              const uint32_t d = tmem + (uint32_t)((s + t) * kOzN);
+              const uint64_t bd = bset + (uint64_t)((t * kOzBTile) >> 4);
+              const bool first = per == 0 && (s == 0 || (s == 1 && t == kOzSlices - 1));
+#pragma unroll
+              for (int k16 = 0; k16 < kOzK / 16; ++k16)
+                mma_bf16(d, ad + 2 * k16, bd + 2 * k16, id, (first && k16 == 0) ? 0u : 1u);
+            }
           }
+          mma_commit(&a_empty[slot]);                                   // A_s read
+          if (s >= 1) mma_commit(&b_empty[set * kOzSlices + kOzLevels - 1 - s]);   // B_{7-s}: its last pair
+          if (s == kOzSlices - 1) mma_commit(&b_empty[set * kOzSlices]);             // and B_0 at s = 6
         }
-        mma_commit(&a_empty[slot]);                   // A_s read
-        if (s >= 2) mma_commit(&b_empty[kOzKept - 1 - s]);   // B_{15 - s} has had its last pair
-        if (s == kOzSlices - 1) {                             // and B_1, B_0 at s = 13
-          mma_commit(&b_empty[1]);
-          mma_commit(&b_empty[0]);
-        }
+        __syncwarp();
         ++ai;
       }
+      if (ok && (per == kOzDrain - 1 || kk == nkb - 1)) {
+        if (elect_one()) mma_commit(acc_full);
+        __syncwarp();
+      }
     }
-    if (ok) mma_commit(acc_full);
-    else atomicExch(&s_abort, 1);
-    s_a_used = ai;
-    s_b_used = bu;
+    if (!ok && lane == 0) atomicExch(&s_abort, 1);
+    if (lane == 0) {
+      s_a_used = ai;
+      s_b_used = bu;
+    }
   }
 
-  // epilogue: warps 4-7
+  // epilogue: warps 4-19
   bool good = true;
   if (wid >= 4) {
-    if (nkb > 0) {
-      good = false;
+    const int q = wid & 3, h = (wid - 4) >> 2;
+    const int row = 32 * q + lane;                    // tile row (TMEM lane)
+    const int ga = ma * kOzM + row;                   // A row
+    long long Ih[16], Il[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) { Ih[k] = 0; Il[k] = 0; }
+    for (int dr = 0; dr < ndrain && good; ++dr) {
+      bool ready = false;
       const uint64_t t0 = global_ns();
-      while (!good && !*(volatile int *)&s_abort) {
-        good = bar_try(acc_full, 0u);
-        if (!good && global_ns() - t0 > P.limit_ns) break;
+      while (!ready && !*(volatile int *)&s_abort) {
+        ready = bar_try(acc_full, (uint32_t)(dr & 1));
+        if (!ready && global_ns() - t0 > P.limit_ns) break;
       }
-      good = __all_sync(0xffffffffu, good);
-    }
-    if (good) {
+      good = __all_sync(0xffffffffu, ready);
+      if (!good) break;
       tc_fence_after();
-      const int row = 32 * (wid & 3) + lane;           // tile row (TMEM lane)
-      const int ga = ma * kOzM + row;                   // A row
-      const int ea = P.ea[ga];
-      {
-        // levels 0..7 into Ih = sum I_L 16^(7-L), levels 8..15 into Il = sum I_L 16^(15-L), each
-        // level's sum an exact integer I_L times 16^-L below 2^24 (both halves below 2^53)
-        long long Ih[32], Il[32];
-        float v[32];
+      float v[16];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) { Ih[k] = 0; Il[k] = 0; }
-        if (nkb > 0) {
-#pragma unroll 1
-          for (int L = 0; L < kOzKept; ++L) {
-            tmem_ld32(tmem + ((uint32_t)(32 * (wid & 3)) << 16) + (uint32_t)(L * kOzN), v);
-            const float up = __int_as_float((127 + 4 * L) << 23);  // 16^L
-            if (L < 8) {
+      for (int L = 0; L < kOzLevels; ++L) {
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(L * kOzN + 16 * h), v);
 #pragma unroll
-              for (int k = 0; k < 32; ++k) Ih[k] += (long long)__float2int_rn(v[k] * up) << (4 * (7 - L));
-            } else {
-#pragma unroll
-              for (int k = 0; k < 32; ++k) Il[k] += (long long)__float2int_rn(v[k] * up) << (4 * (15 - L));
-            }
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const int col = k;
-          const int eb = P.eb[nb * kOzN + col];
-          // the levels' sum Ih 16^-7 + Il 16^-15 (one rounding), times 2^(ea + eb) / 256
-          double r = fma((double)Il[k], 0x1.0p-60, (double)Ih[k] * 0x1.0p-28);
-          const int sc = ea + eb - 8;
-          if (ea <= -2000 || eb <= -2000) r = 0.0;
-          else if (sc >= -1022 && sc <= 1023) r *= __longlong_as_double((long long)(sc + 1023) << 52);  // 2^sc
-          else r = ldexp(r, sc);
-          if (FWD) {
-            const int c = nb * kOzN + col;
-            const int i = ga >> 1, p = ga & 1;
-            if (i < P.rows && c < P.cols) {
-              double *dst = reinterpret_cast<double *>(P.C + (int64_t)c * P.ldc + i) + p;
-              *dst -= r;
-            }
-          } else {
-            P.part[((int64_t)blockIdx.y * P.part_rows + ga) * 64 + nb * kOzN + col] = r;
-          }
+        for (int k = 0; k < 16; ++k) {
+          const long long I = (long long)__float2int_rn(v[k]);   // an integer below 2^24: exact
+          if (L < 4) Ih[k] += I * (long long)(1 << (8 * (3 - L)));
+          else Il[k] += I * (long long)(1 << (8 * (7 - L)));
         }
       }
       tc_fence_before();
+      __syncwarp();
+      if (lane == 0) bar_arrive(acc_empty);
     }
-    if (!good) atomicExch(&s_abort, 1);
+    if (good) {
+      const int ea = P.ea[ga];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int col = 16 * h + k;
+        const int eb = P.eb[nb * kOzN + col];
+        // sum_L I_L 256^-L = 2^-24 (Ih + 2^-32 Il): carry Il's high part into Ih (exact), then
+        // one rounding; the product is 2^(ea + eb - 14) times that sum
+        const long long hi = Ih[k] + (Il[k] >> 32);
+        const long long lo = Il[k] & 0xFFFFFFFFll;
+        double r = fma((double)lo, 0x1.0p-32, (double)hi);
+        const int sc = ea + eb - 38;
+        if (ea <= -2000 || eb <= -2000) r = 0.0;
+        else if (sc >= -1022 && sc <= 1023) r *= __longlong_as_double((long long)(sc + 1023) << 52);  // 2^sc
+        else r = ldexp(r, sc);
+        if (FWD) {
+          const int c = nb * kOzN + col;
+          const int i = ga >> 1, p = ga & 1;
+          if (i < P.rows && c < P.cols) {
+            double *dst = reinterpret_cast<double *>(P.C + (int64_t)c * P.ldc + i) + p;
+            *dst -= r;
+          }
+        } else {
+          P.part[((int64_t)blockIdx.y * P.part_rows + ga) * kOzN + col] = r;
+        }
+      }
+    } else if (!good) {
+      atomicExch(&s_abort, 1);
+    }
   }
   __syncthreads();
   if (s_abort && tid == 0) {
     atomicExch(P.err, 1);
     // loads still in flight: the A tiles issued but not taken, the B tiles likewise (bounded)
     for (int q = s_a_used; q < s_a_issued; ++q) bar_wait(&a_full[q % kOzRing], (uint32_t)((q / kOzRing) & 1), P.limit_ns);
-    const int kk_b = s_b_used / kOzSlices;
-    for (int q = s_b_used; q < s_b_issued; ++q) bar_wait(&b_full[q % kOzSlices], (uint32_t)(kk_b & 1), P.limit_ns);
+    for (int q = s_b_used; q < s_b_issued; ++q) {
+      const int kk = q / kOzSlices, t = q % kOzSlices;
+      bar_wait(&b_full[(kk & 1) * kOzSlices + t], (uint32_t)((kk >> 1) & 1), P.limit_ns);
+    }
     // products in flight: the last A tile's commit
     if (s_a_used > 0) {
       const int q = s_a_used - 1;
@@ -525,27 +565,27 @@ cudaError_t launch_oz_slice_z(const void *Z, int64_t ldz, int64_t cols, OzOperan
   return cudaGetLastError();
 }
 
-// K splits of the adjoint product: at most kOzKMax real K per CTA (the exact levels), and
-// enough splits for about two CTAs per SM
+// K splits of the adjoint product: at most kOzKbMax K-blocks per CTA (the int64 level sums
+// stay exact in FP64), and as many splits as fit one wave of CTAs (one per SM) beside the
+// M-tiles, at least one K-block each
 static int oz_adj_splits(int64_t rows, int64_t cols, int sms, int *kb_per) {
   const int64_t nkb = pad_to(2 * rows, kOzK) / kOzK;
   const int64_t mt = pad_to(cols, kOzM) / kOzM;
-  int64_t per = kOzKMax / kOzK;                       // K-blocks per split, at most
-  int64_t splits = (nkb + per - 1) / per;
-  while (mt * splits < 2 * sms && splits < nkb) ++splits;
-  per = (nkb + splits - 1) / splits;
-  splits = (nkb + per - 1) / per;
+  int64_t splits = std::max<int64_t>(1, sms / mt);
+  splits = std::max<int64_t>(splits, (nkb + kOzKbMax - 1) / kOzKbMax);
+  splits = std::min<int64_t>(splits, nkb);
+  const int64_t per = (nkb + splits - 1) / splits;
   *kb_per = (int)per;
-  return (int)splits;
+  return (int)((nkb + per - 1) / per);
 }
 
-// splits x padded rows of the partial sums, bounded for every rows <= l, cols <= m: the split
-// loop stops once splits x M-tiles reaches 2 sms (so at most 2 sms + mt - 1), or starts above it
-// at ceil(K-blocks / 128) splits
+// splits x padded rows of the partial sums, bounded for every rows <= l, cols <= m: the splits
+// are at most max(sms / mt, ceil(K-blocks / kOzKbMax)), so splits x mt <= max(sms, (K-blocks /
+// kOzKbMax + 1) mt)
 size_t oz_adj_partial_bytes(int64_t l, int64_t m, int sms) {
   const int64_t mt = pad_to(m, kOzM) / kOzM, nkb = pad_to(2 * l, kOzK) / kOzK;
-  const int64_t tiles = std::max<int64_t>(2 * (int64_t)sms + mt, (nkb / (kOzKMax / kOzK) + 1) * mt);
-  return sizeof(double) * (size_t)tiles * kOzM * 64;
+  const int64_t tiles = std::max<int64_t>((int64_t)sms + mt, (nkb / kOzKbMax + 1) * mt);
+  return sizeof(double) * (size_t)tiles * kOzM * kOzN;
 }
 
 __global__ void oz_adj_reduce_kernel(const double *__restrict__ part, int splits, int64_t rows_pad, int64_t cols,
@@ -557,7 +597,7 @@ __global__ void oz_adj_reduce_kernel(const double *__restrict__ part, int splits
   const int j = (int)(e % 32);
   double re = 0.0, im = 0.0;
   for (int s = 0; s < splits; ++s) {
-    const double *d = part + ((int64_t)s * rows_pad + c) * 64;
+    const double *d = part + ((int64_t)s * rows_pad + c) * kOzN;
     re += d[j];
     im += d[32 + j];
   }
@@ -575,7 +615,7 @@ cudaError_t launch_oz_adj(const OzAdjArgs &a, cudaStream_t st) {
   if ((e = oz_map(a.b, kOzN, &bmap)) != cudaSuccess) return e;
   int per = 0;
   const int splits = oz_adj_splits(a.a.k / 2, a.cols, sms, &per);
-  if (sizeof(double) * (size_t)splits * (size_t)a.a.rows_pad * 64 > a.part_bytes) return cudaErrorInvalidValue;
+  if (sizeof(double) * (size_t)splits * (size_t)a.a.rows_pad * kOzN > a.part_bytes) return cudaErrorInvalidValue;
   OzParams P{};
   P.a_rows_pad = (int)a.a.rows_pad;
   P.b_rows_pad = (int)a.b.rows_pad;
@@ -591,7 +631,7 @@ cudaError_t launch_oz_adj(const OzAdjArgs &a, cudaStream_t st) {
       cudaSuccess)
     return e;
   note_launch();
-  oz_gemm_kernel<false><<<dim3((unsigned)(a.a.rows_pad / kOzM), (unsigned)splits, 2u), kOzThreads, kOzSmem, st>>>(
+  oz_gemm_kernel<false><<<dim3((unsigned)(a.a.rows_pad / kOzM), (unsigned)splits), kOzThreads, kOzSmem, st>>>(
       amap, bmap, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   note_launch();

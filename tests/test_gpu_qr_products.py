@@ -2,19 +2,21 @@
 W = V^H C and C - V Z, against double-double references from the oracle (Dot2 sums:
 oracle.adj_matvec_dd / matvec_dd), element by element.
 
-Tolerance, from the arithmetic: every operand entry is kept to 56 bits below its row's
-scale 2^e (the least power of two above the row's largest entry), an absolute error of at
-most 2^(e - 56) <= 2^-55 max|row| per real component, so 2^-54 max|row| in a complex result
-through the two real products of each complex one; the slice pairs beyond level 15 are
-dropped (at most 14 * 15 * 16^-15 * 2^(e+f)/256 <= 2^-56 max|v| max|c| per product term);
-the kept levels are summed exactly and rounded once to FP64, the K splits (at most 4096 real
-terms each) added in FP64. So, with K the real length,
-  |W_jc - W_ref| <= 2^-54 (max|V_:j| sum|C_:c| + max|C_:c| sum|V_:j|) + 2^-56 K max|V_:j| max|C_:c|
-                    + 2^-53 (splits + 1) |V|^T |C|,
-checked with a factor 2 of slack; normwise this is within 2^-52 sqrt(K) ||v_j|| ||c_c||, below
-an FP64 dot product's own a-priori bound (K 2^-53 ||v|| ||c||). Cases: one K range and
-several (more than 4096 real terms: split K, summed in FP64), ragged tile edges, rows and
-columns of very different scales, zero rows and columns."""
+Tolerance, from the arithmetic: every operand entry is truncated to 55 bits below its row's
+scale 2^e (the least power of two above the row's largest entry component), an absolute error
+below 2^(e - 55) <= 2^-54 max|row| per real component. A complex result is two real products
+of the interleaved real forms, whose sums of moduli are at most sqrt 2 times the complex ones,
+so the truncation adds at most 2^-53 (max|V_:j| sum|C_:c| + max|C_:c| sum|V_:j|). The slice
+pairs beyond level 7 are dropped: at most 5.02 2^-64 2^(e+f) <= 2^-59.3 max|v| max|c| per real
+term, so (2 K real terms, sqrt 2 for the modulus) 2^-57.8 K max|V_:j| max|C_:c| for complex
+length K. The kept levels are summed exactly and rounded once to FP64 per K split, the splits
+added in FP64: 2^-53 (splits + 1) |V|^T |C| per component. So
+  |W_jc - W_ref| <= 2^-53 (max|V_:j| sum|C_:c| + max|C_:c| sum|V_:j|) + 2^-57 K max|V_:j| max|C_:c|
+                    + 2^-52 (splits + 1) |V|^T|C|,
+checked with a factor 2 of slack; normwise this is within 2^-51 sqrt(K) ||v_j|| ||c_c||, the
+order of an FP64 dot product's own a-priori bound (2K 2^-53 ||v|| ||c||). Cases: one K range and
+several (split K, summed in FP64; odd K-block counts), ragged tile edges, rows and columns of
+very different scales, zero rows and columns."""
 import numpy as np
 import pytest
 
@@ -52,7 +54,8 @@ def _inputs(rows, cols, seed):
     return V, C, Z
 
 
-@pytest.mark.parametrize("rows,cols,m,n", [(1200, 300, 300, 8192), (1000, 257, 300, 8192), (4400, 1100, 1100, 16384)])
+@pytest.mark.parametrize("rows,cols,m,n", [(1200, 300, 300, 8192), (1000, 257, 300, 8192), (4400, 1100, 1100, 16384),
+                                           (33, 70, 300, 8192)])
 def test_trailing_products_against_double_double(mn, rows, cols, m, n):
     import torch
     V, C, Z = _inputs(rows, cols, seed=rows + cols)
@@ -65,18 +68,16 @@ def test_trailing_products_against_double_double(mn, rows, cols, m, n):
         W, Cn = Wt.cpu().numpy(), Ct.cpu().numpy()
     finally:
         mn.minnorm_plan_destroy(plan)
-    # W = V^H C against Dot2 sums; the K splits the product used (at most 4096 real terms each)
-    splits = 2 * rows
-    splits = -(-splits // 4096) if 2 * rows > 4096 else 1
-    splits = max(splits, 2 * rows // 64)      # the library may split further (at most one per 64)
+    # W = V^H C against Dot2 sums; the library splits K into at most one split per 64 real terms
+    splits = -(-2 * rows // 64)
     absV, absC = np.abs(V), np.abs(C)
     mV, sV = absV.max(axis=0), absV.sum(axis=0)      # per reflector column j
     for c in range(cols):
         xh, xl = oracle.adj_matvec_dd(V, np.ascontiguousarray(C[:, c]))
         ref = xh + xl
         mC, sC = absC[:, c].max(), absC[:, c].sum()
-        tol = 2.0 * (2.0 ** -54 * (mV * sC + mC * sV) + 2.0 ** -56 * (2 * rows) * mV * mC
-                     + 2.0 ** -53 * (splits + 1) * (absV.T @ absC[:, c]))
+        tol = 2.0 * (2.0 ** -53 * (mV * sC + mC * sV) + 2.0 ** -57 * rows * mV * mC
+                     + 2.0 ** -52 * (splits + 1) * (absV.T @ absC[:, c]))
         err = np.abs(W[:, c] - ref)
         assert np.all(err <= tol), (c, np.max(err / np.maximum(tol, 1e-300)))
     # C - V Z against Dot2 sums
@@ -86,8 +87,8 @@ def test_trailing_products_against_double_double(mn, rows, cols, m, n):
         vh, vl = oracle.matvec_dd(V, np.ascontiguousarray(Z[:, c]))
         ref = (C[:, c] - vh) - vl
         mZ, sZ = absZ[:, c].max(), absZ[:, c].sum()
-        tol = 2.0 * (2.0 ** -54 * (mVr * sZ + mZ * sVr) + 2.0 ** -56 * 64 * mVr * mZ
-                     + 2.0 ** -53 * ((absV @ absZ[:, c]) + np.abs(ref) + absC[:, c]))
+        tol = 2.0 * (2.0 ** -53 * (mVr * sZ + mZ * sVr) + 2.0 ** -57 * 32 * mVr * mZ
+                     + 2.0 ** -52 * ((absV @ absZ[:, c]) + np.abs(ref) + absC[:, c]))
         err = np.abs(Cn[:, c] - ref)
         assert np.all(err <= tol), (c, np.max(err / np.maximum(tol, 1e-300)))
 
