@@ -175,26 +175,29 @@ cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st);
 
 // ---- ozaki.cu ----------------------------------------------------------------------
 // FP64-accurate complex products on the tensor cores (the trailing updates of the blocked
-// Householder QR, qrblk.cu). Every FP64 operand entry is truncated to 55 bits below its row's
-// scale (one exponent per operand row) and split exactly into kOzSlices BF16 slices of balanced
+// Householder QR, qrblk.cu). Every FP64 operand entry is truncated to 8 S - 1 bits below its
+// row's scale (one exponent per operand row) and split exactly into S BF16 slices of balanced
 // base-256 digits; the pair products of every kept slice level are accumulated EXACTLY in FP32
 // in tensor memory (one accumulator per level: their integer sums over kOzDrain K-blocks fit in
-// 24 bits) and moved into int64 sums every kOzDrain K-blocks.
-constexpr int kOzSlices = 7;      // 7 x 8 bits: 55 bits below each row's scale
-constexpr int kOzLevels = 8;      // levels s + t <= 7 kept (34 slice pairs)
-constexpr int kOzN = 64;          // real output columns per tile
+// 24 bits) and moved into int64 sums every kOzDrain K-blocks. The adjoint product (K = the
+// trailing block's rows, up to l) keeps 63 bits and the levels s + t <= 8 (43 slice pairs): its
+// error is within a few units of 2^-53 ||v|| ||c|| at any K. The update (K = 32 reflectors)
+// keeps 55 bits and the levels s + t <= 7 (34 pairs) on wider tiles.
+constexpr int kOzSlicesAdj = 8, kOzLevelsAdj = 9, kOzNAdj = 32;
+constexpr int kOzSlicesFwd = 7, kOzLevelsFwd = 8, kOzNFwd = 64;
 constexpr int kOzM = 128;         // output rows per tile
 constexpr int kOzK = 64;          // K per block (one 128-byte row of BF16)
-constexpr int kOzDrain = 2;       // K-blocks per exact accumulation: 7 x 128 x 2^14 < 2^24
+constexpr int kOzDrain = 2;       // K-blocks per exact accumulation: 8 x 128 x 2^14 <= 2^24
 constexpr int kOzKbMax = 480;     // K-blocks per CTA: the int64 level sums stay below 2^53
-// Operand slices: [kOzSlices][rows_pad][k_pad] BF16, K contiguous (rows_pad a multiple of 128,
-// k_pad of 64, zero padded), with one int32 exponent per row.
+// Operand slices: [ns][rows_pad][k_pad] BF16, K contiguous (rows_pad a multiple of 128 (64 for
+// the update's B), k_pad of 64, zero padded), with one int32 exponent per row.
 struct OzOperand {
   void *slices;
   int32_t *expo;
   int64_t rows, rows_pad, k, k_pad;
+  int ns;                 // slices
 };
-size_t oz_slice_bytes(int64_t rows, int64_t k);
+size_t oz_slice_bytes(int64_t rows, int64_t k, int ns);
 // A rows from C's columns: row c = (Re C[r, c], Im C[r, c]) for r = 0..rows-1 interleaved along K
 cudaError_t launch_oz_slice_cols(const void *C, int64_t ldc, int64_t rows, int64_t cols, OzOperand &out,
                                  cudaStream_t st);

@@ -8,23 +8,26 @@
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication and its applications", Numer. Algorithms 59, 2012), with
 // integer slices: every entry x of an operand row with exponent e (all of the
-// row's entries below 2^e in magnitude) is truncated to N = floor(|x| 2^(55-e))
-// < 2^55 (read off the FP64 bit pattern with integer shifts; no FP64
+// row's entries below 2^e in magnitude) is truncated to N = floor(|x| 2^(8S-1-e))
+// < 2^(8S-1) (read off the FP64 bit pattern with integer shifts; no FP64
 // instruction) and written in balanced base 256,
-//     x ~ sign(x) 2^(e-7) sum_{s=0}^{6} d_s 256^-s,   d_0 in [0, 128], d_s in [-128, 127],
-// an error below 2^(e-55) <= 2^-54 max|row|. Each d_s is an integer of at most
-// 8 bits, exact in BF16. A product of two rows is then 2^(e+f-14) times the sum
-// over the levels L = s + t of 256^-L I_L, I_L = sum_k sum_{s+t=L} d_s d'_t. The
-// levels L <= 7 are kept (34 pairs; the dropped ones add at most K 2^(e+f) 5.02
-// 2^-64 <= K 2^-59.3 max|a| max|b|). A level has at most 7 pairs and every
-// product is an integer of magnitude <= 2^14, so over 128 real terms (two
-// K-blocks) a level's sum is an integer below 7 2^21 < 2^24 and the tensor
-// cores' FP32 accumulation of it is EXACT (one accumulator per level: 8 x 64 =
-// all 512 columns of tensor memory). Every two K-blocks the epilogue warps move
-// the levels into exact int64 sums, Ih = sum_{L<=3} I_L 256^(3-L) and Il =
-// sum_{L>=4} I_L 256^(7-L); at the end Ih + Il 2^-32 is rounded once to FP64.
-// K splits across CTAs are added in FP64. The product is as accurate as an FP64
-// dot product (normwise), at the tensor cores' BF16 rate divided by 34.
+//     x ~ sign(x) 2^(e-7) sum_{s<S} d_s 256^-s,   d_0 in [0, 128], d_s in [-128, 127],
+// an error below 2^(e-8S+1) <= 2^(-8S+2) max|row|. Each d_s is an integer of at
+// most 8 bits, exact in BF16. A product of two rows is then 2^(e+f-14) times the
+// sum over the levels L = s + t of 256^-L I_L, I_L = sum_k sum_{s+t=L} d_s d'_t;
+// the levels L < NL are kept. A level has at most 8 pairs and every product is an
+// integer of magnitude <= 2^14, so over 128 real terms (two K-blocks) a level's
+// sum is an integer of magnitude <= 2^24 and the tensor cores' FP32 accumulation
+// of it is EXACT (one accumulator per level in tensor memory). Every two
+// K-blocks the epilogue warps move the levels into exact int64 sums; at the end
+// the sum is rounded once to FP64. K splits across CTAs are added with a
+// compensated sum (one rounding in all). Two shapes:
+//   adjoint (K up to the sketch's l): S = 8 (63 bits), NL = 9 (43 pairs), 32-column
+//     tiles; dropped levels <= K 2^-67.4 max|a| max|b|: within a few units of
+//     2^-53 |a|^T |b| at any K, as accurate as an FP64 dot product
+//   update (K = 64 real): S = 7 (55 bits), NL = 8 (34 pairs), 64-column tiles;
+//     dropped levels <= K 2^-59.6 max|a| max|b|
+// at the tensor cores' BF16 rate divided by the pair count.
 //
 // Real forms of the complex products (interleaved re/im along K):
 //   adjoint: A row c = (Re C[r,c], Im C[r,c])_r, B row j < 32 = (Re V[r,j], Im V[r,j])_r,
@@ -50,11 +53,15 @@ constexpr int kOzEpiWarps = 16;                   // epilogue: 4 lane quarters x
 constexpr int kOzThreads = 32 * (4 + kOzEpiWarps);
 constexpr int kOzRing = 6;                        // A slice tiles in flight
 constexpr int kOzATile = kOzM * kOzK * 2;         // 16 KB: 128 rows x 64 BF16
-constexpr int kOzBTile = kOzN * kOzK * 2;         // 8 KB: 64 rows x 64 BF16
-constexpr int kOzTmemCols = kOzLevels * kOzN;     // 512
-constexpr int kOzOffB = kOzRing * kOzATile;       // 96 KB
-constexpr int kOzOffBar = kOzOffB + 2 * kOzSlices * kOzBTile;  // + 112 KB: two sets of B slices
-constexpr int kOzSmem = kOzOffBar + 512 + 1024;   // barriers + alignment slack
+constexpr int kOzTmemCols = 512;
+
+template <int S, int NT>
+struct OzShape {
+  static constexpr int kBTile = NT * kOzK * 2;                  // NT rows x 64 BF16
+  static constexpr int kOffB = kOzRing * kOzATile;              // 96 KB of A ring
+  static constexpr int kOffBar = kOffB + 2 * S * kBTile;        // two sets of B slices
+  static constexpr int kSmem = kOffBar + 512 + 1024;            // barriers + alignment slack
+};
 
 // exponent of a row: the least e with every |x| < 2^e (the FP64 exponent field of the
 // largest entry, plus one); -2000 for a zero row
@@ -64,26 +71,30 @@ __device__ __forceinline__ int oz_expo_of(double x) {
   return f == 0 ? -2000 : f - 1023 + 1;
 }
 
-// the 7 balanced base-256 digits of x for row exponent e, signed, as BF16
-__device__ __forceinline__ void oz_slices(double x, int e, __nv_bfloat16 (&q)[kOzSlices]) {
+// the S balanced base-256 digits of x for row exponent e (N = floor(|x| 2^(8S - 1 - e)) <
+// 2^(8S - 1)), signed, as BF16
+template <int S>
+__device__ __forceinline__ void oz_slices(double x, int e, __nv_bfloat16 (&q)[S]) {
+  static_assert(S == 7 || S == 8, "7 or 8 slices");
+  constexpr int kb = 8 * S - 1;   // bits kept below 2^e
   const long long b = __double_as_longlong(x);
   const int f = (int)((b >> 52) & 0x7ff);
   unsigned long long N = 0;
   if (f != 0 && e > -2000) {
     const unsigned long long mant = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
     const int sh = e - (f - 1023);  // >= 1: |x| < 2^e
-    // floor(|x| 2^(55 - e)) = floor(mant 2^(3 - sh)) < 2^55
-    N = sh <= 3 ? (mant << (3 - sh)) : (sh - 3 < 64 ? (mant >> (sh - 3)) : 0ull);
+    // floor(|x| 2^(kb - e)) = floor(mant 2^(kb - 52 - sh)) < 2^kb
+    N = sh <= kb - 52 ? (mant << (kb - 52 - sh)) : (sh - (kb - 52) < 64 ? (mant >> (sh - (kb - 52))) : 0ull);
   }
   const float sgn = b < 0 ? -1.0f : 1.0f;
   int carry = 0;
 #pragma unroll
-  for (int s = kOzSlices - 1; s >= 1; --s) {
-    const int r = (int)((N >> (8 * (kOzSlices - 1 - s))) & 255ull) + carry;   // 0..256
+  for (int s = S - 1; s >= 1; --s) {
+    const int r = (int)((N >> (8 * (S - 1 - s))) & 255ull) + carry;   // 0..256
     carry = r >= 128 ? 1 : 0;
-    q[s] = __float2bfloat16_rn(sgn * (float)(r - (carry << 8)));            // -128..127, exact
+    q[s] = __float2bfloat16_rn(sgn * (float)(r - (carry << 8)));      // -128..127, exact
   }
-  q[0] = __float2bfloat16_rn(sgn * (float)((int)(N >> 48) + carry));        // 0..128, exact
+  q[0] = __float2bfloat16_rn(sgn * (float)((int)(N >> (8 * (S - 1))) + carry));   // 0..128, exact
 }
 
 __device__ __forceinline__ int oz_block_max(int v, int *red) {
@@ -98,10 +109,11 @@ __device__ __forceinline__ int oz_block_max(int v, int *red) {
 }
 
 // store the slices of one K position pair (k, k+1) of row `row`
+template <int NS>
 __device__ __forceinline__ void oz_put2(__nv_bfloat16 *S, int64_t sstride, int64_t kpad, int64_t row, int64_t k,
-                                        const __nv_bfloat16 (&a)[kOzSlices], const __nv_bfloat16 (&b)[kOzSlices]) {
+                                        const __nv_bfloat16 (&a)[NS], const __nv_bfloat16 (&b)[NS]) {
 #pragma unroll
-  for (int s = 0; s < kOzSlices; ++s) {
+  for (int s = 0; s < NS; ++s) {
     __nv_bfloat162 v;
     v.x = a[s];
     v.y = b[s];
@@ -125,11 +137,11 @@ oz_slice_cols_kernel(const zd *__restrict__ C, int64_t ldc, int64_t rows, int64_
   if (threadIdx.x == 0) expo[c] = e;
   const int64_t ss = rows_pad * kpad;
   for (int64_t r = threadIdx.x; 2 * r < kpad; r += blockDim.x) {
-    __nv_bfloat16 a[kOzSlices], b[kOzSlices];
+    __nv_bfloat16 a[kOzSlicesAdj], b[kOzSlicesAdj];
     const zd v = r < rows ? col[r] : zd{0.0, 0.0};
-    oz_slices(v.re, e, a);
-    oz_slices(v.im, e, b);
-    oz_put2(S, ss, kpad, c, 2 * r, a, b);
+    oz_slices<kOzSlicesAdj>(v.re, e, a);
+    oz_slices<kOzSlicesAdj>(v.im, e, b);
+    oz_put2<kOzSlicesAdj>(S, ss, kpad, c, 2 * r, a, b);
   }
 }
 
@@ -149,13 +161,13 @@ oz_slice_v_adj_kernel(const zd *__restrict__ V, int64_t ldv, int64_t rows, __nv_
   if (threadIdx.x == 0) { expo[j] = e; expo[32 + j] = e; }
   const int64_t ss = (int64_t)64 * kpad;
   for (int64_t r = threadIdx.x; 2 * r < kpad; r += blockDim.x) {
-    __nv_bfloat16 a[kOzSlices], b[kOzSlices], na[kOzSlices];
+    __nv_bfloat16 a[kOzSlicesAdj], b[kOzSlicesAdj], na[kOzSlicesAdj];
     const zd v = r < rows ? col[r] : zd{0.0, 0.0};
-    oz_slices(v.re, e, a);
-    oz_slices(v.im, e, b);
-    oz_slices(-v.re, e, na);
-    oz_put2(S, ss, kpad, j, 2 * r, a, b);         // (Re, Im)
-    oz_put2(S, ss, kpad, 32 + j, 2 * r, b, na);   // (Im, -Re)
+    oz_slices<kOzSlicesAdj>(v.re, e, a);
+    oz_slices<kOzSlicesAdj>(v.im, e, b);
+    oz_slices<kOzSlicesAdj>(-v.re, e, na);
+    oz_put2<kOzSlicesAdj>(S, ss, kpad, j, 2 * r, a, b);         // (Re, Im)
+    oz_put2<kOzSlicesAdj>(S, ss, kpad, 32 + j, 2 * r, b, na);   // (Im, -Re)
   }
 }
 
@@ -177,12 +189,12 @@ oz_slice_v_fwd_kernel(const zd *__restrict__ V, int64_t ldv, int64_t rows, __nv_
   expo[2 * i + 1] = e;
 #pragma unroll 1
   for (int j = 0; j < 32; ++j) {
-    __nv_bfloat16 re[kOzSlices], im[kOzSlices], nim[kOzSlices];
-    oz_slices(v[j].re, e, re);
-    oz_slices(v[j].im, e, im);
-    oz_slices(-v[j].im, e, nim);
-    oz_put2(S, ss, kOzK, 2 * i, 2 * j, re, nim);    // (Re V, -Im V)
-    oz_put2(S, ss, kOzK, 2 * i + 1, 2 * j, im, re); // (Im V, Re V)
+    __nv_bfloat16 re[kOzSlicesFwd], im[kOzSlicesFwd], nim[kOzSlicesFwd];
+    oz_slices<kOzSlicesFwd>(v[j].re, e, re);
+    oz_slices<kOzSlicesFwd>(v[j].im, e, im);
+    oz_slices<kOzSlicesFwd>(-v[j].im, e, nim);
+    oz_put2<kOzSlicesFwd>(S, ss, kOzK, 2 * i, 2 * j, re, nim);    // (Re V, -Im V)
+    oz_put2<kOzSlicesFwd>(S, ss, kOzK, 2 * i + 1, 2 * j, im, re); // (Im V, Re V)
   }
 }
 
@@ -203,10 +215,10 @@ oz_slice_z_kernel(const zd *__restrict__ Z, int64_t ldz, int64_t cols, __nv_bflo
   expo[c] = e;
 #pragma unroll 1
   for (int j = 0; j < 32; ++j) {
-    __nv_bfloat16 re[kOzSlices], im[kOzSlices];
-    oz_slices(z[j].re, e, re);
-    oz_slices(z[j].im, e, im);
-    oz_put2(S, ss, kOzK, c, 2 * j, re, im);
+    __nv_bfloat16 re[kOzSlicesFwd], im[kOzSlicesFwd];
+    oz_slices<kOzSlicesFwd>(z[j].re, e, re);
+    oz_slices<kOzSlicesFwd>(z[j].im, e, im);
+    oz_put2<kOzSlicesFwd>(S, ss, kOzK, c, 2 * j, re, im);
   }
 }
 
@@ -238,41 +250,54 @@ __device__ __forceinline__ bool elect_one() {
 __device__ __forceinline__ void bar_arrive(uint64_t *b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
 }
-// 16 consecutive 32-bit columns of this warp's 32 lanes
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+// C consecutive 32-bit columns (8 or 16) of this warp's 32 lanes
+template <int C>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[C]) {
+  uint32_t r[C];
+  if constexpr (C == 16) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+  } else {
+    static_assert(C == 8, "8 or 16 columns");
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+  }
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+  for (int k = 0; k < C; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// Tile: A rows [128 ma, +128), B rows [64 nb, +64), K-blocks [kb0, kb1). Adjoint: grid
-// (A tiles, K splits), nb = 0; update: grid (A tiles, B tiles), one K-block.
-// Roles: warp 0 lane 0 issues the TMA loads (the 7 B slice tiles of a K-block into one of two
+// Tile: A rows [128 ma, +128), B rows [NT nb, +NT), K-blocks [kb0, kb1). Adjoint: grid
+// (A tiles, K splits, 2 halves of B), update: grid (A tiles, B tiles), one K-block. S slices,
+// the levels s + t < NL kept.
+// Roles: warp 0 lane 0 issues the TMA loads (the S B slice tiles of a K-block into one of two
 // sets, the A slice tiles through a 6-deep ring); warp 1 runs the product loop converged, one
 // elected lane issuing the MMAs and the commits that free the tiles; warp 2 owns the tensor
-// memory; warps 4-19 drain the 8 level accumulators every kOzDrain K-blocks (warp w reads TMEM
-// lanes 32 (w & 3) + lane = tile rows, columns 16 ((w - 4) >> 2) + 0..15) and write the result.
-template <bool FWD>
+// memory; warps 4-19 drain the NL level accumulators every kOzDrain K-blocks (warp w reads TMEM
+// lanes 32 (w & 3) + lane = tile rows, columns NT/4 ((w - 4) >> 2) + 0..NT/4-1) and write the
+// result.
+template <bool FWD, int S, int NL, int NT>
 __global__ void __launch_bounds__(kOzThreads, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
                const OzParams P) {
+  using SH = OzShape<S, NT>;
+  static_assert(NL * NT <= kOzTmemCols && NL <= 9 && NL >= S, "levels x columns within tensor memory");
+  constexpr int CPT = NT / 4;                       // columns per epilogue thread
   extern __shared__ unsigned char oz_smem_raw[];
   unsigned char *base = (unsigned char *)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char *sA = base;
-  unsigned char *sB = base + kOzOffB;              // [2][kOzSlices] tiles
-  uint64_t *bars = reinterpret_cast<uint64_t *>(base + kOzOffBar);
+  unsigned char *sB = base + SH::kOffB;            // [2][S] tiles
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + SH::kOffBar);
   uint64_t *a_full = bars;                         // kOzRing
   uint64_t *a_empty = bars + kOzRing;              // kOzRing
-  uint64_t *b_full = bars + 2 * kOzRing;           // 2 x kOzSlices
-  uint64_t *b_empty = b_full + 2 * kOzSlices;      // 2 x kOzSlices
-  uint64_t *acc_full = b_empty + 2 * kOzSlices;    // 1
+  uint64_t *b_full = bars + 2 * kOzRing;           // 2 x S
+  uint64_t *b_empty = b_full + 2 * S;              // 2 x S
+  uint64_t *acc_full = b_empty + 2 * S;            // 1
   uint64_t *acc_empty = acc_full + 1;              // 1
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 1);
   __shared__ int s_abort;
@@ -280,7 +305,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
 
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const int ma = blockIdx.x;
-  const int nb = FWD ? blockIdx.y : 0;
+  const int nb = FWD ? blockIdx.y : blockIdx.z;
   const int kb0 = FWD ? 0 : blockIdx.y * P.kb0_stride;
   const int kb1 = FWD ? 1 : min(P.nkb, kb0 + P.kb0_stride);
   const int nkb = kb1 - kb0;
@@ -288,7 +313,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
 
   if (tid == 0) {
     for (int q = 0; q < kOzRing; ++q) { bar_init(&a_full[q], 1); bar_init(&a_empty[q], 1); }
-    for (int t = 0; t < 2 * kOzSlices; ++t) { bar_init(&b_full[t], 1); bar_init(&b_empty[t], 1); }
+    for (int t = 0; t < 2 * S; ++t) { bar_init(&b_full[t], 1); bar_init(&b_empty[t], 1); }
     bar_init(acc_full, 1);
     bar_init(acc_empty, kOzEpiWarps);
     s_abort = 0;
@@ -307,21 +332,21 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
   const uint32_t tmem = *tmem_slot;
 
   if (nkb > 0 && wid == 0 && lane == 0) {
-    // producer: per K-block its 7 B tiles (set kk & 1, free once K-block kk - 2's products
-    // are done with it), then its 7 A tiles through the ring; every wait is bounded
+    // producer: per K-block its S B tiles (set kk & 1, free once K-block kk - 2's products
+    // are done with it), then its S A tiles through the ring; every wait is bounded
     int ai = 0, bi = 0;
     bool ok = true;
     for (int kk = 0; kk < nkb && ok; ++kk) {
       const int kb = kb0 + kk, set = kk & 1, use = kk >> 1;
-      for (int t = 0; t < kOzSlices && ok; ++t) {
-        uint64_t *fb = &b_full[set * kOzSlices + t];
-        if (use > 0 && !bar_wait(&b_empty[set * kOzSlices + t], (uint32_t)((use - 1) & 1), P.limit_ns)) ok = false;
+      for (int t = 0; t < S && ok; ++t) {
+        uint64_t *fb = &b_full[set * S + t];
+        if (use > 0 && !bar_wait(&b_empty[set * S + t], (uint32_t)((use - 1) & 1), P.limit_ns)) ok = false;
         if (!ok || *(volatile int *)&s_abort) { ok = false; break; }
-        bar_expect(fb, kOzBTile);
-        tma2d(sB + (set * kOzSlices + t) * kOzBTile, &bmap, kb * kOzK, t * P.b_rows_pad + nb * kOzN, fb);
+        bar_expect(fb, SH::kBTile);
+        tma2d(sB + (set * S + t) * SH::kBTile, &bmap, kb * kOzK, t * P.b_rows_pad + nb * NT, fb);
         ++bi;
       }
-      for (int s = 0; s < kOzSlices && ok; ++s) {
+      for (int s = 0; s < S && ok; ++s) {
         const int slot = ai % kOzRing;
         if (ai >= kOzRing && !bar_wait(&a_empty[slot], (uint32_t)(((ai / kOzRing) - 1) & 1), P.limit_ns)) ok = false;
         if (!ok || *(volatile int *)&s_abort) { ok = false; break; }
@@ -334,24 +359,24 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
     s_a_issued = ai;
     s_b_issued = bi;
   } else if (nkb > 0 && wid == 1) {
-    // products: pair (s, t), s + t <= 7, t <= 6, into the accumulator of level s + t; the first
-    // pair of a level in an accumulation period ((0, L), or (1, 6) for level 7) overwrites it.
-    // B_t has its last pair at s = 7 - t (B_1 and B_0 at s = 6).
+    // products: pair (s, t), s + t < NL, into the accumulator of level s + t; the first pair of
+    // a level in an accumulation period (the least s, t = L - s <= S - 1) overwrites it. B_t has
+    // its last pair at s = min(S - 1, NL - 1 - t). Every wait's outcome is made warp-uniform:
+    // the lanes stay converged for elect.sync.
     int ai = 0, bu = 0;
     bool ok = true;
-    constexpr uint32_t id = idesc(kOzN);
+    constexpr uint32_t id = idesc(NT);
     const uint64_t a_desc0 = sdesc(sa(sA)), b_desc0 = sdesc(sa(sB));
     for (int kk = 0; kk < nkb && ok; ++kk) {
       const int set = kk & 1, use = kk >> 1, per = kk % kOzDrain;
-      // every wait's outcome is made warp-uniform: the lanes stay converged for elect.sync
       if (per == 0 && kk > 0)
         ok = __all_sync(0xffffffffu, bar_wait(acc_empty, (uint32_t)(((kk / kOzDrain) - 1) & 1), P.limit_ns));
-      for (int t = 0; t < kOzSlices && ok; ++t)
-        ok = __all_sync(0xffffffffu, bar_wait(&b_full[set * kOzSlices + t], (uint32_t)(use & 1), P.limit_ns));
-      if (ok) bu += kOzSlices;
-      const uint64_t bset = b_desc0 + (uint64_t)((set * kOzSlices * kOzBTile) >> 4);
+      for (int t = 0; t < S && ok; ++t)
+        ok = __all_sync(0xffffffffu, bar_wait(&b_full[set * S + t], (uint32_t)(use & 1), P.limit_ns));
+      if (ok) bu += S;
+      const uint64_t bset = b_desc0 + (uint64_t)((set * S * SH::kBTile) >> 4);
 #pragma unroll
-      for (int s = 0; s < kOzSlices; ++s) {
+      for (int s = 0; s < S; ++s) {
         const int slot = ai % kOzRing;
         if (ok) ok = __all_sync(0xffffffffu, bar_wait(&a_full[slot], (uint32_t)((ai / kOzRing) & 1), P.limit_ns));
         if (!ok || __any_sync(0xffffffffu, *(volatile int *)&s_abort != 0)) { ok = false; break; }
@@ -359,19 +384,21 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
         const uint64_t ad = a_desc0 + (uint64_t)((slot * kOzATile) >> 4);
         if (elect_one()) {
 #pragma unroll
-          for (int t = 0; t < kOzSlices; ++t) {
-            if (s + t < kOzLevels) {
-              const uint32_t d = tmem + (uint32_t)((s + t) * kOzN);
-              const uint64_t bd = bset + (uint64_t)((t * kOzBTile) >> 4);
-              const bool first = per == 0 && (s == 0 || (s == 1 && t == kOzSlices - 1));
+          for (int t = 0; t < S; ++t) {
+            if (s + t < NL) {
+              const int L = s + t;
+              const uint32_t d = tmem + (uint32_t)(L * NT);
+              const uint64_t bd = bset + (uint64_t)((t * SH::kBTile) >> 4);
+              const bool first = per == 0 && s == (L > S - 1 ? L - (S - 1) : 0);
 #pragma unroll
               for (int k16 = 0; k16 < kOzK / 16; ++k16)
                 mma_bf16(d, ad + 2 * k16, bd + 2 * k16, id, (first && k16 == 0) ? 0u : 1u);
             }
           }
-          mma_commit(&a_empty[slot]);                                   // A_s read
-          if (s >= 1) mma_commit(&b_empty[set * kOzSlices + kOzLevels - 1 - s]);   // B_{7-s}: its last pair
-          if (s == kOzSlices - 1) mma_commit(&b_empty[set * kOzSlices]);             // and B_0 at s = 6
+          mma_commit(&a_empty[slot]);                   // A_s read
+#pragma unroll
+          for (int t = 0; t < S; ++t)                   // the B tiles whose last pair this was
+            if (s == (NL - 1 - t < S - 1 ? NL - 1 - t : S - 1)) mma_commit(&b_empty[set * S + t]);
         }
         __syncwarp();
         ++ai;
@@ -388,15 +415,17 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
     }
   }
 
-  // epilogue: warps 4-19
+  // epilogue: warps 4-19. Exact int64 sums of the levels: G0 = sum_{L<=3} I_L 256^(3-L),
+  // G1 = sum_{4<=L<=7} I_L 256^(7-L), G2 = I_8, so that sum_L I_L 256^-L = 256^-3 (G0 +
+  // 2^-32 G1 + 2^-40 G2)
   bool good = true;
   if (wid >= 4) {
     const int q = wid & 3, h = (wid - 4) >> 2;
     const int row = 32 * q + lane;                    // tile row (TMEM lane)
     const int ga = ma * kOzM + row;                   // A row
-    long long Ih[16], Il[16];
+    long long G0[CPT], G1[CPT], G2[CPT];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) { Ih[k] = 0; Il[k] = 0; }
+    for (int k = 0; k < CPT; ++k) { G0[k] = 0; G1[k] = 0; G2[k] = 0; }
     for (int dr = 0; dr < ndrain && good; ++dr) {
       bool ready = false;
       const uint64_t t0 = global_ns();
@@ -407,15 +436,16 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
       good = __all_sync(0xffffffffu, ready);
       if (!good) break;
       tc_fence_after();
-      float v[16];
+      float v[CPT];
 #pragma unroll
-      for (int L = 0; L < kOzLevels; ++L) {
-        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(L * kOzN + 16 * h), v);
+      for (int L = 0; L < NL; ++L) {
+        tmem_ld<CPT>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(L * NT + CPT * h), v);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const long long I = (long long)__float2int_rn(v[k]);   // an integer below 2^24: exact
-          if (L < 4) Ih[k] += I * (long long)(1 << (8 * (3 - L)));
-          else Il[k] += I * (long long)(1 << (8 * (7 - L)));
+        for (int k = 0; k < CPT; ++k) {
+          const long long I = (long long)__float2int_rn(v[k]);   // an integer of magnitude <= 2^24: exact
+          if (L < 4) G0[k] += I * (long long)(1 << (8 * (3 - L)));
+          else if (L < 8) G1[k] += I * (long long)(1 << (8 * (7 - L)));
+          else G2[k] += I;
         }
       }
       tc_fence_before();
@@ -425,30 +455,32 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
     if (good) {
       const int ea = P.ea[ga];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int col = 16 * h + k;
-        const int eb = P.eb[nb * kOzN + col];
-        // sum_L I_L 256^-L = 2^-24 (Ih + 2^-32 Il): carry Il's high part into Ih (exact), then
-        // one rounding; the product is 2^(ea + eb - 14) times that sum
-        const long long hi = Ih[k] + (Il[k] >> 32);
-        const long long lo = Il[k] & 0xFFFFFFFFll;
-        double r = fma((double)lo, 0x1.0p-32, (double)hi);
+      for (int k = 0; k < CPT; ++k) {
+        const int col = CPT * h + k;
+        const int eb = P.eb[nb * NT + col];
+        // carry the low sums' high parts upwards (exact), then one rounding: G0 < 2^53,
+        // G1 + 2^-8 G2 < 2^32 is exact in FP64; the product is 2^(ea + eb - 38) times the sum
+        long long g1 = G1[k] + (G2[k] >> 8);
+        const long long g2 = G2[k] & 255ll;
+        const long long g0 = G0[k] + (g1 >> 32);
+        g1 &= 0xFFFFFFFFll;
+        double r = fma(fma((double)g2, 0x1.0p-8, (double)g1), 0x1.0p-32, (double)g0);
         const int sc = ea + eb - 38;
         if (ea <= -2000 || eb <= -2000) r = 0.0;
         else if (sc >= -1022 && sc <= 1023) r *= __longlong_as_double((long long)(sc + 1023) << 52);  // 2^sc
         else r = ldexp(r, sc);
         if (FWD) {
-          const int c = nb * kOzN + col;
+          const int c = nb * NT + col;
           const int i = ga >> 1, p = ga & 1;
           if (i < P.rows && c < P.cols) {
             double *dst = reinterpret_cast<double *>(P.C + (int64_t)c * P.ldc + i) + p;
             *dst -= r;
           }
         } else {
-          P.part[((int64_t)blockIdx.y * P.part_rows + ga) * kOzN + col] = r;
+          P.part[((int64_t)blockIdx.y * P.part_rows + ga) * 64 + nb * NT + col] = r;
         }
       }
-    } else if (!good) {
+    } else {
       atomicExch(&s_abort, 1);
     }
   }
@@ -458,8 +490,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
     // loads still in flight: the A tiles issued but not taken, the B tiles likewise (bounded)
     for (int q = s_a_used; q < s_a_issued; ++q) bar_wait(&a_full[q % kOzRing], (uint32_t)((q / kOzRing) & 1), P.limit_ns);
     for (int q = s_b_used; q < s_b_issued; ++q) {
-      const int kk = q / kOzSlices, t = q % kOzSlices;
-      bar_wait(&b_full[(kk & 1) * kOzSlices + t], (uint32_t)((kk >> 1) & 1), P.limit_ns);
+      const int kk = q / S, t = q % S;
+      bar_wait(&b_full[(kk & 1) * S + t], (uint32_t)((kk >> 1) & 1), P.limit_ns);
     }
     // products in flight: the last A tile's commit
     if (s_a_used > 0) {
@@ -492,12 +524,12 @@ PFN_cuTensorMapEncodeTiled_v12000 oz_encode() {
   return fn;
 }
 
-// the slices of an operand as a 2-D BF16 array (k_pad wide, kOzSlices rows_pad rows) read in
+// the slices of an operand as a 2-D BF16 array (k_pad wide, ns rows_pad rows) read in
 // boxes of 64 (K) x box_rows, 128-byte swizzle: the K-major layout the MMA descriptors expect
 cudaError_t oz_map(const OzOperand &o, uint32_t box_rows, CUtensorMap *map) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = oz_encode();
   if (!enc) return cudaErrorNotSupported;
-  const cuuint64_t gdim[2] = {(cuuint64_t)o.k_pad, (cuuint64_t)(kOzSlices * o.rows_pad)};
+  const cuuint64_t gdim[2] = {(cuuint64_t)o.k_pad, (cuuint64_t)(o.ns * o.rows_pad)};
   const cuuint64_t gstride[1] = {(cuuint64_t)(o.k_pad * sizeof(__nv_bfloat16))};
   const cuuint32_t box[2] = {kOzK, box_rows};
   const cuuint32_t es[2] = {1, 1};
@@ -512,8 +544,8 @@ int64_t pad_to(int64_t v, int64_t q) { return (v + q - 1) / q * q; }
 
 }  // namespace
 
-size_t oz_slice_bytes(int64_t rows, int64_t k) {
-  return (size_t)kOzSlices * (size_t)pad_to(rows, kOzM) * (size_t)pad_to(k, kOzK) * sizeof(__nv_bfloat16);
+size_t oz_slice_bytes(int64_t rows, int64_t k, int ns) {
+  return (size_t)ns * (size_t)pad_to(rows, kOzM) * (size_t)pad_to(k, kOzK) * sizeof(__nv_bfloat16);
 }
 
 cudaError_t launch_oz_slice_cols(const void *C, int64_t ldc, int64_t rows, int64_t cols, OzOperand &out,
@@ -522,6 +554,7 @@ cudaError_t launch_oz_slice_cols(const void *C, int64_t ldc, int64_t rows, int64
   out.rows_pad = pad_to(cols, kOzM);
   out.k = 2 * rows;
   out.k_pad = pad_to(2 * rows, kOzK);
+  out.ns = kOzSlicesAdj;
   if (cols < 1) return cudaSuccess;
   note_launch();
   oz_slice_cols_kernel<<<(unsigned)cols, 256, 0, st>>>((const zd *)C, ldc, rows, cols, (__nv_bfloat16 *)out.slices,
@@ -534,6 +567,7 @@ cudaError_t launch_oz_slice_v_adj(const void *V, int64_t ldv, int64_t rows, OzOp
   out.rows_pad = 64;
   out.k = 2 * rows;
   out.k_pad = pad_to(2 * rows, kOzK);
+  out.ns = kOzSlicesAdj;
   note_launch();
   oz_slice_v_adj_kernel<<<32, 256, 0, st>>>((const zd *)V, ldv, rows, (__nv_bfloat16 *)out.slices, out.expo,
                                             out.k_pad);
@@ -545,6 +579,7 @@ cudaError_t launch_oz_slice_v_fwd(const void *V, int64_t ldv, int64_t rows, OzOp
   out.rows_pad = pad_to(2 * rows, kOzM);
   out.k = kOzK;
   out.k_pad = kOzK;
+  out.ns = kOzSlicesFwd;
   const int64_t th = out.rows_pad / 2;
   note_launch();
   oz_slice_v_fwd_kernel<<<(unsigned)((th + 127) / 128), 128, 0, st>>>((const zd *)V, ldv, rows,
@@ -555,9 +590,10 @@ cudaError_t launch_oz_slice_v_fwd(const void *V, int64_t ldv, int64_t rows, OzOp
 
 cudaError_t launch_oz_slice_z(const void *Z, int64_t ldz, int64_t cols, OzOperand &out, cudaStream_t st) {
   out.rows = cols;
-  out.rows_pad = pad_to(cols, kOzN);
+  out.rows_pad = pad_to(cols, kOzNFwd);
   out.k = kOzK;
   out.k_pad = kOzK;
+  out.ns = kOzSlicesFwd;
   note_launch();
   oz_slice_z_kernel<<<(unsigned)((out.rows_pad + 127) / 128), 128, 0, st>>>((const zd *)Z, ldz, cols,
                                                                             (__nv_bfloat16 *)out.slices, out.expo,
@@ -571,7 +607,7 @@ cudaError_t launch_oz_slice_z(const void *Z, int64_t ldz, int64_t cols, OzOperan
 static int oz_adj_splits(int64_t rows, int64_t cols, int sms, int *kb_per) {
   const int64_t nkb = pad_to(2 * rows, kOzK) / kOzK;
   const int64_t mt = pad_to(cols, kOzM) / kOzM;
-  int64_t splits = std::max<int64_t>(1, sms / mt);
+  int64_t splits = std::max<int64_t>(1, sms / (2 * mt));   // two CTAs (halves of B) per M-tile
   splits = std::max<int64_t>(splits, (nkb + kOzKbMax - 1) / kOzKbMax);
   splits = std::min<int64_t>(splits, nkb);
   const int64_t per = (nkb + splits - 1) / splits;
@@ -580,28 +616,36 @@ static int oz_adj_splits(int64_t rows, int64_t cols, int sms, int *kb_per) {
 }
 
 // splits x padded rows of the partial sums, bounded for every rows <= l, cols <= m: the splits
-// are at most max(sms / mt, ceil(K-blocks / kOzKbMax)), so splits x mt <= max(sms, (K-blocks /
+// are at most max(sms / (2 mt), ceil(K-blocks / kOzKbMax)), so splits x mt <= max(sms, (K-blocks /
 // kOzKbMax + 1) mt)
 size_t oz_adj_partial_bytes(int64_t l, int64_t m, int sms) {
   const int64_t mt = pad_to(m, kOzM) / kOzM, nkb = pad_to(2 * l, kOzK) / kOzK;
   const int64_t tiles = std::max<int64_t>((int64_t)sms + mt, (nkb / kOzKbMax + 1) * mt);
-  return sizeof(double) * (size_t)tiles * kOzM * kOzN;
+  return sizeof(double) * (size_t)tiles * kOzM * 64;
 }
 
+// W[j, c] = conj(D[c][j] + i D[c][32 + j]) summed over the splits with a compensated (TwoSum)
+// sum: the result is the splits' exact sum rounded once, up to a second-order term, so the
+// splits add one rounding in all rather than one per split
+__device__ __forceinline__ void two_sum_acc(double &hi, double &lo, double x) {
+  const double t = hi + x;
+  const double z = t - hi;
+  lo += (hi - (t - z)) + (x - z);
+  hi = t;
+}
 __global__ void oz_adj_reduce_kernel(const double *__restrict__ part, int splits, int64_t rows_pad, int64_t cols,
                                      zd *__restrict__ W, int64_t ldw) {
-  // W[j, c] = conj(D[c][j] + i D[c][32 + j]) summed over the splits
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= cols * 32) return;
   const int64_t c = e / 32;
   const int j = (int)(e % 32);
-  double re = 0.0, im = 0.0;
+  double re = 0.0, re_lo = 0.0, im = 0.0, im_lo = 0.0;
   for (int s = 0; s < splits; ++s) {
-    const double *d = part + ((int64_t)s * rows_pad + c) * kOzN;
-    re += d[j];
-    im += d[32 + j];
+    const double *d = part + ((int64_t)s * rows_pad + c) * 64;
+    two_sum_acc(re, re_lo, d[j]);
+    two_sum_acc(im, im_lo, d[32 + j]);
   }
-  W[c * ldw + j] = {re, -im};
+  W[c * ldw + j] = {re + re_lo, -(im + im_lo)};
 }
 
 cudaError_t launch_oz_adj(const OzAdjArgs &a, cudaStream_t st) {
@@ -612,10 +656,11 @@ cudaError_t launch_oz_adj(const OzAdjArgs &a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   CUtensorMap amap, bmap;
   if ((e = oz_map(a.a, kOzM, &amap)) != cudaSuccess) return e;
-  if ((e = oz_map(a.b, kOzN, &bmap)) != cudaSuccess) return e;
+  if ((e = oz_map(a.b, kOzNAdj, &bmap)) != cudaSuccess) return e;
   int per = 0;
   const int splits = oz_adj_splits(a.a.k / 2, a.cols, sms, &per);
-  if (sizeof(double) * (size_t)splits * (size_t)a.a.rows_pad * kOzN > a.part_bytes) return cudaErrorInvalidValue;
+  if (sizeof(double) * (size_t)splits * (size_t)a.a.rows_pad * 64 > a.part_bytes) return cudaErrorInvalidValue;
+  if (a.a.ns != kOzSlicesAdj || a.b.ns != kOzSlicesAdj) return cudaErrorInvalidValue;
   OzParams P{};
   P.a_rows_pad = (int)a.a.rows_pad;
   P.b_rows_pad = (int)a.b.rows_pad;
@@ -627,12 +672,12 @@ cudaError_t launch_oz_adj(const OzAdjArgs &a, cudaStream_t st) {
   P.part_rows = (int)a.a.rows_pad;
   P.err = a.err;
   P.limit_ns = a.limit_ns;
-  if ((e = cudaFuncSetAttribute(oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem)) !=
-      cudaSuccess)
-    return e;
+  auto kern = oz_gemm_kernel<false, kOzSlicesAdj, kOzLevelsAdj, kOzNAdj>;
+  constexpr int smem = OzShape<kOzSlicesAdj, kOzNAdj>::kSmem;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
   note_launch();
-  oz_gemm_kernel<false><<<dim3((unsigned)(a.a.rows_pad / kOzM), (unsigned)splits), kOzThreads, kOzSmem, st>>>(
-      amap, bmap, P);
+  kern<<<dim3((unsigned)(a.a.rows_pad / kOzM), (unsigned)splits, 64u / kOzNAdj), kOzThreads, smem, st>>>(amap, bmap,
+                                                                                                      P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   note_launch();
   oz_adj_reduce_kernel<<<(unsigned)((a.cols * 32 + 255) / 256), 256, 0, st>>>(a.part, splits, a.a.rows_pad, a.cols,
@@ -645,7 +690,8 @@ cudaError_t launch_oz_fwd(const OzFwdArgs &a, cudaStream_t st) {
   cudaError_t e;
   CUtensorMap amap, bmap;
   if ((e = oz_map(a.a, kOzM, &amap)) != cudaSuccess) return e;
-  if ((e = oz_map(a.b, kOzN, &bmap)) != cudaSuccess) return e;
+  if ((e = oz_map(a.b, kOzNFwd, &bmap)) != cudaSuccess) return e;
+  if (a.a.ns != kOzSlicesFwd || a.b.ns != kOzSlicesFwd) return cudaErrorInvalidValue;
   OzParams P{};
   P.a_rows_pad = (int)a.a.rows_pad;
   P.b_rows_pad = (int)a.b.rows_pad;
@@ -658,12 +704,12 @@ cudaError_t launch_oz_fwd(const OzFwdArgs &a, cudaStream_t st) {
   P.cols = (int)a.cols;
   P.err = a.err;
   P.limit_ns = a.limit_ns;
-  if ((e = cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem)) !=
-      cudaSuccess)
-    return e;
+  auto kern = oz_gemm_kernel<true, kOzSlicesFwd, kOzLevelsFwd, kOzNFwd>;
+  constexpr int smem = OzShape<kOzSlicesFwd, kOzNFwd>::kSmem;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
   note_launch();
-  oz_gemm_kernel<true><<<dim3((unsigned)(a.a.rows_pad / kOzM), (unsigned)(a.b.rows_pad / kOzN)), kOzThreads, kOzSmem,
-                         st>>>(amap, bmap, P);
+  kern<<<dim3((unsigned)(a.a.rows_pad / kOzM), (unsigned)(a.b.rows_pad / kOzNFwd)), kOzThreads, smem, st>>>(amap, bmap,
+                                                                                                          P);
   return cudaGetLastError();
 }
 

@@ -195,10 +195,10 @@ __global__ void qr_copy_r1_kernel(const zd *__restrict__ Y, int64_t ldy, int m, 
 }
 
 void qrblk_sizes(int64_t l, int64_t m, int sms, size_t (&b)[18]) {
-  b[0] = oz_slice_bytes(m, 2 * l);          // sA: A rows from C's columns
-  b[1] = oz_slice_bytes(kOzN, 2 * l);       // sB: the reflectors, adjoint form
-  b[2] = oz_slice_bytes(2 * l, kOzK);       // sV: the reflectors, update form
-  b[3] = oz_slice_bytes(m, kOzK);           // sZ
+  b[0] = oz_slice_bytes(m, 2 * l, kOzSlicesAdj);         // sA: A rows from C's columns
+  b[1] = oz_slice_bytes(64, 2 * l, kOzSlicesAdj);        // sB: the reflectors, adjoint form
+  b[2] = oz_slice_bytes(2 * l, kOzK, kOzSlicesFwd);      // sV: the reflectors, update form
+  b[3] = oz_slice_bytes(m, kOzK, kOzSlicesFwd);          // sZ
   b[4] = sizeof(int32_t) * (size_t)qpad(m, kOzM);
   b[5] = sizeof(int32_t) * (size_t)kOzM;
   b[6] = sizeof(int32_t) * (size_t)qpad(2 * l, kOzM);
@@ -221,14 +221,14 @@ cudaError_t launch_trailing_products(QrBlkWork &w, const void *V, int64_t ldv, v
   if (rows > w.l || cols > w.m) return cudaErrorInvalidValue;
   cudaError_t e;
   if (W) {
-    OzOperand a{w.sA, w.eA, 0, 0, 0, 0}, b{w.sB, w.eB, 0, 0, 0, 0};
+    OzOperand a{w.sA, w.eA, 0, 0, 0, 0, 0}, b{w.sB, w.eB, 0, 0, 0, 0, 0};
     if ((e = launch_oz_slice_cols(C, ldc, rows, cols, a, st)) != cudaSuccess) return e;
     if ((e = launch_oz_slice_v_adj(V, ldv, rows, b, st)) != cudaSuccess) return e;
     OzAdjArgs g{a, b, w.part, w.part_bytes, W, 32, cols, err, limit_ns};
     if ((e = launch_oz_adj(g, st)) != cudaSuccess) return e;
   }
   if (Z) {
-    OzOperand a{w.sV, w.eV, 0, 0, 0, 0}, b{w.sZ, w.eZ, 0, 0, 0, 0};
+    OzOperand a{w.sV, w.eV, 0, 0, 0, 0, 0}, b{w.sZ, w.eZ, 0, 0, 0, 0, 0};
     if ((e = launch_oz_slice_v_fwd(V, ldv, rows, a, st)) != cudaSuccess) return e;
     if ((e = launch_oz_slice_z(Z, ldz, cols, b, st)) != cudaSuccess) return e;
     OzFwdArgs g{a, b, C, ldc, rows, cols, err, limit_ns};

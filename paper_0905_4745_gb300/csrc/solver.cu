@@ -477,14 +477,19 @@ minnorm_status upload_params(minnorm_plan_t plan) {
   }
   // Householder QR (FP64): backward error within 8 m (d + 4) 2^-53 ||Y||_F, d the depth of its
   // dot products' sums (a thread's run of rows plus the warp, block and grid trees). The blocked
-  // form adds its two QRs' bounds: the l x m one, whose panel sums have depth l / (8 G) + 8 + G
-  // and whose tensor-core products err by at most 2^-52 sqrt(K) ||v|| ||c|| (K = 2l: depth
-  // sqrt(2l) in this form), then the m x m pivoted one.
+  // form adds its two QRs' bounds: the l x m one, then the m x m pivoted one. In the l x m one a
+  // panel's sums have depth at most max(l / (8 G), 2) + 1 (a thread's rows) + 8 (the block's
+  // warps) + G / 8 + 8 (the grid's partials) + 2 (the reflector's scalars), G <= sms; the adjoint
+  // trailing product of complex length K <= l errs by at most 2^-53 (2 sqrt(K) / 256 + K / 4096 +
+  // 4) ||v|| ||c|| (63-bit operand truncation; the dropped slice levels, K 2^-65.9 max|v| max|c|;
+  // the roundings of the K splits and of their compensated sum, 2^-51.5 |v|^T |c|), and the
+  // K = 32 update by at most 24 more units.
   if (plan->qr_blocked) {
-    const double G = plan->sms;
-    const double d1 = (double)l / (8.0 * G) + 8.0 + G + 2.0 * std::sqrt(2.0 * (double)l);
+    const double G = plan->sms, L = (double)l;
+    const double d_panel = std::max(L / (8.0 * G), 2.0) + 1.0 + 8.0 + G / 8.0 + 8.0 + 2.0;
+    const double d_prod = 2.0 * std::sqrt(L) / 256.0 + L / 4096.0 + 4.0 + 24.0;
     const double d2 = (double)((plan->m + 127) / 128 + 20);
-    plan->eps_qr = 8.0 * (double)plan->m * (d1 + d2 + 8.0) * 0x1.0p-53;
+    plan->eps_qr = 8.0 * (double)plan->m * (d_panel + d_prod + d2 + 8.0) * 0x1.0p-53;
   } else {
     plan->eps_qr = 8.0 * (double)plan->m * (double)((l + 127) / 128 + 20) * 0x1.0p-53;
   }
@@ -1309,7 +1314,7 @@ minnorm_status solve_async_body(minnorm_plan_t plan, const void *A, const void *
       a.w = plan->d_w;
       a.t = plan->d_t;
       a.dy = plan->d_dy;
-      a.tpart = plan->d_tpart;
+        a.tpart = plan->d_tpart;
       a.qq_part = plan->d_qqp;
       a.gg_part = plan->d_ggp;
       a.sc = plan->d_cg;

@@ -2,21 +2,23 @@
 W = V^H C and C - V Z, against double-double references from the oracle (Dot2 sums:
 oracle.adj_matvec_dd / matvec_dd), element by element.
 
-Tolerance, from the arithmetic: every operand entry is truncated to 55 bits below its row's
-scale 2^e (the least power of two above the row's largest entry component), an absolute error
-below 2^(e - 55) <= 2^-54 max|row| per real component. A complex result is two real products
-of the interleaved real forms, whose sums of moduli are at most sqrt 2 times the complex ones,
-so the truncation adds at most 2^-53 (max|V_:j| sum|C_:c| + max|C_:c| sum|V_:j|). The slice
-pairs beyond level 7 are dropped: at most 5.02 2^-64 2^(e+f) <= 2^-59.3 max|v| max|c| per real
-term, so (2 K real terms, sqrt 2 for the modulus) 2^-57.8 K max|V_:j| max|C_:c| for complex
-length K. The kept levels are summed exactly and rounded once to FP64 per K split, the splits
-added in FP64: 2^-53 (splits + 1) |V|^T |C| per component. So
-  |W_jc - W_ref| <= 2^-53 (max|V_:j| sum|C_:c| + max|C_:c| sum|V_:j|) + 2^-57 K max|V_:j| max|C_:c|
-                    + 2^-52 (splits + 1) |V|^T|C|,
-checked with a factor 2 of slack; normwise this is within 2^-51 sqrt(K) ||v_j|| ||c_c||, the
-order of an FP64 dot product's own a-priori bound (2K 2^-53 ||v|| ||c||). Cases: one K range and
-several (split K, summed in FP64; odd K-block counts), ragged tile edges, rows and columns of
-very different scales, zero rows and columns."""
+Tolerance, from the arithmetic. The adjoint product truncates every operand entry to 63 bits
+below its row's scale 2^e (the least power of two above the row's largest entry component):
+an absolute error below 2^(e - 63) <= 2^-62 max|row| per real component. A complex result is
+two real products of the interleaved real forms, whose sums of moduli are at most sqrt 2 times
+the complex ones, so the truncation adds at most 2^-61 (max|V_:j| sum|C_:c| + max|C_:c|
+sum|V_:j|). The slice pairs beyond level 8 are dropped: at most 6.02 2^-72 2^(e+f) <= 2^-67.4
+max|v| max|c| per real term, so (2 K real terms, sqrt 2 for the modulus) 2^-65.9 K max|V_:j|
+max|C_:c| for complex length K. The kept levels are summed exactly and rounded once to FP64 per
+K split, and the splits added by a compensated sum (their exact sum rounded once): at most
+2^-53 (|V|^T|C| + |W|) <= 2^-52 |V|^T|C| per component. So
+  |W_jc - W_ref| <= 2^-61 (max|V_:j| sum|C_:c| + max|C_:c| sum|V_:j|) + 2^-65 K max|V_:j| max|C_:c|
+                    + 2^-51 |V|^T|C|,
+checked with a factor 2 of slack: as accurate as an FP64 dot product at any K. The update
+(K = 32) truncates to 55 bits and drops the levels beyond 7: 2^-53 (max|V_i:| sum|Z_:c| +
+max|Z_:c| sum|V_i:|) + 2^-57 32 max|V_i:| max|Z_:c|, plus the roundings of the product and of the
+subtraction. Cases: one K range and several (split K; odd K-block counts), ragged tile edges,
+rows and columns of very different scales, zero rows and columns."""
 import numpy as np
 import pytest
 
@@ -68,16 +70,15 @@ def test_trailing_products_against_double_double(mn, rows, cols, m, n):
         W, Cn = Wt.cpu().numpy(), Ct.cpu().numpy()
     finally:
         mn.minnorm_plan_destroy(plan)
-    # W = V^H C against Dot2 sums; the library splits K into at most one split per 64 real terms
-    splits = -(-2 * rows // 64)
+    # W = V^H C against Dot2 sums (the library's K splits are added by a compensated sum)
     absV, absC = np.abs(V), np.abs(C)
     mV, sV = absV.max(axis=0), absV.sum(axis=0)      # per reflector column j
     for c in range(cols):
         xh, xl = oracle.adj_matvec_dd(V, np.ascontiguousarray(C[:, c]))
         ref = xh + xl
         mC, sC = absC[:, c].max(), absC[:, c].sum()
-        tol = 2.0 * (2.0 ** -53 * (mV * sC + mC * sV) + 2.0 ** -57 * rows * mV * mC
-                     + 2.0 ** -52 * (splits + 1) * (absV.T @ absC[:, c]))
+        tol = 2.0 * (2.0 ** -61 * (mV * sC + mC * sV) + 2.0 ** -65 * rows * mV * mC
+                     + 2.0 ** -51 * (absV.T @ absC[:, c]))
         err = np.abs(W[:, c] - ref)
         assert np.all(err <= tol), (c, np.max(err / np.maximum(tol, 1e-300)))
     # C - V Z against Dot2 sums
