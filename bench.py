@@ -56,7 +56,11 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.0
 # so traffic is one read of Y.
 PROFILED_TRAFFIC = {("c2", 3): 21.82e6}
 KERNEL_CLASSES = {0: "cg_adjoint_product", 1: "cg_forward_product", 2: "exact_residual", 3: "pivoted_qr",
-                  4: "srft_sketch", 5: "cg_fused"}
+                  4: "srft_sketch", 5: "cg_fused", 6: "qrp_triangle", 7: "r_inverse"}
+# the blocked QR of tall sketches (l > 2048) does its trailing updates as FP64-accurate products on
+# the tensor cores: 43 (adjoint) and 34 (update) BF16 slice-pair products per FP64 multiply-add,
+# the two products carrying equal flops, so its FP64-equivalent peak is the BF16 peak / 38.5
+OZAKI_MEAN_PAIRS = 38.5
 REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
                0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
@@ -271,8 +275,12 @@ def class_amount(k, m, n, l, launches):
         return launches * 8.0 * m * n, "GB/s", "hbm"
     if k == 2:             # x = A^* y and b - A x over the 16-byte fixed-point A
         return launches * 2 * 16.0 * m * n, "GB/s", "alu"
-    if k == 3:             # pivoted QR + P R^-1
-        return launches * (8.0 * m * m * (l - m / 3.0) + 8.0 * m ** 3 / 6.0), "TFLOP/s", "alu"
+    if k == 3:             # the QR of Y: FP64 (l <= 2048) or blocked with tensor-core products
+        return launches * 8.0 * m * m * (l - m / 3.0), "TFLOP/s", "tensor" if l > 2048 else "alu"
+    if k == 6:             # the pivoted QR of the m x m triangle
+        return launches * 16.0 * m ** 3 / 3.0, "TFLOP/s", "alu"
+    if k == 7:             # P R^-1
+        return launches * 8.0 * m ** 3 / 6.0, "TFLOP/s", "alu"
     return launches * (8.0 * m * n + 16.0 * l * m), "GB/s", "hbm"   # sketch: read A once, write Y
 
 
@@ -297,6 +305,10 @@ def side_roofline(shapes, stats_of, pk):
         peak, src = pk["hbm_gbs"], "measured HBM copy"
         if dom == 2:   # integer-ALU bound: report the bytes rate against HBM for scale
             src = "measured HBM copy (the pass is integer-ALU bound)"
+    elif bound == "tensor":
+        achieved = amount / (ms / 1000.0) / 1e12
+        peak = pk["bf16_tflops"] / OZAKI_MEAN_PAIRS
+        src = "FP64-equivalent: measured BF16 peak / %.1f slice pairs" % OZAKI_MEAN_PAIRS
     else:
         achieved = amount / (ms / 1000.0) / 1e12
         peak, src = FP64_NOMINAL_TFLOPS, "FP64 from unit counts and clock"
@@ -643,10 +655,11 @@ def main():
         flops = 2 * m * n * 50          # two passes, ~50 FP64 flops per complex element (TwoProd/TwoSum)
         achieved = flops / (per_launch_ms / 1000.0) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s"}
-    elif dom == 3:
-        flops = 8.0 * m * m * (l - m / 3.0) + 8.0 * m ** 3 / 6.0
+    elif dom in (3, 6, 7):
+        flops, _, bound = class_amount(dom, m, n, l, 1)
         achieved = flops / (per_launch_ms / 1000.0) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s"}
+        peak = pk["bf16_tflops"] / OZAKI_MEAN_PAIRS if bound == "tensor" else FP64_NOMINAL_TFLOPS
+        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s"}
     else:
         bytes_per = m * n * esz + 16 * l * m
         achieved = bytes_per / (per_launch_ms / 1000.0) / 1e9
@@ -655,6 +668,8 @@ def main():
     roof["traffic"] = PROFILED_TRAFFIC.get((args.workload, dom)) if full else None
     roof["kernel"] = KERNEL_CLASSES[dom]
     roof["peak_source"] = (pk_kind if roof["unit"] == "GB/s" else
+                           "FP64-equivalent: %s BF16 peak / %.1f slice pairs" % (pk_kind, OZAKI_MEAN_PAIRS)
+                           if roof["bound"] == "tensor" else
                            "derived, not measured: FP64 from unit counts and clock, 152 SMs x 2 DFMA/clk x 2 "
                            "x 2.07 GHz (recipe table 1.25 TFLOP/s)")
     # CG matvec bandwidth (the metric's second half)

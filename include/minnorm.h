@@ -350,10 +350,13 @@ int64_t minnorm_launch_count(void);
 
 /* Kernel timing since the last minnorm_sketch when the plan has
  * MINNORM_FLAG_TIMING: for kernel class k (0: CG product A^* w, 1: CG product
- * A q, 2: an exact residual (x = A^* y and b - A x), 3: QR and P R^{-1},
- * 4: sketch (both chains and the FFT), 5: fused CG solves) the number of
- * timed regions (for k = 5: the CG iterations run inside them) and their
- * summed milliseconds (CUDA events on the plan's stream). Errors: EINVAL. */
+ * A q, 2: an exact residual (x = A^* y and b - A x), 3: the QR of Y (the
+ * pivoted QR when l <= 2048; for taller sketches the blocked QR without
+ * pivoting), 4: sketch (both chains and the FFT), 5: fused CG solves, 6: the
+ * pivoted QR of the m x m triangle (taller sketches only), 7: P R^{-1}) the
+ * number of timed regions (for k = 5: the CG iterations run inside them) and
+ * their summed milliseconds (CUDA events on the plan's stream). Errors: EINVAL
+ * (k outside 0..7). */
 minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *launches, double *ms);
 
 /* ------------------------------------------------------------------------

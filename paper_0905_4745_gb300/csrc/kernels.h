@@ -254,6 +254,10 @@ void qrblk_sizes(int64_t l, int64_t m, int sms, size_t (&bytes)[18]);
 // its m x m triangle (launch_qrp with the arguments of q); the pivots and R are those of the
 // pivoted QR of Y (R up to a unit diagonal)
 cudaError_t launch_qr_blocked(QrBlkWork &w, const QrArgs &q, int sms, cudaStream_t st);
+// its two parts: the blocked QR of Y without pivoting (R1 into the workspace), and the pivoted
+// QR of the m x m triangle R1
+cudaError_t launch_qr_tall(QrBlkWork &w, const QrArgs &q, int sms, cudaStream_t st);
+cudaError_t launch_qr_triangle(QrBlkWork &w, const QrArgs &q, cudaStream_t st);
 // rows of a panel one CTA may hold in shared memory; the blocked QR needs l <= kPanelMaxRows * sms
 constexpr int kPanelMaxRows = 384;
 int qrblk_panel_grid(int64_t L, int sms);

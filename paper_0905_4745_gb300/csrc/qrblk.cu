@@ -244,10 +244,10 @@ int qrblk_panel_grid(int64_t L, int sms) {
   return (L + g - 1) / g <= kPanelMaxRows ? (int)g : 0;
 }
 
-// Y P = Q R for the l x m sketch Y (column-major, ld l, overwritten): blocked Householder QR of
-// Y without pivoting (panels of 32 columns, trailing updates on the tensor cores), then the
-// pivoted QR of the m x m triangle R1 with the arguments of q (its Y replaced by R1).
-cudaError_t launch_qr_blocked(QrBlkWork &w, const QrArgs &q, int sms, cudaStream_t st) {
+// Y = Q1 R1 for the l x m sketch Y (column-major, ld l, overwritten): blocked Householder QR
+// of Y without pivoting (panels of 32 columns, trailing updates on the tensor cores); R1 (the
+// upper triangle) into the workspace.
+cudaError_t launch_qr_tall(QrBlkWork &w, const QrArgs &q, int sms, cudaStream_t st) {
   const int64_t l = q.l, m = q.m;
   if (l > w.l || m > w.m || l < m) return cudaErrorInvalidValue;
   zd *Y = static_cast<zd *>(q.Y);
@@ -288,11 +288,21 @@ cudaError_t launch_qr_blocked(QrBlkWork &w, const QrArgs &q, int sms, cudaStream
   }
   note_launch();
   qr_copy_r1_kernel<<<(unsigned)((m * m + 255) / 256), 256, 0, st>>>(Y, l, (int)m, static_cast<zd *>(w.R1));
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// R1 P = Q2 R: the pivoted QR of the m x m triangle with the arguments of q (its Y replaced by R1)
+cudaError_t launch_qr_triangle(QrBlkWork &w, const QrArgs &q, cudaStream_t st) {
   QrArgs q2 = q;
   q2.Y = w.R1;
-  q2.l = (int)m;
+  q2.l = q.m;
   return launch_qrp(q2, st);
+}
+
+// Y P = Q R: launch_qr_tall, then launch_qr_triangle
+cudaError_t launch_qr_blocked(QrBlkWork &w, const QrArgs &q, int sms, cudaStream_t st) {
+  cudaError_t e = launch_qr_tall(w, q, sms, st);
+  return e != cudaSuccess ? e : launch_qr_triangle(w, q, st);
 }
 
 }  // namespace mn

@@ -63,6 +63,9 @@ struct ScratchPool {
   size_t s_bytes = 0, afix_bytes = 0, a32_bytes = 0;
 };
 
+// kernel classes of minnorm_kernel_stats (see minnorm.h)
+constexpr int kNumClasses = 8;
+
 struct minnorm_plan_s {
   const ScratchPool *pool = nullptr;  // if set, S1, S2, afix and A32 point into it
   int64_t m = 0, n = 0, l = 0;
@@ -187,8 +190,8 @@ struct minnorm_plan_s {
   std::vector<KernelTimer> timers;
   std::vector<cudaEvent_t> event_pool;
   size_t event_next = 0;
-  int stat_launches[6] = {0, 0, 0, 0, 0, 0};
-  double stat_ms[6] = {0, 0, 0, 0, 0, 0};
+  int stat_launches[kNumClasses] = {};
+  double stat_ms[kNumClasses] = {};
   float ms_sketch = 0, ms_qr = 0, ms_solve = 0;
   int fused_iters = 0;
   std::vector<void *> allocs;
@@ -277,7 +280,7 @@ struct Timed {
 };
 
 void reset_stats(minnorm_plan_t plan) {
-  for (int k = 0; k < 6; ++k) { plan->stat_launches[k] = 0; plan->stat_ms[k] = 0; }
+  for (int k = 0; k < kNumClasses; ++k) { plan->stat_launches[k] = 0; plan->stat_ms[k] = 0; }
   plan->fused_iters = 0;
 }
 
@@ -719,13 +722,20 @@ minnorm_status sketch_transform(minnorm_plan_t plan, const void *A, int64_t lda)
 minnorm_status sketch_factor(minnorm_plan_t plan) {
   cudaStream_t st = plan->st;
   const int64_t m = plan->m, l = plan->l;
+  QrArgs q{plan->d_Y, (int)l, (int)m, plan->d_vn1, plan->d_vn2, plan->d_beta, plan->d_piv, plan->d_R,
+           plan->d_qrmail, plan->d_err, plan->wait_limit_ns};
   {
     Timed tm(plan, 3);
     CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
-    QrArgs q{plan->d_Y, (int)l, (int)m, plan->d_vn1, plan->d_vn2, plan->d_beta, plan->d_piv, plan->d_R,
-             plan->d_qrmail, plan->d_err, plan->wait_limit_ns};
-    if (plan->qr_blocked) CK(launch_qr_blocked(plan->qb, q, plan->sms, st));
+    if (plan->qr_blocked) CK(launch_qr_tall(plan->qb, q, plan->sms, st));
     else CK(launch_qrp(q, st));
+  }
+  if (plan->qr_blocked) {
+    Timed tm(plan, 6);
+    CK(launch_qr_triangle(plan->qb, q, st));
+  }
+  {
+    Timed tm(plan, 7);
     CK(launch_prinv(plan->d_R, plan->d_piv, (int)m, plan->d_Wp, plan->d_WpH, st));
     // ||R||_F, ||P R^{-1}||_F and ||A||_F for the certificate's delta
     CK(launch_sumsq(m * m, plan->d_R, plan->d_red, plan->d_cert, st));
@@ -2080,7 +2090,7 @@ minnorm_status minnorm_plan_tuning(minnorm_plan_t plan, int32_t *x_chunks, int32
 }
 
 minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *launches, double *ms) {
-  if (!plan || k < 0 || k > 5 || !launches || !ms) return MINNORM_EINVAL;
+  if (!plan || k < 0 || k >= kNumClasses || !launches || !ms) return MINNORM_EINVAL;
   *launches = k == 5 ? plan->fused_iters : plan->stat_launches[k];
   *ms = plan->stat_ms[k];
   return MINNORM_OK;
@@ -2261,7 +2271,7 @@ minnorm_status minnorm_batch_solve(minnorm_batch_t batch, const void *const *A, 
 
 minnorm_status minnorm_batch_kernel_stats(minnorm_batch_t batch, int32_t system, int32_t k, int32_t *launches,
                                           double *ms) {
-  if (!batch || !launches || !ms || k < 0 || k > 5) return MINNORM_EINVAL;
+  if (!batch || !launches || !ms || k < 0 || k >= kNumClasses) return MINNORM_EINVAL;
   if (system < -1 || system >= (int32_t)batch->plans.size()) return MINNORM_EINVAL;
   int32_t nl = 0;
   double t = 0.0;
