@@ -98,8 +98,10 @@ qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ld
     const int par = j & 1;
     if (!grid_sync(bar, G, epoch, limit_ns)) { if (tid == 0) atomicExch(err, 1); return; }
     {
+      // slots i < j (the dots e_i of the earlier reflectors) are needed by CTA 0 alone (for T)
       zd a = {0.0, 0.0};
-      for (int q = wid; q < G; q += kPanelWarps) a = a + ldcg(part + ((int64_t)par * G + q) * kPanel + lane);
+      if (b == 0 || lane >= j)
+        for (int q = wid; q < G; q += kPanelWarps) a = a + ldcg(part + ((int64_t)par * G + q) * kPanel + lane);
       s_acc[wid][lane] = a;
       if (wid == 0) s_row[lane] = ldcg(rowb + par * kPanel + lane);
     }
@@ -150,16 +152,25 @@ qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ld
     // the own rows r >= j: P[r, c] -= conj(tau) d_c v_r (c > j; the lanes past jb have d = 0),
     // column j becomes v (beta on the diagonal)
     const zd f = lane > j ? conjg(tj) * s_d[lane] : zd{0.0, 0.0};
-    for (int rr = max(r0, j) - r0 + wid; rr < nr; rr += kPanelWarps) {
-      const int r = r0 + rr;
-      zd *row = s_P + rr * kPanelLd;
-      const zd x = row[j];
-      const zd v = r == j ? zd{1.0, 0.0} : x * sc;
-      zd p = row[lane];
-      p = p - f * v;
-      if (lane == j) p = r == j ? zd{s_scal[0], 0.0} : v;
-      __syncwarp();
-      row[lane] = p;
+    // the warp's rows in batches of 32: v_r = s x_r (1 on row j) is formed once per row, by the
+    // lane of the row's place in the batch, and broadcast (an FP64 instruction holds the pipe
+    // for the whole warp, whatever its active lanes)
+    const int rs = max(r0, j) - r0 + wid;
+    for (int rb = rs; rb < nr; rb += 32 * kPanelWarps) {
+      const int rl = rb + kPanelWarps * lane;
+      zd vl = {0.0, 0.0};
+      if (rl < nr) vl = r0 + rl == j ? zd{1.0, 0.0} : s_P[rl * kPanelLd + j] * sc;
+      const int cnt = min(32, (nr - rb + kPanelWarps - 1) / kPanelWarps);
+      for (int t = 0; t < cnt; ++t) {
+        const int rr = rb + kPanelWarps * t;
+        const int r = r0 + rr;
+        zd *row = s_P + rr * kPanelLd;
+        const zd v = shfl_zd(vl, t);
+        zd p = row[lane];
+        p = p - f * v;
+        if (lane == j) p = r == j ? zd{s_scal[0], 0.0} : v;
+        row[lane] = p;
+      }
     }
     __syncthreads();
     if (j + 1 < jb) post(j + 1);

@@ -87,17 +87,19 @@ __device__ __forceinline__ cx<R> block_reverse_carry(R P, cx<R> Q, R *sP, cx<R> 
 //   out = Theta v                                          (chain of Eq. big_def)
 //   dst[row, j] = (post ? post[j] : 1) * out_j
 template <typename R, typename S, bool CONJ, bool POST>
-__global__ void __launch_bounds__(kChainThreads)
+__global__ void __launch_bounds__(kChainThreads, 3)
 chain_kernel(const S *__restrict__ src, int64_t ld_src, cx<R> *__restrict__ dst, int64_t ld_dst,
              const int32_t *__restrict__ idx, const cx<R> *__restrict__ phase,
              const cx<R> *__restrict__ cs, const cx<R> *__restrict__ post,
              const int32_t *__restrict__ halo, int n, int seg, int cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // V holds the gathered inputs, then (second scan pass, in place) the outputs: output o of the
+  // segment at V[o - off], off = 1 for the first segment (whose out_0 is kept in s_out0)
   cx<R> *V = reinterpret_cast<cx<R> *>(smem_raw);
   cx<R> *CS = V + cap;
-  cx<R> *OUT = CS + cap;
   __shared__ R sP[kChainThreads / 32];
   __shared__ cx<R> sQ[kChainThreads / 32];
+  __shared__ cx<R> s_out0;
 
   const int g = blockIdx.x;
   const int64_t row = blockIdx.y;
@@ -111,7 +113,7 @@ chain_kernel(const S *__restrict__ src, int64_t ld_src, cx<R> *__restrict__ dst,
   // the gather is latency-bound: issue the index loads, then the gathered loads, of several
   // elements per thread before using any of them
   // (the phase and rotation loads do not depend on the gather: they go with the index loads)
-  constexpr int kG = 8;
+  constexpr int kG = 4;
   for (int t0 = threadIdx.x; t0 < cnt; t0 += kG * blockDim.x) {
     int ix[kG];
     cx<R> ph[kG], rc[kG];
@@ -150,20 +152,21 @@ chain_kernel(const S *__restrict__ src, int64_t ld_src, cx<R> *__restrict__ dst,
     P *= c.im;
   }
   cx<R> C = block_reverse_carry<R>(P, Q, sP, sQ);
+  const int off = lo + 1 - j0;  // 1 for the first segment, else 0
   for (int t = a1 - 1; t >= a0; --t) {
     const cx<R> c = CS[t];
     const cx<R> v = V[t];
-    const int k = lo + t;  // element index; C holds C_{k+1}
-    const int o = k + 1 - j0;
-    if (o >= 0 && o < len) OUT[o] = {fma(c.re, C.re, -c.im * v.re), fma(c.re, C.im, -c.im * v.im)};
+    // element k = lo + t; C holds C_{k+1}; output o = k + 1 - j0 = t + off goes to V[t] (this
+    // thread has just read V[t]; no other thread touches its run of V in this pass)
+    if (t < len - off) V[t] = {fma(c.re, C.re, -c.im * v.re), fma(c.re, C.im, -c.im * v.im)};
     C = {fma(c.im, C.re, c.re * v.re), fma(c.im, C.im, c.re * v.im)};
   }
-  if (j0 == 0 && a0 == 0 && a1 > a0) OUT[0] = C;  // out_0 = C_0
+  if (j0 == 0 && a0 == 0 && a1 > a0) s_out0 = C;  // out_0 = C_0
   __syncthreads();
 
   cx<R> *drow = dst + row * ld_dst;
   for (int t = threadIdx.x; t < len; t += blockDim.x) {
-    cx<R> o = OUT[t];
+    cx<R> o = (off == 1 && t == 0) ? s_out0 : V[t - off];
     if (POST) o = o * post[j0 + t];
     drow[j0 + t] = o;
   }
@@ -392,7 +395,7 @@ __global__ void widen_kernel(int64_t len, const zf *__restrict__ src, zd *__rest
 // ---- host launchers -----------------------------------------------------
 template <typename R, typename S, bool CONJ, bool POST>
 static cudaError_t launch_chain_t(const ChainArgs &a, cudaStream_t st) {
-  const size_t smem = sizeof(cx<R>) * (size_t)(2 * a.cap + a.seg);
+  const size_t smem = sizeof(cx<R>) * (size_t)(2 * a.cap);
   cudaError_t e = cudaFuncSetAttribute(chain_kernel<R, S, CONJ, POST>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
