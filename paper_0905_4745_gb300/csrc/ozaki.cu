@@ -234,7 +234,7 @@ struct OzParams {
   // adjoint: partial sums part[split][row][64]
   double *part;
   int part_rows;
-  // update: C[i, c] -= D for i < rows, c < cols
+  // update: C[i, c] -= (V Z)[i, c] for i < rows, c < cols
   zd *C;
   int64_t ldc;
   int rows, cols;
@@ -272,19 +272,19 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[C]) {
   for (int k = 0; k < C; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// Tile: A rows [128 ma, +128), B rows [NT nb, +NT), K-blocks [kb0, kb1). Adjoint: grid
-// (A tiles, K splits, 2 halves of B), update: grid (A tiles, B tiles), one K-block. S slices,
-// the levels s + t < NL kept.
+// The adjoint product W^H = C^H V. Tile: A rows [128 ma, +128), B rows [NT nb, +NT), K-blocks
+// [kb0, kb1); grid (A tiles, K splits, B tiles). S slices, the levels s + t < NL kept; the FP64
+// partial sums of a K split go to part[split][A row][64].
 // Roles: warp 0 lane 0 issues the TMA loads (the S B slice tiles of a K-block into one of two
 // sets, the A slice tiles through a 6-deep ring); warp 1 runs the product loop converged, one
 // elected lane issuing the MMAs and the commits that free the tiles; warp 2 owns the tensor
 // memory; warps 4-19 drain the NL level accumulators every kOzDrain K-blocks (warp w reads TMEM
 // lanes 32 (w & 3) + lane = tile rows, columns NT/4 ((w - 4) >> 2) + 0..NT/4-1) and write the
 // result.
-template <bool FWD, int S, int NL, int NT>
+template <int S, int NL, int NT>
 __global__ void __launch_bounds__(kOzThreads, 1)
-oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
-               const OzParams P) {
+oz_adj_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
+              const OzParams P) {
   using SH = OzShape<S, NT>;
   static_assert(NL * NT <= kOzTmemCols && NL <= 9 && NL >= S, "levels x columns within tensor memory");
   constexpr int CPT = NT / 4;                       // columns per epilogue thread
@@ -305,9 +305,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
 
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const int ma = blockIdx.x;
-  const int nb = FWD ? blockIdx.y : blockIdx.z;
-  const int kb0 = FWD ? 0 : blockIdx.y * P.kb0_stride;
-  const int kb1 = FWD ? 1 : min(P.nkb, kb0 + P.kb0_stride);
+  const int nb = blockIdx.z;
+  const int kb0 = blockIdx.y * P.kb0_stride;
+  const int kb1 = min(P.nkb, kb0 + P.kb0_stride);
   const int nkb = kb1 - kb0;
   const int ndrain = (nkb + kOzDrain - 1) / kOzDrain;
 
@@ -469,16 +469,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
         if (ea <= -2000 || eb <= -2000) r = 0.0;
         else if (sc >= -1022 && sc <= 1023) r *= __longlong_as_double((long long)(sc + 1023) << 52);  // 2^sc
         else r = ldexp(r, sc);
-        if (FWD) {
-          const int c = nb * NT + col;
-          const int i = ga >> 1, p = ga & 1;
-          if (i < P.rows && c < P.cols) {
-            double *dst = reinterpret_cast<double *>(P.C + (int64_t)c * P.ldc + i) + p;
-            *dst -= r;
-          }
-        } else {
-          P.part[((int64_t)blockIdx.y * P.part_rows + ga) * 64 + nb * NT + col] = r;
-        }
+        P.part[((int64_t)blockIdx.y * P.part_rows + ga) * 64 + nb * NT + col] = r;
       }
     } else {
       atomicExch(&s_abort, 1);
@@ -497,6 +488,234 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
     if (s_a_used > 0) {
       const int q = s_a_used - 1;
       bar_wait(&a_empty[q % kOzRing], (uint32_t)((q / kOzRing) & 1), P.limit_ns);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (wid == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kOzTmemCols) : "memory");
+  }
+}
+
+// The update C -= V Z as a persistent kernel. CTA g takes the A row tiles (128 rows of the real
+// form of V) g, g + G, ...: a row tile's S A slices are loaded once and stay in shared memory
+// while the 32-column tiles of Z stream through two B buffers; the level accumulators of a column
+// tile (8 levels x 32 TMEM columns) alternate between the two halves of tensor memory, so the
+// epilogue of one column tile overlaps the products of the next. Roles as in oz_adj_kernel
+// (warp 0 loads, warp 1 multiplies, warp 2 owns tensor memory, warps 4-19 drain and write).
+constexpr int kOzFwdNT = 32;
+struct OzFwdShape {
+  static constexpr int kBTile = kOzFwdNT * kOzK * 2;                  // 4 KB
+  static constexpr int kOffB = kOzSlicesFwd * kOzATile;               // 112 KB: the row tile's A slices
+  static constexpr int kOffBar = kOffB + 2 * kOzSlicesFwd * kBTile;   // + 56 KB: two sets of B slices
+  static constexpr int kSmem = kOffBar + 256 + 1024;
+};
+
+__global__ void __launch_bounds__(kOzThreads, 1)
+oz_fwd_persistent_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
+                         const OzParams P, int n_row_tiles, int n_col_tiles) {
+  constexpr int S = kOzSlicesFwd, NL = kOzLevelsFwd, NT = kOzFwdNT, CPT = NT / 4;
+  static_assert(2 * NL * NT <= kOzTmemCols, "two accumulator sets in tensor memory");
+  using SH = OzFwdShape;
+  extern __shared__ unsigned char oz_smem_raw[];
+  unsigned char *base = (unsigned char *)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *sA = base;
+  unsigned char *sB = base + SH::kOffB;               // [2][S] tiles
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + SH::kOffBar);
+  uint64_t *a_full = bars, *a_empty = bars + 1;
+  uint64_t *b_full = bars + 2, *b_empty = bars + 4;   // 2 each
+  uint64_t *acc_full = bars + 6, *acc_empty = bars + 8;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 10);
+  __shared__ int s_abort;
+  __shared__ int s_a_issued, s_a_used, s_b_issued, s_b_used;
+
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x;
+  const int nrt = (int)blockIdx.x < n_row_tiles ? (n_row_tiles - (int)blockIdx.x + G - 1) / G : 0;
+  const int ntiles = nrt * n_col_tiles;   // (row tile, column tile) items, column tiles innermost
+
+  if (tid == 0) {
+    bar_init(a_full, 1);
+    bar_init(a_empty, 1);
+    for (int q = 0; q < 2; ++q) {
+      bar_init(&b_full[q], 1);
+      bar_init(&b_empty[q], 1);
+      bar_init(&acc_full[q], 1);
+      bar_init(&acc_empty[q], kOzEpiWarps);
+    }
+    s_abort = 0;
+    s_a_issued = s_a_used = s_b_issued = s_b_used = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (wid == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tmem_slot)),
+                 "r"(kOzTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (ntiles > 0 && wid == 0 && lane == 0) {
+    // producer: a row tile's A slices once the previous row tile's products are done with them,
+    // then one B set per column tile once the products two tiles back have read it
+    int ai = 0, bi = 0;
+    bool ok = true;
+    for (int it = 0; it < ntiles && ok; ++it) {
+      const int rti = it / n_col_tiles, ct = it - rti * n_col_tiles;
+      if (ct == 0) {
+        if (rti > 0 && !bar_wait(a_empty, (uint32_t)((rti - 1) & 1), P.limit_ns)) { ok = false; break; }
+        bar_expect(a_full, S * kOzATile);
+        const int rt = (int)blockIdx.x + G * rti;
+        for (int s = 0; s < S; ++s) tma2d(sA + s * kOzATile, &amap, 0, s * P.a_rows_pad + rt * kOzM, a_full);
+        ++ai;
+      }
+      const int set = it & 1, use = it >> 1;
+      if (use > 0 && !bar_wait(&b_empty[set], (uint32_t)((use - 1) & 1), P.limit_ns)) { ok = false; break; }
+      if (*(volatile int *)&s_abort) { ok = false; break; }
+      bar_expect(&b_full[set], S * SH::kBTile);
+      for (int t = 0; t < S; ++t)
+        tma2d(sB + (set * S + t) * SH::kBTile, &bmap, 0, t * P.b_rows_pad + ct * NT, &b_full[set]);
+      ++bi;
+    }
+    if (!ok) atomicExch(&s_abort, 1);
+    s_a_issued = ai;
+    s_b_issued = bi;
+  } else if (ntiles > 0 && wid == 1) {
+    // products of a column tile: pair (s, t), s + t < NL, into the level accumulator s + t of the
+    // tile's TMEM half (the first pair of each level overwrites it); the commits free the B set,
+    // fill the accumulator half and, after a row tile's last column tile, free the A slices
+    int au = 0, bu = 0;
+    bool ok = true;
+    constexpr uint32_t id = idesc(NT);
+    const uint64_t a_desc0 = sdesc(sa(sA)), b_desc0 = sdesc(sa(sB));
+    for (int it = 0; it < ntiles && ok; ++it) {
+      const int rti = it / n_col_tiles, ct = it - rti * n_col_tiles;
+      const int set = it & 1, use = it >> 1;
+      if (ct == 0) {
+        ok = __all_sync(0xffffffffu, bar_wait(a_full, (uint32_t)(rti & 1), P.limit_ns));
+        if (!ok) break;
+        ++au;
+      }
+      if (use > 0) ok = __all_sync(0xffffffffu, bar_wait(&acc_empty[set], (uint32_t)((use - 1) & 1), P.limit_ns));
+      if (ok) ok = __all_sync(0xffffffffu, bar_wait(&b_full[set], (uint32_t)(use & 1), P.limit_ns));
+      if (!ok || __any_sync(0xffffffffu, *(volatile int *)&s_abort != 0)) { ok = false; break; }
+      ++bu;
+      tc_fence_after();
+      const uint64_t bset = b_desc0 + (uint64_t)((set * S * SH::kBTile) >> 4);
+      const uint32_t dbase = tmem + (uint32_t)(set * NL * NT);
+      if (elect_one()) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const uint64_t ad = a_desc0 + (uint64_t)((s * kOzATile) >> 4);
+#pragma unroll
+          for (int t = 0; t < S; ++t) {
+            if (s + t < NL) {
+              const int L = s + t;
+              const uint32_t d = dbase + (uint32_t)(L * NT);
+              const uint64_t bd = bset + (uint64_t)((t * SH::kBTile) >> 4);
+              const bool first = s == (L > S - 1 ? L - (S - 1) : 0);
+#pragma unroll
+              for (int k16 = 0; k16 < kOzK / 16; ++k16)
+                mma_bf16(d, ad + 2 * k16, bd + 2 * k16, id, (first && k16 == 0) ? 0u : 1u);
+            }
+          }
+        }
+        mma_commit(&b_empty[set]);
+        mma_commit(&acc_full[set]);
+        if (ct == n_col_tiles - 1) mma_commit(a_empty);
+      }
+      __syncwarp();
+    }
+    if (!ok && lane == 0) atomicExch(&s_abort, 1);
+    if (lane == 0) {
+      s_a_used = au;
+      s_b_used = bu;
+    }
+  }
+
+  // epilogue: warps 4-19; warp w reads TMEM lanes 32 (w & 3) + lane, columns CPT ((w - 4) >> 2) + 0..CPT-1
+  if (wid >= 4) {
+    const int q = wid & 3, h = (wid - 4) >> 2;
+    const int row = 32 * q + lane;
+    bool good = true;
+    for (int it = 0; it < ntiles && good; ++it) {
+      const int rti = it / n_col_tiles, ct = it - rti * n_col_tiles;
+      const int set = it & 1, use = it >> 1;
+      // the tile's entries of C first: their loads overlap the wait for the products and the drain
+      const int ga = ((int)blockIdx.x + G * rti) * kOzM + row;
+      const int i = ga >> 1, p = ga & 1;
+      double cv[CPT];
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        const int c = ct * NT + CPT * h + k;
+        cv[k] = (i < P.rows && c < P.cols) ? reinterpret_cast<const double *>(P.C + (int64_t)c * P.ldc + i)[p] : 0.0;
+      }
+      bool ready = false;
+      const uint64_t t0 = global_ns();
+      while (!ready && !*(volatile int *)&s_abort) {
+        ready = bar_try(&acc_full[set], (uint32_t)(use & 1));
+        if (!ready && global_ns() - t0 > P.limit_ns) break;
+      }
+      good = __all_sync(0xffffffffu, ready);
+      if (!good) break;
+      tc_fence_after();
+      long long G0[CPT], G1[CPT];
+      float v[CPT];
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) { G0[k] = 0; G1[k] = 0; }
+#pragma unroll
+      for (int L = 0; L < NL; ++L) {
+        tmem_ld<CPT>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(set * NL * NT + L * NT + CPT * h), v);
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+          const long long I = (long long)__float2int_rn(v[k]);   // an integer of magnitude <= 2^24: exact
+          if (L < 4) G0[k] += I * (long long)(1 << (8 * (3 - L)));
+          else G1[k] += I * (long long)(1 << (8 * (7 - L)));
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) bar_arrive(&acc_empty[set]);
+      // C[i, c] -= 2^(ea + eb - 38) (G0 + 2^-32 G1)
+      const int ea = P.ea[ga];
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        const int c = ct * NT + CPT * h + k;
+        if (i < P.rows && c < P.cols) {
+          const int eb = P.eb[c];
+          // one K-block: |G0| <= 2^44.1 and |G1| <= 2^46.4, so G0 2^17 + G1 2^-15 fits an int64; the
+          // dropped low 15 bits of G1 are below 2^(ea + eb - 55) <= 2^-53 max|v| max|z|. One
+          // conversion, and the scale 2^(ea + eb - 55) added to the exponent field with an
+          // integer add: two FP64-pipe instructions per output with the subtraction
+          double r = 0.0;
+          const long long comb = G0[k] * (1ll << 17) + (G1[k] >> 15);
+          if (comb != 0 && ea > -2000 && eb > -2000) {
+            r = (double)comb;
+            const int sc = ea + eb - 55;
+            const long long rb = __double_as_longlong(r);
+            const int fe = (int)((rb >> 52) & 0x7ff) + sc;
+            r = (fe >= 1 && fe <= 2046) ? __longlong_as_double(rb + ((long long)sc << 52)) : ldexp(r, sc);
+          }
+          reinterpret_cast<double *>(P.C + (int64_t)c * P.ldc + i)[p] = cv[k] - r;
+        }
+      }
+    }
+    if (!good) atomicExch(&s_abort, 1);
+  }
+  __syncthreads();
+  if (s_abort && tid == 0) {
+    atomicExch(P.err, 1);
+    // loads still in flight (bounded waits): A row tiles and B sets issued but not taken
+    for (int k = s_a_used; k < s_a_issued; ++k) bar_wait(a_full, (uint32_t)(k & 1), P.limit_ns);
+    for (int k = s_b_used; k < s_b_issued; ++k) bar_wait(&b_full[k & 1], (uint32_t)((k >> 1) & 1), P.limit_ns);
+    // products in flight: the last column tile's commit
+    if (s_b_used > 0) {
+      const int k = s_b_used - 1;
+      bar_wait(&acc_full[k & 1], (uint32_t)((k >> 1) & 1), P.limit_ns);
     }
   }
   tc_fence_before();
@@ -672,7 +891,7 @@ cudaError_t launch_oz_adj(const OzAdjArgs &a, cudaStream_t st) {
   P.part_rows = (int)a.a.rows_pad;
   P.err = a.err;
   P.limit_ns = a.limit_ns;
-  auto kern = oz_gemm_kernel<false, kOzSlicesAdj, kOzLevelsAdj, kOzNAdj>;
+  auto kern = oz_adj_kernel<kOzSlicesAdj, kOzLevelsAdj, kOzNAdj>;
   constexpr int smem = OzShape<kOzSlicesAdj, kOzNAdj>::kSmem;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
   note_launch();
@@ -687,11 +906,15 @@ cudaError_t launch_oz_adj(const OzAdjArgs &a, cudaStream_t st) {
 
 cudaError_t launch_oz_fwd(const OzFwdArgs &a, cudaStream_t st) {
   if (a.rows < 1 || a.cols < 1) return cudaSuccess;
-  cudaError_t e;
+  if (a.a.ns != kOzSlicesFwd || a.b.ns != kOzSlicesFwd || a.a.k_pad != kOzK || a.b.k_pad != kOzK)
+    return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   CUtensorMap amap, bmap;
   if ((e = oz_map(a.a, kOzM, &amap)) != cudaSuccess) return e;
-  if ((e = oz_map(a.b, kOzNFwd, &bmap)) != cudaSuccess) return e;
-  if (a.a.ns != kOzSlicesFwd || a.b.ns != kOzSlicesFwd) return cudaErrorInvalidValue;
+  if ((e = oz_map(a.b, kOzFwdNT, &bmap)) != cudaSuccess) return e;
   OzParams P{};
   P.a_rows_pad = (int)a.a.rows_pad;
   P.b_rows_pad = (int)a.b.rows_pad;
@@ -704,12 +927,15 @@ cudaError_t launch_oz_fwd(const OzFwdArgs &a, cudaStream_t st) {
   P.cols = (int)a.cols;
   P.err = a.err;
   P.limit_ns = a.limit_ns;
-  auto kern = oz_gemm_kernel<true, kOzSlicesFwd, kOzLevelsFwd, kOzNFwd>;
-  constexpr int smem = OzShape<kOzSlicesFwd, kOzNFwd>::kSmem;
-  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+  const int n_row_tiles = (int)(a.a.rows_pad / kOzM);
+  const int n_col_tiles = (int)((a.cols + kOzFwdNT - 1) / kOzFwdNT);
+  const int grid = std::min(n_row_tiles, sms);
+  if ((int64_t)n_col_tiles * kOzFwdNT > a.b.rows_pad) return cudaErrorInvalidValue;
+  if ((e = cudaFuncSetAttribute(oz_fwd_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                OzFwdShape::kSmem)) != cudaSuccess)
+    return e;
   note_launch();
-  kern<<<dim3((unsigned)(a.a.rows_pad / kOzM), (unsigned)(a.b.rows_pad / kOzNFwd)), kOzThreads, smem, st>>>(amap, bmap,
-                                                                                                          P);
+  oz_fwd_persistent_kernel<<<grid, kOzThreads, OzFwdShape::kSmem, st>>>(amap, bmap, P, n_row_tiles, n_col_tiles);
   return cudaGetLastError();
 }
 

@@ -65,6 +65,8 @@ struct ScratchPool {
 
 // kernel classes of minnorm_kernel_stats (see minnorm.h)
 constexpr int kNumClasses = 8;
+// Step 2 by the blocked QR (qrblk.cu) for sketches of more than this many rows
+constexpr int64_t kQrBlockedMinRows = 2048;
 
 struct minnorm_plan_s {
   const ScratchPool *pool = nullptr;  // if set, S1, S2, afix and A32 point into it
@@ -627,7 +629,7 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
     ALLOC(plan->d_ggp, sizeof(double) * plan->sms);
   }
   // Step 2 for tall sketches: the blocked QR with tensor-core trailing updates (its workspace now)
-  plan->qr_blocked = l > 2048 && !plan->pool && qrblk_panel_grid(l, plan->sms) > 0;
+  plan->qr_blocked = l > kQrBlockedMinRows && !plan->pool && qrblk_panel_grid(l, plan->sms) > 0;
   if (plan->qr_blocked) {
     minnorm_status qs = qrblk_alloc(plan);
     if (qs != MINNORM_OK) return qs;

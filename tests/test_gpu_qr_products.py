@@ -16,8 +16,9 @@ K split, and the splits added by a compensated sum (their exact sum rounded once
                     + 2^-51 |V|^T|C|,
 checked with a factor 2 of slack: as accurate as an FP64 dot product at any K. The update
 (K = 32) truncates to 55 bits and drops the levels beyond 7: 2^-53 (max|V_i:| sum|Z_:c| +
-max|Z_:c| sum|V_i:|) + 2^-57 32 max|V_i:| max|Z_:c|, plus the roundings of the product and of the
-subtraction. Cases: one K range and several (split K; odd K-block counts), ragged tile edges,
+max|Z_:c| sum|V_i:|) + 2^-57 32 max|V_i:| max|Z_:c|, plus the low 15 bits of its level sums
+dropped before the one conversion (below 2^-53 max|V_i:| max|Z_:c|, within the first term) and
+the roundings of the product and of the subtraction. Cases: one K range and several (split K; odd K-block counts), ragged tile edges,
 rows and columns of very different scales, zero rows and columns."""
 import numpy as np
 import pytest
