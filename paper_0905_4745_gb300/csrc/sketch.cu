@@ -177,11 +177,18 @@ __device__ __forceinline__ int bitrev(int j, int logL) {
   return logL == 0 ? 0 : (int)(__brev((unsigned)j) >> (32 - logL));
 }
 
-// stw[k] = e^{-2 pi i k / L} for k < L/2, copied from the table tw (NT entries, L divides NT)
-// into shared memory: every butterfly stage then reads its twiddle there
+// The twiddles of every butterfly stage, stage by stage: stw[h + k] = e^{-2 pi i k / (2h)} for
+// h = 1, 2, 4, ..., L/2 and k < h (L entries, stw[0] unused), copied from the table tw (NT
+// entries, e^{-2 pi i j / NT}, L divides NT) into shared memory. A stage's twiddles are then
+// consecutive words (a warp's reads are conflict-free), and each is the table entry of the
+// plain layout, so the transform is unchanged.
 template <typename R>
 __device__ __forceinline__ void load_twiddles(cx<R> *stw, int logL, const cx<R> *__restrict__ tw, int logNT) {
-  for (int k = threadIdx.x; k < (1 << (logL - 1)); k += blockDim.x) stw[k] = tw[(int64_t)k << (logNT - logL)];
+  for (int idx = threadIdx.x + 1; idx < (1 << logL); idx += blockDim.x) {
+    const int lh = 31 - __clz(idx);
+    const int k = idx - (1 << lh);
+    stw[idx] = tw[(int64_t)k << (logNT - lh - 1)];
+  }
 }
 
 // In-place radix-2 DIT FFT (forward, e^{-2 pi i jk/L}) of B sequences of length
@@ -194,14 +201,13 @@ __device__ __forceinline__ void smem_fft(cx<R> *data, int B, int logL, int strid
   const int total = B * halfL;
   for (int lh = 0; lh < logL; ++lh) {
     const int h = 1 << lh;
-    const int twshift = logL - lh - 1;  // (L/2) / h
     for (int b = threadIdx.x; b < total; b += blockDim.x) {
       const int seqi = b >> (logL - 1);
       const int bb = b & (halfL - 1);
       const int k = bb & (h - 1);
       const int pos = ((bb >> lh) << (lh + 1)) + k;
       cx<R> *d = data + seqi * stride;
-      const cx<R> w = stw[k << twshift];
+      const cx<R> w = stw[h + k];
       const cx<R> u = d[pos];
       const cx<R> v = d[pos + h] * w;
       d[pos] = u + v;
@@ -240,7 +246,7 @@ fft_row_kernel(const cx<R> *__restrict__ src, int64_t ld_src, int logn, const cx
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R> *data = reinterpret_cast<cx<R> *>(smem_raw);
   const int n = 1 << logn;
-  cx<R> *stw = data + n;  // n/2 twiddles
+  cx<R> *stw = data + n;  // n twiddle slots (stage by stage)
   const int64_t row = blockIdx.y;
   const cx<R> *s = src + row * ld_src;
   load_twiddles<R>(stw, logn, tw, logn);
@@ -284,7 +290,7 @@ fft_pass_a_kernel(const cx<R> *__restrict__ src, int64_t ld, cx<R> *__restrict__
   const int64_t row = blockIdx.y;
   const cx<R> *s = src + row * ld;
   const int total = tj * N2;
-  cx<R> *stw = data + tj * (N2 + 1);  // N2/2 twiddles
+  cx<R> *stw = data + tj * (N2 + 1);  // N2 twiddle slots (stage by stage)
   load_twiddles<R>(stw, logN2, tw, logn);
   for (int e0 = threadIdx.x; e0 < total; e0 += 8 * blockDim.x) {  // eight loads in flight per thread
     cx<R> v[8];
@@ -338,7 +344,7 @@ fft_pass_b_kernel(const cx<R> *__restrict__ W, int64_t ldw, int logn, int logN1,
   const int64_t row = blockIdx.y;
   const cx<R> *w = W + row * ldw + (int64_t)k2_0 * N1;
   const int total = tk * N1;
-  cx<R> *stw = data + tk * (N1 + 1);  // N1/2 twiddles
+  cx<R> *stw = data + tk * (N1 + 1);  // N1 twiddle slots (stage by stage)
   load_twiddles<R>(stw, logN1, tw, logn);
   for (int e0 = threadIdx.x; e0 < total; e0 += 8 * blockDim.x) {  // eight loads in flight per thread
     cx<R> v[8];
@@ -437,7 +443,7 @@ static cudaError_t launch_fft_t(const FftArgs &a, cudaStream_t st) {
   const double scale = 1.0 / sqrt((double)(1LL << a.logn));
   cudaError_t e;
   if (a.logN1 == 0) {
-    const size_t smem = (sizeof(cx<R>) << a.logn) + (sizeof(cx<R>) << (a.logn - 1));  // data + twiddles
+    const size_t smem = (sizeof(cx<R>) << a.logn) * 2;  // data + twiddles
     e = cudaFuncSetAttribute(fft_row_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     note_launch();
@@ -450,8 +456,8 @@ static cudaError_t launch_fft_t(const FftArgs &a, cudaStream_t st) {
   const int N1 = 1 << a.logN1, N2 = 1 << (a.logn - a.logN1);
   // sequences padded by one element: the strided transposes into and out of shared memory
   // then touch distinct banks
-  const size_t smemA = sizeof(cx<R>) * ((size_t)a.tj * (N2 + 1) + N2 / 2);
-  const size_t smemB = sizeof(cx<R>) * ((size_t)a.tk * (N1 + 1) + N1 / 2);
+  const size_t smemA = sizeof(cx<R>) * ((size_t)a.tj * (N2 + 1) + N2);
+  const size_t smemB = sizeof(cx<R>) * ((size_t)a.tk * (N1 + 1) + N1);
   e = cudaFuncSetAttribute(fft_pass_a_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemA);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(fft_pass_b_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemB);
