@@ -1093,17 +1093,17 @@ cudaError_t launch_qrp(const QrArgs &a, cudaStream_t st) {
 // The chain of k steps is latency-bound, so each step is kept short: the
 // reciprocals of R's (real) diagonal are formed once per CTA, the thread that
 // finishes w_{j-1} scales it at once (no FP64 division inside the chain, one
-// FP64 instruction per step instead of one per thread), and with STAGE the next
-// column of R is copied into shared memory by cp.async while the current one is
-// applied (each thread copies and reads only its own rows).
+// FP64 instruction per step instead of one per thread), w_j goes to Wp and WpH
+// as soon as it is final (its pivot index read a step ahead), and with STAGE
+// the next column of R is copied into shared memory by cp.async while the
+// current one is applied (each thread copies and reads only its own rows).
 template <bool STAGE>
 __global__ void __launch_bounds__(128)
 prinv_kernel(const zd *__restrict__ R, const int32_t *__restrict__ piv, int m, zd *__restrict__ Wp,
              zd *__restrict__ WpH) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   zd *w = reinterpret_cast<zd *>(smem_raw);
-  zd *wout = w + m;
-  zd *rcol = wout + m;                                      // STAGE: 2 x m
+  zd *rcol = w + m;                                         // STAGE: 2 x m
   double *rinv = reinterpret_cast<double *>(rcol + (STAGE ? 2 * m : 0));
   __shared__ zd s_wj[2];
   const int tid = threadIdx.x;
@@ -1119,10 +1119,15 @@ prinv_kernel(const zd *__restrict__ R, const int32_t *__restrict__ piv, int m, z
   }
   __syncthreads();
   if (tid == 0) s_wj[k & 1] = {rinv[k], 0.0};
+  int pj = tid == 0 ? piv[k] : 0;
   for (int j = k; j >= 0; --j) {
     __syncthreads();  // s_wj[j & 1] = w_j / r_jj
     const zd wj = s_wj[j & 1];
-    if (tid == 0) wout[j] = wj;
+    if (tid == 0) {
+      Wp[(int64_t)pj * m + k] = wj;
+      WpH[(int64_t)k * m + pj] = conjg(wj);
+      if (j > 0) pj = piv[j - 1];
+    }
     if (STAGE && j > 0)  // column j-1 for the next step
       for (int i = tid; i < j - 1; i += blockDim.x)
         cp_async16(rcol + ((j - 1) & 1) * m + i, R + i + (int64_t)(j - 1) * m, 16);
@@ -1137,13 +1142,6 @@ prinv_kernel(const zd *__restrict__ R, const int32_t *__restrict__ piv, int m, z
     }
     if (STAGE) cp_async_wait_all();
   }
-  __syncthreads();
-  for (int i = tid; i <= k; i += blockDim.x) {
-    const zd v = wout[i];
-    const int pi = piv[i];
-    Wp[(int64_t)pi * m + k] = v;
-    WpH[(int64_t)k * m + pi] = conjg(v);
-  }
 }
 
 cudaError_t launch_prinv(const void *R, const int32_t *piv, int m, void *Wp, void *WpH, cudaStream_t st) {
@@ -1151,9 +1149,10 @@ cudaError_t launch_prinv(const void *R, const int32_t *piv, int m, void *Wp, voi
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(WpH, 0, sizeof(zd) * (size_t)m * m, st);
   if (e != cudaSuccess) return e;
-  const size_t staged = (sizeof(zd) * 4 + sizeof(double)) * (size_t)m;
-  const bool stage = staged <= 96 * 1024;
-  const size_t smem = stage ? staged : (sizeof(zd) * 2 + sizeof(double)) * (size_t)m;
+  // staged while two CTAs per SM still fit (m <= 2048)
+  const size_t staged = (sizeof(zd) * 3 + sizeof(double)) * (size_t)m;
+  const bool stage = staged <= 112 * 1024;
+  const size_t smem = stage ? staged : (sizeof(zd) + sizeof(double)) * (size_t)m;
   auto kern = stage ? prinv_kernel<true> : prinv_kernel<false>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
