@@ -67,6 +67,9 @@ struct ScratchPool {
 constexpr int kNumClasses = 8;
 // Step 2 by the blocked QR (qrblk.cu) for sketches of more than this many rows
 constexpr int64_t kQrBlockedMinRows = 2048;
+// relative residual reduction of an inner CG solve in mixed precision (each refinement step
+// then reduces the error by about this much, or by the floor the complex64 A sets)
+constexpr double kInnerTolMixed = 2e-3;
 
 struct minnorm_plan_s {
   const ScratchPool *pool = nullptr;  // if set, S1, S2, afix and A32 point into it
@@ -1146,7 +1149,7 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
   CK(cudaMemsetAsync(plan->d_xh, 0, sizeof(zd) * n, st));
   CK(cudaMemsetAsync(plan->d_xl, 0, sizeof(zd) * n, st));
   CK(cudaMemcpyAsync(plan->d_r, b, sizeof(zd) * m, cudaMemcpyDeviceToDevice, st));
-  const double tol_inner = plan->fp32 ? 1e-3 : 1e-11;
+  const double tol_inner = plan->fp32 ? kInnerTolMixed : 1e-11;
   const int maxit = plan->fp32 ? 40 : 300;
   double err = INFINITY, best = INFINITY, prev = INFINITY;
   int cg_total = 0, dd_passes = 0, outer = 0, stagnant = 0;
@@ -1301,7 +1304,7 @@ minnorm_status solve_async_body(minnorm_plan_t plan, const void *A, const void *
   CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
   CK(launch_solve_state_init(plan->d_ss, st));
   const CertConsts *cc = plan->d_cc;
-  const double tol_inner = plan->fp32 ? 1e-3 : 1e-11;
+  const double tol_inner = plan->fp32 ? kInnerTolMixed : 1e-11;
   const int maxit = plan->fp32 ? 40 : 300;
   const bool fused = plan->fused_ok && cg_fused_supported(plan->m, plan->n, plan->g_cg.ld, Acg);
   for (int outer = 0; outer <= kMaxOuter; ++outer) {
@@ -1601,7 +1604,7 @@ minnorm_status solve_block_chunk(minnorm_plan_t plan, const void *A, int64_t lda
   const int64_t m = plan->m, n = plan->n;
   const void *Acg = plan->d_A32 ? (const void *)plan->d_A32 : A;
   const int64_t lda_cg = plan->d_A32 ? n : lda;
-  const double tol_inner = 1e-3;
+  const double tol_inner = kInnerTolMixed;
   const int maxit = 40;
   int *use = plan->d_bint;
   struct Col {
