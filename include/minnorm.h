@@ -355,8 +355,11 @@ int64_t minnorm_launch_count(void);
  * pivoting), 4: sketch (both chains and the FFT), 5: fused CG solves, 6: the
  * pivoted QR of the m x m triangle (taller sketches only), 7: P R^{-1}) the
  * number of timed regions (for k = 5: the CG iterations run inside them) and
- * their summed milliseconds (CUDA events on the plan's stream). Errors: EINVAL
- * (k outside 0..7). */
+ * their summed milliseconds (CUDA events on the plan's stream). Classes 0 and
+ * 1 count launches enqueued: the two-pass CG enqueues its iterations in chunks,
+ * and the launches after its test has fired return at once, so those counts
+ * may exceed the CG iterations of minnorm_info. Errors: EINVAL (k outside
+ * 0..7). */
 minnorm_status minnorm_kernel_stats(minnorm_plan_t plan, int32_t k, int32_t *launches, double *ms);
 
 /* ------------------------------------------------------------------------

@@ -223,10 +223,15 @@ def test_certificate_premise(mn, m, n, prec, dtype):
 
 
 # ---------------------------------------------------------------- Step 4 ----
-@pytest.mark.parametrize("m,n,prec,dtype", [(32, 4096, 0, "c128"), (64, 65536, 0, "c128"),
-                                            (17, 3000 * 0 + 8192, 1, "c128"), (96, 16384, 1, "c64"),
-                                            (40, 8192, 0, "c64")])
-def test_cg_products_match_oracle(mn, m, n, prec, dtype):
+# pad: row stride n + pad. The complex64 forward product reads two entries per 16-byte load only
+# for an even stride and column count; odd ones (pad 1 or 3, n = 3001) take the 8-byte form.
+# m = 700 leaves a ragged last block of rows (8 per CTA).
+@pytest.mark.parametrize("m,n,prec,dtype,pad", [(32, 4096, 0, "c128", 0), (64, 65536, 0, "c128", 0),
+                                                (17, 8192, 1, "c128", 0), (96, 16384, 1, "c64", 0),
+                                                (40, 8192, 0, "c64", 0), (96, 16384, 1, "c64", 1),
+                                                (40, 8192, 0, "c64", 3), (700, 8192, 1, "c64", 0),
+                                                (21, 3001, 1, "c64", 0)])
+def test_cg_products_match_oracle(mn, m, n, prec, dtype, pad):
     import torch
     s = synth.make_system(m, n, exponent=3, seed=500 + m, dtype=dtype)
     A64 = s.A.astype(np.complex128)
@@ -234,7 +239,9 @@ def test_cg_products_match_oracle(mn, m, n, prec, dtype):
     w = rng.standard_normal(m) + 1j * rng.standard_normal(m)
     plan = _plan(mn, m, n, prec, seed=2, dtype=mn.C64 if dtype == "c64" else mn.C128)
     try:
-        A = _t(s.A)
+        Ap = np.zeros((m, n + pad), s.A.dtype)
+        Ap[:, :n] = s.A
+        A = _t(Ap)
         mn.minnorm_sketch(plan, A)
         q = torch.empty(n, dtype=torch.complex128, device=_dev())
         t = torch.empty(m, dtype=torch.complex128, device=_dev())
