@@ -285,6 +285,16 @@ minnorm_status minnorm_get_sketch(minnorm_plan_t plan, void *Y_out);
  * piv[k] of Y) of the last minnorm_sketch (Step 2). Errors: ESTATE, EINVAL. */
 minnorm_status minnorm_get_factor(minnorm_plan_t plan, void *R_out, void *piv_out);
 
+/* Copy the preconditioner P R^{-1} of the last minnorm_sketch (Step 2's
+ * factors as Steps 3-4 apply them: the CG runs on the system preconditioned
+ * by it) to W_out (device, m x m complex128, column-major: row piv[k] of
+ * P R^{-1} is row k of R^{-1}). Computed in FP64 by back substitution, or,
+ * for sketches factored by the blocked QR and m >= 256, by blocks of 32 rows
+ * with the rank-32 updates on the tensor cores; either way with
+ * ||R X - I||_F <= 4 m 2^-53 ||R||_F ||X||_F for X = P^T W_out, the bound the
+ * certificate uses. Errors: ESTATE, EINVAL. */
+minnorm_status minnorm_get_preconditioner(minnorm_plan_t plan, void *W_out);
+
 /* One CG product pair of Step 4 in the plan's precision, on device vectors:
  * q = A^* w (w: m complex128 -> q: n complex128) and t = A q (t: m complex128).
  * In MINNORM_MIXED the products read the complex64 copy of A made by

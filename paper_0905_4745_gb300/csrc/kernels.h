@@ -258,6 +258,13 @@ cudaError_t launch_qr_blocked(QrBlkWork &w, const QrArgs &q, int sms, cudaStream
 // QR of the m x m triangle R1
 cudaError_t launch_qr_tall(QrBlkWork &w, const QrArgs &q, int sms, cudaStream_t st);
 cudaError_t launch_qr_triangle(QrBlkWork &w, const QrArgs &q, cudaStream_t st);
+// P R^{-1} (Wp = P R^{-1} and WpH = Wp^*, row-major, the layout of launch_prinv) by blocks of 32
+// rows with the K = 32 updates on the tensor cores; R: m x m complex column-major, upper
+// triangular with a real diagonal; uses the workspace's triangle buffer (free after
+// launch_qr_triangle) and its update slices. For kPinvBlockedMinM <= m <= the workspace's m.
+constexpr int kPinvBlockedMinM = 256;
+cudaError_t launch_prinv_blocked(QrBlkWork &w, const void *R, const int32_t *piv, int m, void *Wp, void *WpH,
+                                 int *err, uint64_t limit_ns, cudaStream_t st);
 // rows of a panel one CTA may hold in shared memory; the blocked QR needs l <= kPanelMaxRows * sms
 constexpr int kPanelMaxRows = 384;
 int qrblk_panel_grid(int64_t L, int sms);

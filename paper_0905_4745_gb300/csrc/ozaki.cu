@@ -145,7 +145,10 @@ oz_slice_cols_kernel(const zd *__restrict__ C, int64_t ldc, int64_t rows, int64_
   }
 }
 
-// B rows of the adjoint product from the 32 reflectors: one CTA per reflector j (two rows)
+// B rows of the adjoint product from the 32 reflectors: CTA (j, chunk) writes reflector j's two
+// rows for its chunk of the K positions; every CTA of a reflector forms the same exponent from
+// the whole column (read from L2), so the chunks need no second pass
+constexpr int kOzVadjChunks = 8;
 __global__ void __launch_bounds__(256)
 oz_slice_v_adj_kernel(const zd *__restrict__ V, int64_t ldv, int64_t rows, __nv_bfloat16 *__restrict__ S,
                       int32_t *__restrict__ expo, int64_t kpad) {
@@ -158,9 +161,10 @@ oz_slice_v_adj_kernel(const zd *__restrict__ V, int64_t ldv, int64_t rows, __nv_
     e = max(e, max(oz_expo_of(v.re), oz_expo_of(v.im)));
   }
   e = oz_block_max(e, red);
-  if (threadIdx.x == 0) { expo[j] = e; expo[32 + j] = e; }
+  if (threadIdx.x == 0 && blockIdx.y == 0) { expo[j] = e; expo[32 + j] = e; }
   const int64_t ss = (int64_t)64 * kpad;
-  for (int64_t r = threadIdx.x; 2 * r < kpad; r += blockDim.x) {
+  const int64_t np = kpad / 2, r0 = np * blockIdx.y / gridDim.y, r1 = np * (blockIdx.y + 1) / gridDim.y;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     __nv_bfloat16 a[kOzSlicesAdj], b[kOzSlicesAdj], na[kOzSlicesAdj];
     const zd v = r < rows ? col[r] : zd{0.0, 0.0};
     oz_slices<kOzSlicesAdj>(v.re, e, a);
@@ -171,55 +175,48 @@ oz_slice_v_adj_kernel(const zd *__restrict__ V, int64_t ldv, int64_t rows, __nv_
   }
 }
 
-// A rows of the update: one thread per row i of V (two rows 2i, 2i+1, K = 64)
-__global__ void __launch_bounds__(128)
+// A rows of the update: one warp per row i of V (two rows 2i, 2i+1, K = 64), lane j = column j;
+// the row's exponent is the warp's maximum
+__global__ void __launch_bounds__(256)
 oz_slice_v_fwd_kernel(const zd *__restrict__ V, int64_t ldv, int64_t rows, __nv_bfloat16 *__restrict__ S,
                       int32_t *__restrict__ expo, int64_t rows_pad) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (2 * i >= rows_pad) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (2 * i >= rows_pad) return;   // warp-uniform
   const int64_t ss = rows_pad * kOzK;
-  zd v[32];
-  int e = -2000;
+  const zd v = i < rows ? V[(int64_t)lane * ldv + i] : zd{0.0, 0.0};
+  int e = max(oz_expo_of(v.re), oz_expo_of(v.im));
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    v[j] = i < rows ? V[(int64_t)j * ldv + i] : zd{0.0, 0.0};
-    e = max(e, max(oz_expo_of(v[j].re), oz_expo_of(v[j].im)));
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (lane == 0) {
+    expo[2 * i] = e;
+    expo[2 * i + 1] = e;
   }
-  expo[2 * i] = e;
-  expo[2 * i + 1] = e;
-#pragma unroll 1
-  for (int j = 0; j < 32; ++j) {
-    __nv_bfloat16 re[kOzSlicesFwd], im[kOzSlicesFwd], nim[kOzSlicesFwd];
-    oz_slices<kOzSlicesFwd>(v[j].re, e, re);
-    oz_slices<kOzSlicesFwd>(v[j].im, e, im);
-    oz_slices<kOzSlicesFwd>(-v[j].im, e, nim);
-    oz_put2<kOzSlicesFwd>(S, ss, kOzK, 2 * i, 2 * j, re, nim);    // (Re V, -Im V)
-    oz_put2<kOzSlicesFwd>(S, ss, kOzK, 2 * i + 1, 2 * j, im, re); // (Im V, Re V)
-  }
+  __nv_bfloat16 re[kOzSlicesFwd], im[kOzSlicesFwd], nim[kOzSlicesFwd];
+  oz_slices<kOzSlicesFwd>(v.re, e, re);
+  oz_slices<kOzSlicesFwd>(v.im, e, im);
+  oz_slices<kOzSlicesFwd>(-v.im, e, nim);
+  oz_put2<kOzSlicesFwd>(S, ss, kOzK, 2 * i, 2 * lane, re, nim);    // (Re V, -Im V)
+  oz_put2<kOzSlicesFwd>(S, ss, kOzK, 2 * i + 1, 2 * lane, im, re); // (Im V, Re V)
 }
 
-// B rows of the update: one thread per column c of Z (32 x cols, column-major)
-__global__ void __launch_bounds__(128)
+// B rows of the update: one warp per column c of Z (32 x cols, column-major), lane j = row j
+__global__ void __launch_bounds__(256)
 oz_slice_z_kernel(const zd *__restrict__ Z, int64_t ldz, int64_t cols, __nv_bfloat16 *__restrict__ S,
                   int32_t *__restrict__ expo, int64_t rows_pad) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= rows_pad) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (c >= rows_pad) return;   // warp-uniform
   const int64_t ss = rows_pad * kOzK;
-  zd z[32];
-  int e = -2000;
+  const zd z = c < cols ? Z[c * ldz + lane] : zd{0.0, 0.0};
+  int e = max(oz_expo_of(z.re), oz_expo_of(z.im));
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    z[j] = c < cols ? Z[c * ldz + j] : zd{0.0, 0.0};
-    e = max(e, max(oz_expo_of(z[j].re), oz_expo_of(z[j].im)));
-  }
-  expo[c] = e;
-#pragma unroll 1
-  for (int j = 0; j < 32; ++j) {
-    __nv_bfloat16 re[kOzSlicesFwd], im[kOzSlicesFwd];
-    oz_slices<kOzSlicesFwd>(z[j].re, e, re);
-    oz_slices<kOzSlicesFwd>(z[j].im, e, im);
-    oz_put2<kOzSlicesFwd>(S, ss, kOzK, c, 2 * j, re, im);
-  }
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (lane == 0) expo[c] = e;
+  __nv_bfloat16 re[kOzSlicesFwd], im[kOzSlicesFwd];
+  oz_slices<kOzSlicesFwd>(z.re, e, re);
+  oz_slices<kOzSlicesFwd>(z.im, e, im);
+  oz_put2<kOzSlicesFwd>(S, ss, kOzK, c, 2 * lane, re, im);
 }
 
 }  // namespace
@@ -498,12 +495,15 @@ oz_adj_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
   }
 }
 
-// The update C -= V Z as a persistent kernel. CTA g takes the A row tiles (128 rows of the real
-// form of V) g, g + G, ...: a row tile's S A slices are loaded once and stay in shared memory
-// while the 32-column tiles of Z stream through two B buffers; the level accumulators of a column
-// tile (8 levels x 32 TMEM columns) alternate between the two halves of tensor memory, so the
-// epilogue of one column tile overlaps the products of the next. Roles as in oz_adj_kernel
-// (warp 0 loads, warp 1 multiplies, warp 2 owns tensor memory, warps 4-19 drain and write).
+// The update C -= V Z as a persistent kernel. The (row tile, column tile) items (row tiles of 128
+// rows of the real form of V, column tiles of 32 columns of Z; column tiles innermost) are dealt
+// to the CTAs in equal contiguous shares, so every SM has work even when the update has fewer
+// row tiles than SMs (short, wide updates). A CTA loads a row tile's S A slices when its share
+// enters that row tile (at most a few times) and keeps them in shared memory while the column
+// tiles of Z stream through two B buffers; the level accumulators of a column tile (8 levels x
+// 32 TMEM columns) alternate between the two halves of tensor memory, so the epilogue of one
+// column tile overlaps the products of the next. Roles as in oz_adj_kernel (warp 0 loads, warp
+// 1 multiplies, warp 2 owns tensor memory, warps 4-19 drain and write).
 constexpr int kOzFwdNT = 32;
 struct OzFwdShape {
   static constexpr int kBTile = kOzFwdNT * kOzK * 2;                  // 4 KB
@@ -531,9 +531,9 @@ oz_fwd_persistent_kernel(const __grid_constant__ CUtensorMap amap, const __grid_
   __shared__ int s_a_issued, s_a_used, s_b_issued, s_b_used;
 
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-  const int G = gridDim.x;
-  const int nrt = (int)blockIdx.x < n_row_tiles ? (n_row_tiles - (int)blockIdx.x + G - 1) / G : 0;
-  const int ntiles = nrt * n_col_tiles;   // (row tile, column tile) items, column tiles innermost
+  const int64_t n_items = (int64_t)n_row_tiles * n_col_tiles;
+  const int64_t item0 = n_items * blockIdx.x / gridDim.x;
+  const int ntiles = (int)(n_items * (blockIdx.x + 1) / gridDim.x - item0);   // this CTA's items
 
   if (tid == 0) {
     bar_init(a_full, 1);
@@ -565,11 +565,12 @@ oz_fwd_persistent_kernel(const __grid_constant__ CUtensorMap amap, const __grid_
     int ai = 0, bi = 0;
     bool ok = true;
     for (int it = 0; it < ntiles && ok; ++it) {
-      const int rti = it / n_col_tiles, ct = it - rti * n_col_tiles;
-      if (ct == 0) {
-        if (rti > 0 && !bar_wait(a_empty, (uint32_t)((rti - 1) & 1), P.limit_ns)) { ok = false; break; }
+      const int64_t gi = item0 + it;
+      const int rt = (int)(gi / n_col_tiles), ct = (int)(gi - (int64_t)rt * n_col_tiles);
+      if (it == 0 || ct == 0) {   // the share enters row tile rt: its A slices, once the products
+                                  // of the previous row tile are done with the buffer
+        if (ai > 0 && !bar_wait(a_empty, (uint32_t)((ai - 1) & 1), P.limit_ns)) { ok = false; break; }
         bar_expect(a_full, S * kOzATile);
-        const int rt = (int)blockIdx.x + G * rti;
         for (int s = 0; s < S; ++s) tma2d(sA + s * kOzATile, &amap, 0, s * P.a_rows_pad + rt * kOzM, a_full);
         ++ai;
       }
@@ -593,10 +594,11 @@ oz_fwd_persistent_kernel(const __grid_constant__ CUtensorMap amap, const __grid_
     constexpr uint32_t id = idesc(NT);
     const uint64_t a_desc0 = sdesc(sa(sA)), b_desc0 = sdesc(sa(sB));
     for (int it = 0; it < ntiles && ok; ++it) {
-      const int rti = it / n_col_tiles, ct = it - rti * n_col_tiles;
+      const int64_t gi = item0 + it;
+      const int ct = (int)(gi % n_col_tiles);
       const int set = it & 1, use = it >> 1;
-      if (ct == 0) {
-        ok = __all_sync(0xffffffffu, bar_wait(a_full, (uint32_t)(rti & 1), P.limit_ns));
+      if (it == 0 || ct == 0) {
+        ok = __all_sync(0xffffffffu, bar_wait(a_full, (uint32_t)(au & 1), P.limit_ns));
         if (!ok) break;
         ++au;
       }
@@ -626,7 +628,7 @@ oz_fwd_persistent_kernel(const __grid_constant__ CUtensorMap amap, const __grid_
         }
         mma_commit(&b_empty[set]);
         mma_commit(&acc_full[set]);
-        if (ct == n_col_tiles - 1) mma_commit(a_empty);
+        if (ct == n_col_tiles - 1 || it == ntiles - 1) mma_commit(a_empty);   // the row tile's last item
       }
       __syncwarp();
     }
@@ -643,10 +645,11 @@ oz_fwd_persistent_kernel(const __grid_constant__ CUtensorMap amap, const __grid_
     const int row = 32 * q + lane;
     bool good = true;
     for (int it = 0; it < ntiles && good; ++it) {
-      const int rti = it / n_col_tiles, ct = it - rti * n_col_tiles;
+      const int64_t gi = item0 + it;
+      const int rt = (int)(gi / n_col_tiles), ct = (int)(gi - (int64_t)rt * n_col_tiles);
       const int set = it & 1, use = it >> 1;
       // the tile's entries of C first: their loads overlap the wait for the products and the drain
-      const int ga = ((int)blockIdx.x + G * rti) * kOzM + row;
+      const int ga = rt * kOzM + row;
       const int i = ga >> 1, p = ga & 1;
       double cv[CPT];
 #pragma unroll
@@ -788,8 +791,8 @@ cudaError_t launch_oz_slice_v_adj(const void *V, int64_t ldv, int64_t rows, OzOp
   out.k_pad = pad_to(2 * rows, kOzK);
   out.ns = kOzSlicesAdj;
   note_launch();
-  oz_slice_v_adj_kernel<<<32, 256, 0, st>>>((const zd *)V, ldv, rows, (__nv_bfloat16 *)out.slices, out.expo,
-                                            out.k_pad);
+  oz_slice_v_adj_kernel<<<dim3(32, kOzVadjChunks), 256, 0, st>>>((const zd *)V, ldv, rows, (__nv_bfloat16 *)out.slices,
+                                                                 out.expo, out.k_pad);
   return cudaGetLastError();
 }
 
@@ -799,11 +802,11 @@ cudaError_t launch_oz_slice_v_fwd(const void *V, int64_t ldv, int64_t rows, OzOp
   out.k = kOzK;
   out.k_pad = kOzK;
   out.ns = kOzSlicesFwd;
-  const int64_t th = out.rows_pad / 2;
+  const int64_t warps = out.rows_pad / 2;   // one per row of V, padding rows included
   note_launch();
-  oz_slice_v_fwd_kernel<<<(unsigned)((th + 127) / 128), 128, 0, st>>>((const zd *)V, ldv, rows,
-                                                                      (__nv_bfloat16 *)out.slices, out.expo,
-                                                                      out.rows_pad);
+  oz_slice_v_fwd_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>((const zd *)V, ldv, rows,
+                                                                     (__nv_bfloat16 *)out.slices, out.expo,
+                                                                     out.rows_pad);
   return cudaGetLastError();
 }
 
@@ -814,9 +817,9 @@ cudaError_t launch_oz_slice_z(const void *Z, int64_t ldz, int64_t cols, OzOperan
   out.k_pad = kOzK;
   out.ns = kOzSlicesFwd;
   note_launch();
-  oz_slice_z_kernel<<<(unsigned)((out.rows_pad + 127) / 128), 128, 0, st>>>((const zd *)Z, ldz, cols,
-                                                                            (__nv_bfloat16 *)out.slices, out.expo,
-                                                                            out.rows_pad);
+  oz_slice_z_kernel<<<(unsigned)((out.rows_pad + 7) / 8), 256, 0, st>>>((const zd *)Z, ldz, cols,
+                                                                        (__nv_bfloat16 *)out.slices, out.expo,
+                                                                        out.rows_pad);
   return cudaGetLastError();
 }
 
@@ -929,7 +932,8 @@ cudaError_t launch_oz_fwd(const OzFwdArgs &a, cudaStream_t st) {
   P.limit_ns = a.limit_ns;
   const int n_row_tiles = (int)(a.a.rows_pad / kOzM);
   const int n_col_tiles = (int)((a.cols + kOzFwdNT - 1) / kOzFwdNT);
-  const int grid = std::min(n_row_tiles, sms);
+  // one CTA per SM, each with an equal share of the items (at least one)
+  const int grid = (int)std::min<int64_t>((int64_t)n_row_tiles * n_col_tiles, sms);
   if ((int64_t)n_col_tiles * kOzFwdNT > a.b.rows_pad) return cudaErrorInvalidValue;
   if ((e = cudaFuncSetAttribute(oz_fwd_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 OzFwdShape::kSmem)) != cudaSuccess)

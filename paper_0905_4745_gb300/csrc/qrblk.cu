@@ -316,4 +316,117 @@ cudaError_t launch_qr_blocked(QrBlkWork &w, const QrArgs &q, int sms, cudaStream
   return e != cudaSuccess ? e : launch_qr_triangle(w, q, st);
 }
 
+// ---- P R^{-1} by blocks of rows (Step 4's preconditioner) ---------------------------
+// X = R^{-1} (R upper triangular, real diagonal) by block rows of kPanel from the bottom, the
+// top block taking the remainder, right-looking: with C = I,
+//   X_J = R_JJ^{-1} C_J                (block row J of C; FP64 back substitution, one warp per column)
+//   C[0:j0, j0:m] -= R[0:j0, J] X_J    (the K = 32 update C -= V Z on the tensor cores)
+// then Wp = P X and WpH = Wp^*. Every update of a block row reads only block rows below it, so
+// X overwrites C in place.
+//
+// Rounding. F = R X - I, block row I: F_I = delta_I + sum_{J > I} D_IJ, with delta_I the back
+// substitution's residual, |delta_I| <= 4 (bw + 2) 2^-53 |R_II| |X_I| (bw <= 32), and D_IJ the
+// error of update J on block row I. The update's bound per entry (the products' operands cut to
+// 55 bits below their row's scale, the dropped slice levels, the product rounded once to FP64,
+// then the subtraction), with max|V_i:| <= ||V_i:||, sum|Z_:c| <= sqrt 32 ||Z_:c|| and so on:
+//   |D_ic| <= 2^-53 ((2 sqrt 32 + 4) ||V_i:|| ||Z_:c|| + |C_ic after the update|),
+// and |C_ic| <= [i == c] + (|R| |X|)_ic at every stage (a factor sqrt 2 more on the first term
+// for the real forms of complex entries). Summed over the NB = ceil(m / 32) blocks (Cauchy-Schwarz
+// over J for the first term) and taken in the Frobenius norm:
+//   ||F||_F <= 2^-53 ((136 + sqrt 2 (2 sqrt 32 + 4) + NB) ||R||_F ||X||_F + NB sqrt m)
+//           <= 2^-53 (160 + 2 NB) ||R||_F ||X||_F   (sqrt m = ||I||_F <= ||R||_F ||X||_F (1 + ||F||_F)),
+// below the column-by-column substitution's 4 m 2^-53 ||R||_F ||X||_F, which the certificate
+// uses, for every m >= kPinvBlockedMinM.
+constexpr int kPinvWarps = 8;
+
+__global__ void __launch_bounds__(256)
+prinv_ident_kernel(zd *__restrict__ X, int m) {
+  const int64_t n = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    X[e] = {e % (m + 1) == 0 ? 1.0 : 0.0, 0.0};
+}
+
+// X[j0:j0+bw, c] = R_JJ^{-1} X[j0:j0+bw, c] for c = j0..m-1: lane i holds row j0 + i; the
+// reciprocals of R's (real) diagonal formed once per CTA, as in prinv_kernel
+__global__ void __launch_bounds__(32 * kPinvWarps)
+prinv_diag_kernel(const zd *__restrict__ R, int m, zd *__restrict__ X, int j0, int bw) {
+  __shared__ zd sR[kPanel][kPanel + 1];   // sR[k][i] = R[j0 + i, j0 + k]
+  __shared__ double sinv[kPanel];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int e = tid; e < bw * bw; e += blockDim.x) {
+    const int i = e % bw, k = e / bw;
+    sR[k][i] = R[(int64_t)(j0 + i) + (int64_t)(j0 + k) * m];
+  }
+  if (tid < bw) sinv[tid] = 1.0 / R[(int64_t)(j0 + tid) * (m + 1)].re;
+  __syncthreads();
+  const int64_t c = (int64_t)j0 + (int64_t)blockIdx.x * kPinvWarps + w;
+  if (c >= m) return;   // warp-uniform
+  zd *col = X + c * m + j0;
+  zd x = {0.0, 0.0};
+  if (lane < bw) x = col[lane];
+  for (int k = bw - 1; k >= 0; --k) {
+    if (lane == k) {
+      x.re *= sinv[k];
+      x.im *= sinv[k];
+    }
+    const double xr = __shfl_sync(0xffffffffu, x.re, k), xi = __shfl_sync(0xffffffffu, x.im, k);
+    if (lane < k) {
+      const zd a = sR[k][lane];
+      x.re = fma(-a.re, xr, fma(a.im, xi, x.re));
+      x.im = fma(-a.re, xi, fma(-a.im, xr, x.im));
+    }
+  }
+  if (lane < bw) col[lane] = x;
+}
+
+// Wp[piv[i], k] = X[i, k] and WpH[k, piv[i]] = conj(X[i, k]) for i <= k, zero below the diagonal
+// (every entry of both written once; 32 x 32 tiles through shared memory for Wp's rows)
+__global__ void __launch_bounds__(256)
+prinv_scatter_kernel(const zd *__restrict__ X, const int32_t *__restrict__ piv, int m, zd *__restrict__ Wp,
+                     zd *__restrict__ WpH) {
+  __shared__ zd t[32][33];   // t[k - k0][i - i0]
+  const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + tx, k = k0 + r;
+    zd v = {0.0, 0.0};
+    if (i < m && k < m) {
+      if (i <= k) v = X[(int64_t)i + (int64_t)k * m];
+      WpH[(int64_t)k * m + piv[i]] = conjg(v);
+    }
+    t[r][tx] = v;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r, k = k0 + tx;
+    if (i < m && k < m) Wp[(int64_t)piv[i] * m + k] = t[tx][r];
+  }
+}
+
+cudaError_t launch_prinv_blocked(QrBlkWork &w, const void *R, const int32_t *piv, int m, void *Wp, void *WpH,
+                                 int *err, uint64_t limit_ns, cudaStream_t st) {
+  if (m > w.m || m < 1) return cudaErrorInvalidValue;
+  zd *X = static_cast<zd *>(w.R1);   // m x m, free once the triangle's pivoted QR has run
+  const zd *Rz = static_cast<const zd *>(R);
+  note_launch();
+  prinv_ident_kernel<<<1024, 256, 0, st>>>(X, m);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  for (int j1 = m; j1 > 0; j1 -= kPanel) {
+    const int j0 = j1 > kPanel ? j1 - kPanel : 0, bw = j1 - j0;
+    note_launch();
+    prinv_diag_kernel<<<(unsigned)((m - j0 + kPinvWarps - 1) / kPinvWarps), 32 * kPinvWarps, 0, st>>>(Rz, m, X, j0,
+                                                                                                      bw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (j0 > 0 &&
+        (e = launch_trailing_products(w, Rz + (int64_t)j0 * m, m, X + (int64_t)j0 * m, m, j0, m - j0,
+                                      X + j0 + (int64_t)j0 * m, m, nullptr, err, limit_ns, st)) != cudaSuccess)
+      return e;
+  }
+  const dim3 grid((unsigned)((m + 31) / 32), (unsigned)((m + 31) / 32));
+  note_launch();
+  prinv_scatter_kernel<<<grid, 256, 0, st>>>(X, piv, m, static_cast<zd *>(Wp), static_cast<zd *>(WpH));
+  return cudaGetLastError();
+}
+
 }  // namespace mn

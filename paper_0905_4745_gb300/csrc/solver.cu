@@ -741,7 +741,11 @@ minnorm_status sketch_factor(minnorm_plan_t plan) {
   }
   {
     Timed tm(plan, 7);
-    CK(launch_prinv(plan->d_R, plan->d_piv, (int)m, plan->d_Wp, plan->d_WpH, st));
+    if (plan->qr_blocked && m >= kPinvBlockedMinM)
+      CK(launch_prinv_blocked(plan->qb, plan->d_R, plan->d_piv, (int)m, plan->d_Wp, plan->d_WpH, plan->d_err,
+                              plan->wait_limit_ns, st));
+    else
+      CK(launch_prinv(plan->d_R, plan->d_piv, (int)m, plan->d_Wp, plan->d_WpH, st));
     // ||R||_F, ||P R^{-1}||_F and ||A||_F for the certificate's delta
     CK(launch_sumsq(m * m, plan->d_R, plan->d_red, plan->d_cert, st));
     CK(launch_sumsq(m * m, plan->d_Wp, plan->d_red + 1024, plan->d_cert + 1, st));
@@ -1993,6 +1997,22 @@ minnorm_status minnorm_get_factor(minnorm_plan_t plan, void *R_out, void *piv_ou
   CK(cudaMemcpyAsync(R_out, plan->d_R, sizeof(zd) * plan->m * plan->m, cudaMemcpyDeviceToDevice, plan->st));
   note_launch();
   piv_widen_kernel<<<(int)((plan->m + 255) / 256), 256, 0, plan->st>>>(plan->d_piv, (int64_t *)piv_out, (int)plan->m);
+  CK(cudaGetLastError());
+  return MINNORM_OK;
+}
+
+// out = conj(in), n complex entries
+__global__ void conj_copy_kernel(const zd *__restrict__ in, zd *__restrict__ out, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = conjg(in[e]);
+}
+
+minnorm_status minnorm_get_preconditioner(minnorm_plan_t plan, void *W_out) {
+  if (!plan || !W_out) return MINNORM_EINVAL;
+  if (!plan->sketched) return MINNORM_ESTATE;
+  // column-major P R^{-1}: entry (i, k) at i + k m, the conjugate of WpH's row-major (k, i)
+  note_launch();
+  conj_copy_kernel<<<1024, 256, 0, plan->st>>>(plan->d_WpH, static_cast<zd *>(W_out), plan->m * plan->m);
   CK(cudaGetLastError());
   return MINNORM_OK;
 }

@@ -22,7 +22,7 @@ FLAG_TIMING, FLAG_KEEP_SKETCH = 1, 2
 # every symbol include/minnorm.h declares
 EXPORTS = ["minnorm_plan_create", "minnorm_plan_set_params", "minnorm_plan_export_params", "minnorm_sketch", "minnorm_solve", "minnorm_solve_wait", "minnorm_plan_set_wait_limit", "minnorm_trailing_products",
            "minnorm_solve_host", "minnorm_plan_destroy", "minnorm_status_string", "minnorm_get_sketch",
-           "minnorm_get_factor", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats",
+           "minnorm_get_factor", "minnorm_get_preconditioner", "minnorm_cg_products", "minnorm_residual_dd", "minnorm_kernel_stats",
            "minnorm_launch_count", "minnorm_qr_noalloc", "minnorm_solve_many", "minnorm_batch_create",
            "minnorm_batch_solve", "minnorm_batch_destroy", "minnorm_batch_kernel_stats", "minnorm_block_products", "minnorm_plan_tuning"]
 
@@ -77,6 +77,7 @@ def lib():
         L.minnorm_status_string.restype = C.c_char_p
         L.minnorm_get_sketch.argtypes = [p, p]
         L.minnorm_get_factor.argtypes = [p, p, p]
+        L.minnorm_get_preconditioner.argtypes = [p, p]
         L.minnorm_cg_products.argtypes = [p, p, i64, p, p, p]
         L.minnorm_block_products.argtypes = [p, p, i64, p, p, p]
         L.minnorm_plan_tuning.argtypes = [p, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
@@ -263,6 +264,10 @@ def minnorm_get_sketch(plan, Y_out):
 
 def minnorm_get_factor(plan, R_out, piv_out):
     return _check(lib().minnorm_get_factor(plan, _ptr(R_out), _ptr(piv_out)), "minnorm_get_factor")
+
+
+def minnorm_get_preconditioner(plan, W_out):
+    return _check(lib().minnorm_get_preconditioner(plan, _ptr(W_out)), "minnorm_get_preconditioner")
 
 
 def minnorm_cg_products(plan, A, w, q=None, t=None, lda=None):
