@@ -247,6 +247,8 @@ struct QrBlkWork {
   void *ppart = nullptr;                           // 2 x sms x 32 complex: a panel's posted slots
   void *rowb = nullptr;                            // 2 x 32 complex: a panel's posted rows
   GridBarrier *bar = nullptr;
+  cudaStream_t side = nullptr;                     // a panel's T, beside its adjoint product
+  cudaEvent_t ev_panel = nullptr, ev_t = nullptr;
 };
 // bytes of each buffer: sA, sB, sV, sZ, eA, eB, eV, eZ, part, W, Z, T, tau, Vb, R1, ppart, rowb, bar
 void qrblk_sizes(int64_t l, int64_t m, int sms, size_t (&bytes)[18]);

@@ -46,15 +46,16 @@ __device__ __forceinline__ zd sel_zd(bool p, zd a, zd b) { return {p ? a.re : b.
 // s = 1 / (alpha - beta) (v = (1, s x)):
 //     d_c = v^H P[j:, c] = P[j, c] + conj(s) g_c          (c > j),
 //     e_i = v_i^H v      = conj(V[j, i]) + s h_i          (i < j),
-// updates its rows, and in the same pass forms its slots for column j + 1. CTA 0 builds the
-// compact WY factor T (Schreiber and Van Loan; LAPACK's zlarft, forward and columnwise):
-// T[j, j] = tau_j, T[:j, j] = -tau_j T[:j, :j] e. The posted values are double-buffered
+// updates its rows, and in the same pass forms its slots for column j + 1. CTA 0 records
+// e (column j of E, the strictly upper part of V^H V) and tau_j, from which qr_t_kernel builds
+// the compact WY factor T off the panel's critical path. The posted values are double-buffered
 // by the parity of j, so one barrier per column separates every write from its reads.
 // Outputs: R's entries and the reflectors in P (beta on the diagonal), V (L x 32, unit
-// diagonal, zeros above; the columns past jb zero), T (32 x 32, column-major), tau.
+// diagonal, zeros above; the columns past jb zero), E (32 x 32, column-major; entries i < j
+// of column j), tau.
 // Dynamic shared memory: kPanelLd * ceil(L / G) complex entries.
 __global__ void __launch_bounds__(kPanelThreads)
-qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ldv, zd *__restrict__ T,
+qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ldv, zd *__restrict__ E,
                 zd *__restrict__ tau, zd *__restrict__ part, zd *__restrict__ rowb, GridBarrier *bar, int *err,
                 uint64_t limit_ns) {
   extern __shared__ zd s_P[];   // own rows, row-major with stride kPanelLd
@@ -62,7 +63,6 @@ qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ld
   __shared__ zd s_tot[kPanel];
   __shared__ zd s_row[kPanel];
   __shared__ zd s_d[kPanel];
-  __shared__ zd s_T[kPanel * kPanel];
   __shared__ double s_scal[5];   // beta, Re/Im tau, Re/Im s
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int r0 = (int)((int64_t)L * b / G), r1 = (int)((int64_t)L * (b + 1) / G);
@@ -72,8 +72,6 @@ qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ld
     const int c = e / nr, r = e - c * nr;
     s_P[r * kPanelLd + c] = c < jb ? ldcg(P + (int64_t)c * ld + r0 + r) : zd{0.0, 0.0};
   }
-  if (b == 0)
-    for (int e = tid; e < kPanel * kPanel; e += kPanelThreads) s_T[e] = {0.0, 0.0};
   __syncthreads();
   // the slots of column jn over the own rows r > jn, from the block as it stands; lane c
   // forms its slot branch-free (conj(a) b with a, b chosen by the lane's side of jn)
@@ -126,6 +124,10 @@ qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ld
       if (lane > j && lane < jb) dv = s_row[lane] + conjg(sc) * t;
       else if (lane < j) dv = conjg(s_row[lane]) + sc * t;
       s_d[lane] = dv;
+      if (b == 0) {
+        if (lane < j) E[j * kPanel + lane] = dv;   // e_lane = v_lane^H v_j
+        if (lane == 0) tau[j] = tj;
+      }
       if (lane == 0) {
         s_scal[0] = bt;
         s_scal[1] = tj.re;
@@ -137,18 +139,6 @@ qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ld
     __syncthreads();
     const zd tj = {s_scal[1], s_scal[2]};
     const zd sc = {s_scal[3], s_scal[4]};
-    // T column j (CTA 0): T[j, j] = tau_j, T[i, j] = -tau_j sum_{k=i..j-1} T[i, k] e_k
-    if (b == 0 && tid < kPanel) {
-      const int i = tid;
-      if (i < j) {
-        zd sum = {0.0, 0.0};
-        for (int k = i; k < j; ++k) mac(sum, s_T[k * kPanel + i], s_d[k]);
-        s_T[j * kPanel + i] = {-(tj.re * sum.re - tj.im * sum.im), -(tj.re * sum.im + tj.im * sum.re)};
-      } else if (i == j) {
-        s_T[j * kPanel + j] = tj;
-        tau[j] = tj;
-      }
-    }
     // the own rows r >= j: P[r, c] -= conj(tau) d_c v_r (c > j; the lanes past jb have d = 0),
     // column j becomes v (beta on the diagonal)
     const zd f = lane > j ? conjg(tj) * s_d[lane] : zd{0.0, 0.0};
@@ -182,8 +172,31 @@ qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ld
     if (c < jb) P[(int64_t)c * ld + gr] = p;
     V[(int64_t)c * ldv + gr] = c >= jb ? zd{0.0, 0.0} : gr > c ? p : gr == c ? zd{1.0, 0.0} : zd{0.0, 0.0};
   }
-  if (b == 0)
-    for (int e = tid; e < kPanel * kPanel; e += kPanelThreads) T[e] = s_T[e];
+}
+
+// The compact WY factor T of a panel from its E and tau, in place (column j of E is read before
+// column j of T is written; T 32 x 32 column-major, zero past jb): Schreiber and Van Loan's
+// recurrence (LAPACK's zlarft, forward and columnwise) T[j, j] = tau_j,
+// T[i, j] = -tau_j sum_{k=i..j-1} T[i, k] e_k. One warp, lane = row i.
+__global__ void __launch_bounds__(32)
+qr_t_kernel(zd *__restrict__ ET, const zd *__restrict__ tau, int jb) {
+  __shared__ zd sT[kPanel][kPanel + 1];   // sT[k][i] = T[i, k]
+  const int i = threadIdx.x;
+  for (int k = 0; k < kPanel; ++k) sT[k][i] = {0.0, 0.0};
+  __syncwarp();
+  for (int j = 0; j < jb; ++j) {
+    const zd tj = tau[j];
+    const zd e = i < j ? ET[j * kPanel + i] : zd{0.0, 0.0};
+    zd sum = {0.0, 0.0};
+    for (int k = 0; k < j; ++k) {
+      const zd ek = shfl_zd(e, k);
+      if (k >= i) mac(sum, sT[k][i], ek);
+    }
+    if (i < j) sT[j][i] = {-(tj.re * sum.re - tj.im * sum.im), -(tj.re * sum.im + tj.im * sum.re)};
+    else if (i == j) sT[j][i] = tj;
+    __syncwarp();
+  }
+  for (int k = 0; k < kPanel; ++k) ET[k * kPanel + i] = sT[k][i];
 }
 
 // Z = T^H W: Z[:, c] = T^H W[:, c], T 32 x 32 upper triangular (one thread per (row k, column c))
@@ -285,9 +298,17 @@ cudaError_t launch_qr_tall(QrBlkWork &w, const QrArgs &q, int sms, cudaStream_t 
     if (k0 + jb < m) {
       const int64_t cols = m - k0 - jb;
       zd *C = Y + (k0 + jb) * l + k0;
+      // T on the side stream while the adjoint product runs; Z = T^H W waits for it
+      if ((e = cudaEventRecord(w.ev_panel, st)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(w.side, w.ev_panel, 0)) != cudaSuccess) return e;
+      note_launch();
+      qr_t_kernel<<<1, 32, 0, w.side>>>(static_cast<zd *>(w.T), tau, jb);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(w.ev_t, w.side)) != cudaSuccess) return e;
       if ((e = launch_trailing_products(w, w.Vb, l, C, l, L, cols, nullptr, 0, w.W, q.err, q.limit_ns, st)) !=
           cudaSuccess)
         return e;
+      if ((e = cudaStreamWaitEvent(st, w.ev_t, 0)) != cudaSuccess) return e;
       note_launch();
       qr_tw_kernel<<<(unsigned)((cols * kPanel + 255) / 256), 256, 0, st>>>(
           static_cast<const zd *>(w.T), static_cast<const zd *>(w.W), static_cast<zd *>(w.Z), cols);

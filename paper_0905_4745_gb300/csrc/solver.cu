@@ -1459,6 +1459,9 @@ minnorm_status qrblk_alloc(minnorm_plan_t plan) {
   ALLOC(w.ppart, b[15]);
   ALLOC(w.rowb, b[16]);
   ALLOC(w.bar, b[17]);
+  if (cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking) != cudaSuccess) return MINNORM_ENOMEM;
+  if (cudaEventCreateWithFlags(&w.ev_panel, cudaEventDisableTiming) != cudaSuccess) return MINNORM_ENOMEM;
+  if (cudaEventCreateWithFlags(&w.ev_t, cudaEventDisableTiming) != cudaSuccess) return MINNORM_ENOMEM;
   plan->qb_ready = true;
   return MINNORM_OK;
 }
@@ -1958,6 +1961,12 @@ minnorm_status minnorm_plan_destroy(minnorm_plan_t plan) {
     cudaStreamDestroy(plan->st_copy);
     for (cudaEvent_t e : plan->ev_host) cudaEventDestroy(e);
   }
+  if (plan->qb.side) {
+    cudaStreamSynchronize(plan->qb.side);
+    cudaStreamDestroy(plan->qb.side);
+  }
+  if (plan->qb.ev_panel) cudaEventDestroy(plan->qb.ev_panel);
+  if (plan->qb.ev_t) cudaEventDestroy(plan->qb.ev_t);
   for (void *p : plan->allocs) cudaFree(p);
   for (cudaEvent_t e : plan->event_pool) cudaEventDestroy(e);
   if (plan->h_norms) cudaFreeHost(plan->h_norms);
