@@ -55,7 +55,8 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.0
 # (16.91 + 2.77 MB) + prinv_kernel<1> (2.14 MB + 0.5 KB); Y (16 MiB) stays in L2 through the QR,
 # so traffic is one read of Y.
 PROFILED_TRAFFIC = {("c2", 3): 21.82e6}
-KERNEL_CLASSES = {0: "cg_adjoint_product", 1: "cg_forward_product", 2: "exact_residual", 3: "pivoted_qr",
+# class 0: the CG's A^* w pass, or both products in one pass over A (mixed precision, 512 < m <= 4096)
+KERNEL_CLASSES = {0: "cg_product", 1: "cg_forward_product", 2: "exact_residual", 3: "pivoted_qr",
                   4: "srft_sketch", 5: "cg_fused", 6: "qrp_triangle", 7: "r_inverse"}
 # the blocked QR of tall sketches (l > 2048) does its trailing updates as FP64-accurate products on
 # the tensor cores: 43 (adjoint) and 34 (update) BF16 slice-pair products per FP64 multiply-add,
@@ -279,8 +280,8 @@ def class_amount(k, m, n, l, launches):
         return launches * 8.0 * m * m * (l - m / 3.0), "TFLOP/s", "tensor" if l > 2048 else "alu"
     if k == 6:             # the pivoted QR of the m x m triangle
         return launches * 16.0 * m ** 3 / 3.0, "TFLOP/s", "alu"
-    if k == 7:             # P R^-1
-        return launches * 8.0 * m ** 3 / 6.0, "TFLOP/s", "alu"
+    if k == 7:             # P R^-1: by blocks with tensor-core updates for the blocked QR's sketches
+        return launches * 8.0 * m ** 3 / 6.0, "TFLOP/s", "tensor" if l > 2048 and m >= 256 else "alu"
     return launches * (8.0 * m * n + 16.0 * l * m), "GB/s", "hbm"   # sketch: read A once, write Y
 
 
@@ -680,12 +681,14 @@ def main():
     # in chunks and the launches after the CG's test has fired return at once, so the launch count
     # overstates the passes (their few microseconds stay in the time: a conservative figure).
     cg_iters = sum(i["cg_iters"] for _, i in infos if i)
+    one_pass = stats[5][0] > 0 or (stats[0][0] > 0 and stats[1][0] == 0)
     if stats[5][0] > 0:     # fused CG: one pass over A per iteration
         cg_ms = stats[5][1] / max(1, cg_iters)
+    elif one_pass:          # both products in one pass over A per iteration
+        cg_ms = stats[0][1] / max(1, cg_iters)
     else:                   # separate A^* w and A q passes
         cg_ms = (stats[0][1] + stats[1][1]) / max(1, 2 * cg_iters)
-    # one pass over A per CG iteration for the fused kernel, two (A^* w, then A q) otherwise
-    cg_passes = 1 if stats[5][0] > 0 else 2
+    cg_passes = 1 if one_pass else 2
     cg_gbs = m * n * esz / (cg_ms / 1000.0) / 1e9 if cg_ms > 0 else None
     cg_roof = None
     if cg_gbs:

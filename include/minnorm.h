@@ -299,7 +299,11 @@ minnorm_status minnorm_get_preconditioner(minnorm_plan_t plan, void *W_out);
  * q = A^* w (w: m complex128 -> q: n complex128) and t = A q (t: m complex128).
  * In MINNORM_MIXED the products read the complex64 copy of A made by
  * minnorm_sketch and are computed in FP32; otherwise FP64. Either output
- * pointer may be NULL to skip it. Errors: ESTATE, EINVAL. */
+ * pointer may be NULL to skip it. With q NULL in MINNORM_MIXED and
+ * 512 < m <= 4096, t comes from the CG's one-pass form (A read once, by
+ * clusters of CTAs; an even lda and a 16-byte aligned A). Errors: ESTATE,
+ * EINVAL, ETIMEOUT (a load of the one-pass form did not arrive within the
+ * plan's wait limit; the plan is then usable only for destroy). */
 minnorm_status minnorm_cg_products(minnorm_plan_t plan, const void *A, int64_t lda,
                                    const void *w, void *q, void *t);
 
@@ -359,8 +363,9 @@ minnorm_status minnorm_plan_tuning(minnorm_plan_t plan, int32_t *x_chunks, int32
 int64_t minnorm_launch_count(void);
 
 /* Kernel timing since the last minnorm_sketch when the plan has
- * MINNORM_FLAG_TIMING: for kernel class k (0: CG product A^* w, 1: CG product
- * A q, 2: an exact residual (x = A^* y and b - A x), 3: the QR of Y (the
+ * MINNORM_FLAG_TIMING: for kernel class k (0: CG product A^* w, or both
+ * products in one pass over A for mixed-precision plans with 512 < m <= 4096,
+ * 1: CG product A q of the two-pass form, 2: an exact residual (x = A^* y and b - A x), 3: the QR of Y (the
  * pivoted QR when l <= 2048; for taller sketches the blocked QR without
  * pivoting), 4: sketch (both chains and the FFT), 5: fused CG solves, 6: the
  * pivoted QR of the m x m triangle (taller sketches only), 7: P R^{-1}) the

@@ -20,8 +20,11 @@
 // common.cuh); s and u of a CTA's rows stay in its registers, and dy = Wp u is
 // accumulated as the sum of alpha_k w_k by the owners of the rows of w. The
 // search direction p is kept, identically, in every CTA's shared memory.
+#include <cooperative_groups.h>
 #include <cuda.h>
 #include <cudaTypedefs.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -477,6 +480,216 @@ cg_fused_kernel(const __grid_constant__ CUtensorMap amap, const CgFusedParams P)
   }
 }
 
+
+// ---- one-pass CG product for 512 < m <= 4096 -------------------------------------
+// t = A (A^* w) and ||A^* w||^2 for one mixed-precision CG iteration, reading A (complex64)
+// from HBM once. A cluster of CL = ceil(m / 512) CTAs shares each 16-column sub-panel: CTA r
+// holds rows 512 r .. 512 r + 511 of it (two rows and eight columns per thread, the register
+// layout of cg_fused_kernel), brought into shared memory by 2-D TMA loads through a three-stage
+// mbarrier ring. Per sub-panel every CTA forms the partial q_j = sum_i conj(A_ij) w_i over its
+// rows, writes it into every CTA of the cluster (distributed shared memory, double-buffered by
+// the sub-panel's parity), meets the others at one cluster barrier, adds the CL partials in rank
+// order (so q is the same in every CTA) and accumulates t_i += sum_j A_ij q_j for its rows. The
+// clusters take every NC-th sub-panel, so the grid's reads sweep every row front to back
+// together; each cluster writes its partial t, added in FP64 by cg_pair_finish_kernel. Every
+// CTA of a cluster runs the same number of cluster barriers whatever happens (a load that does
+// not arrive within the wait limit turns the rest of the pass into zeros and reports the error),
+// so no CTA can be left waiting at one.
+// the cluster barrier in two halves (every thread of the cluster arrives, then waits)
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+constexpr int kPairRows = 2 * kBoxRows;   // rows per CTA
+constexpr int kPairMaxCluster = 8;
+constexpr int kPairStageBytes = kPairRows * 128;
+
+struct CgPairParams {
+  int m, n, nsub;        // rows, columns, 16-column sub-panels
+  const zf *w;           // m
+  zf *tpart;             // clusters x m
+  double *qq_part;       // clusters
+  int *err;
+  uint64_t limit_ns;
+  const int *skip;
+};
+
+__global__ void __launch_bounds__(kCgThreads, 1)
+cg_pair_kernel(const __grid_constant__ CUtensorMap amap, const CgPairParams P) {
+  namespace cgr = cooperative_groups;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ float xch[2][kPairMaxCluster][2 * kPanel];   // every rank's partial q, by parity
+  __shared__ float s_red[kCgThreads / 32][32];
+  __shared__ __align__(16) float q_f[2 * kPanel];
+  __shared__ zf th[kPairRows];
+  __shared__ uint64_t mbar[kStages];
+  // an asynchronous or finished CG: every CTA reads the same word, so the whole grid returns
+  if (P.skip && *P.skip) return;
+  cgr::cluster_group cl = cgr::this_cluster();
+  const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int NC = (int)(gridDim.x / CL), c = (int)(blockIdx.x / CL);
+  unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  auto stage = [&](int q) { return base + q * kPairStageBytes; };
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int r0 = rank * kPairRows;
+  const int nsp = P.nsub > c ? (P.nsub - c + NC - 1) / NC : 0;   // the same in every CTA of the cluster
+  if (tid == 0) {
+    for (int q = 0; q < kStages; ++q) mbar_init(&mbar[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const uint64_t pol = policy_evict_first();
+  uint32_t pending = 0;   // thread 0: bit q set while a load issued into stage q is not waited for
+  auto issue = [&](int e) {
+    const int sl = e % kStages;
+    mbar_expect_tx(&mbar[sl], (uint32_t)kPairStageBytes);
+    for (int bx = 0; bx < kPairRows / kBoxRows; ++bx)
+      tma_load_2d(stage(sl) + bx * kBoxRows * 128, &amap, (c + e * NC) * 2 * kPanel, r0 + bx * kBoxRows, &mbar[sl],
+                  pol);
+    pending |= 1u << sl;
+  };
+  if (tid == 0)
+    for (int e = 0; e < kStages && e < nsp; ++e) issue(e);
+  const int h = wid & 1, ra = 32 * (wid >> 1) + lane, rb = ra + kBoxRows;
+  const int ga = r0 + ra, gb = r0 + rb;
+  const zf w0 = ga < P.m ? P.w[ga] : zf{0.f, 0.f};
+  const zf w1 = gb < P.m ? P.w[gb] : zf{0.f, 0.f};
+  zf t0 = {0.f, 0.f}, t1 = {0.f, 0.f};
+  float qq_loc = 0.f;
+  uint32_t parity = 0;   // bit q: the parity of stage q's next phase, as this thread saw them complete
+  bool ok = true;
+  // Sub-panel e's partial q leaves for the peers before its t is formed: the cluster barrier of
+  // e stays open while the CTA reads sub-panel e + 1 and forms its partial (its registers are
+  // kept), and only then waits, adds the partials of e and updates t from e's registers.
+  float4 p0[4], p1[4];   // the registers of the sub-panel whose q is in flight
+  float pq = 0.f;        // warp 0: this CTA's partial q of the newest sub-panel
+  // (a) sub-panel e into registers (a0, a1), its partial q into s_red and, in warp 0, pq
+  auto take = [&](int e, float4 (&a0)[4], float4 (&a1)[4]) {
+    const int st = e % kStages;
+    bool w_ok = true;
+    if (ok) {
+      w_ok = mbar_wait(&mbar[st], (parity >> st) & 1u, P.limit_ns);
+      if (w_ok) parity ^= 1u << st;
+    }
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      a0[kc] = make_float4(0.f, 0.f, 0.f, 0.f);
+      a1[kc] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (ok && w_ok) {
+      const unsigned char *S = stage(st);
+      const int ch = 4 * h;
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc) {
+        a0[kc] = *reinterpret_cast<const float4 *>(S + ra * 128 + (((ch + kc) ^ (ra & 7)) << 4));
+        a1[kc] = *reinterpret_cast<const float4 *>(S + rb * 128 + (((ch + kc) ^ (rb & 7)) << 4));
+      }
+    }
+    float cq[16];
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      cq[4 * kc + 0] = fmaf(a0[kc].x, w0.re, fmaf(a0[kc].y, w0.im, fmaf(a1[kc].x, w1.re, a1[kc].y * w1.im)));
+      cq[4 * kc + 1] = fmaf(a0[kc].x, w0.im, fmaf(-a0[kc].y, w0.re, fmaf(a1[kc].x, w1.im, -a1[kc].y * w1.re)));
+      cq[4 * kc + 2] = fmaf(a0[kc].z, w0.re, fmaf(a0[kc].w, w0.im, fmaf(a1[kc].z, w1.re, a1[kc].w * w1.im)));
+      cq[4 * kc + 3] = fmaf(a0[kc].z, w0.im, fmaf(-a0[kc].w, w0.re, fmaf(a1[kc].z, w1.im, -a1[kc].w * w1.re)));
+    }
+    warp_transpose_sum16(cq, lane);
+    if (lane < 16) s_red[wid][lane] = cq[0];
+    // the stage is in registers everywhere and the warp sums are in place; a failed wait
+    // anywhere in the CTA ends its loads (the cluster barriers still run)
+    const bool was_ok = ok;
+    if (__syncthreads_or(ok && !w_ok)) ok = false;
+    if (tid == 0) {
+      if (was_ok && w_ok) pending &= ~(1u << st);   // thread 0 saw this stage's copy arrive
+      if (ok && e + kStages < nsp) issue(e + kStages);
+    }
+    if (wid == 0) {
+      float qf = 0.f;
+#pragma unroll
+      for (int w2 = 0; w2 < kCgThreads / 64; ++w2) qf += s_red[2 * w2 + (lane >> 4)][lane & 15];
+      pq = qf;
+    }
+  };
+  // (b) the partial of sub-panel e into every CTA of the cluster (after the barrier of e - 1:
+  // every peer has read that slot's previous contents, those of e - 2)
+  auto send = [&](int e) {
+    if (wid == 0)
+      for (int r = 0; r < CL; ++r) *cl.map_shared_rank(&xch[e & 1][rank][lane], r) = pq;
+  };
+  // (c) the total q of sub-panel e (after its barrier) and t from its registers
+  auto finish = [&](int e, const float4 (&a0)[4], const float4 (&a1)[4]) {
+    if (wid == 0) {
+      float qt = 0.f;
+      for (int r = 0; r < CL; ++r) qt += xch[e & 1][r][lane];
+      q_f[lane] = qt;
+      if (rank == 0 && (c + e * NC) * kPanel + (lane >> 1) < P.n) qq_loc = fmaf(qt, qt, qq_loc);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      const float4 q4 = *reinterpret_cast<const float4 *>(q_f + 16 * h + 4 * kc);
+      mac(t0, zf{a0[kc].x, a0[kc].y}, zf{q4.x, q4.y});
+      mac(t0, zf{a0[kc].z, a0[kc].w}, zf{q4.z, q4.w});
+      mac(t1, zf{a1[kc].x, a1[kc].y}, zf{q4.x, q4.y});
+      mac(t1, zf{a1[kc].z, a1[kc].w}, zf{q4.z, q4.w});
+    }
+  };
+  if (nsp > 0) {
+    take(0, p0, p1);
+    send(0);
+    cluster_arrive();
+    for (int e = 1; e < nsp; ++e) {
+      float4 a0[4], a1[4];
+      take(e, a0, a1);
+      cluster_wait();       // the partials of e - 1 are in place everywhere
+      send(e);
+      finish(e - 1, p0, p1);
+      cluster_arrive();
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc) {
+        p0[kc] = a0[kc];
+        p1[kc] = a1[kc];
+      }
+    }
+    cluster_wait();
+    finish(nsp - 1, p0, p1);
+  }
+  // the two column halves of a row meet in shared memory
+  if (h == 1) {
+    th[ra] = t0;
+    th[rb] = t1;
+  }
+  __syncthreads();
+  if (h == 0 && ok) {
+    if (ga < P.m) P.tpart[(int64_t)c * P.m + ga] = t0 + th[ra];
+    if (gb < P.m) P.tpart[(int64_t)c * P.m + gb] = t1 + th[rb];
+  }
+  if (rank == 0 && wid == 0) {  // only rank 0 accumulated |q|^2
+    qq_loc = warp_sum(qq_loc);
+    if (lane == 0) P.qq_part[c] = (double)qq_loc;
+  }
+  if (!ok && tid == 0) {
+    atomicExch(P.err, 1);
+    for (int q = 0; q < kStages; ++q)   // copies still in flight (bounded waits)
+      if ((pending >> q) & 1u) mbar_wait(&mbar[q], (parity >> q) & 1u, P.limit_ns);
+  }
+  cl.sync();   // no CTA leaves while a peer may still write into its shared memory
+}
+
+// t[i] = sum over the clusters of tpart[c][i], in FP64 and in cluster order
+__global__ void __launch_bounds__(256)
+cg_pair_finish_kernel(const zf *__restrict__ tpart, int nc, int m, zd *__restrict__ t, const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double re = 0.0, im = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    const zf v = tpart[(int64_t)c * m + i];
+    re += (double)v.re;
+    im += (double)v.im;
+  }
+  t[i] = {re, im};
+}
+
 // ---- host -------------------------------------------------------------------
 
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -565,6 +778,85 @@ cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st) {
   cfg.numAttrs = 1;
   note_launch();
   return cudaLaunchKernelEx(&cfg, cg_fused_kernel, map, P);
+}
+
+// ---- the one-pass product's launch ---------------------------------------------------
+bool cg_pair_supported(int64_t m, int64_t n, int64_t lda, const void *A) {
+  return m > kMaxFusedRows && m <= (int64_t)kPairRows * kPairMaxCluster && n >= kPanel && (lda % 2) == 0 &&
+         (((uintptr_t)A) & 15) == 0 && get_encode() != nullptr;
+}
+
+static size_t cg_pair_smem() { return 1024 + (size_t)kStages * kPairStageBytes; }
+static int cg_pair_cluster_size(int64_t m) { return (int)((m + kPairRows - 1) / kPairRows); }
+
+static cudaLaunchConfig_t cg_pair_config(int cl, int nc, cudaLaunchAttribute *attr, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(cl * nc));
+  cfg.blockDim = dim3(kCgThreads);
+  cfg.dynamicSmemBytes = cg_pair_smem();
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// clusters of the one-pass product: as many as are resident at once (one CTA per SM), at most
+// one per sub-panel; 0 when the cluster shape cannot be launched
+int cg_pair_clusters(int64_t m, int64_t n) {
+  if (m <= kMaxFusedRows || m > (int64_t)kPairRows * kPairMaxCluster) return 0;
+  if (cudaFuncSetAttribute(cg_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cg_pair_smem()) !=
+      cudaSuccess)
+    return 0;
+  const int cl = cg_pair_cluster_size(m);
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = cg_pair_config(cl, 1, attr, nullptr);
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, cg_pair_kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int64_t nsub = (n + kPanel - 1) / kPanel;
+  return (int)std::min<int64_t>(nc, nsub);
+}
+
+cudaError_t launch_cg_pair(const CgPairArgs &a, cudaStream_t st) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+  if (!enc || a.nc < 1) return cudaErrorNotSupported;
+  CUtensorMap map;
+  // A as a 2-D array of floats: dim0 = 2n (re, im interleaved), dim1 = m rows
+  const cuuint64_t gdim[2] = {(cuuint64_t)(2 * a.n), (cuuint64_t)a.m};
+  const cuuint64_t gstride[1] = {(cuuint64_t)(a.lda * sizeof(zf))};
+  const cuuint32_t box[2] = {2 * kPanel, kBoxRows};
+  const cuuint32_t estride[2] = {1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(a.A), gdim, gstride, box,
+                   estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  CgPairParams P;
+  P.m = (int)a.m;
+  P.n = (int)a.n;
+  P.nsub = (int)((a.n + kPanel - 1) / kPanel);
+  P.w = (const zf *)a.w32;
+  P.tpart = (zf *)a.tpart;
+  P.qq_part = a.qq_part;
+  P.err = a.err;
+  P.limit_ns = a.limit_ns;
+  P.skip = a.skip;
+  cudaError_t e = cudaFuncSetAttribute(cg_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)cg_pair_smem());
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = cg_pair_config(cg_pair_cluster_size(a.m), a.nc, attr, st);
+  note_launch();
+  if ((e = cudaLaunchKernelEx(&cfg, cg_pair_kernel, map, P)) != cudaSuccess) return e;
+  note_launch();
+  cg_pair_finish_kernel<<<(unsigned)((a.m + 255) / 256), 256, 0, st>>>((const zf *)a.tpart, a.nc, (int)a.m,
+                                                                       (zd *)a.t, a.skip);
+  return cudaGetLastError();
 }
 
 }  // namespace mn

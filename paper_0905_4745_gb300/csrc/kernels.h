@@ -172,6 +172,23 @@ struct CgFusedArgs {
 };
 bool cg_fused_supported(int64_t m, int64_t n, int64_t lda, const void *A);
 cudaError_t launch_cg_fused(const CgFusedArgs &a, cudaStream_t st);
+// One pass over A per mixed-precision CG iteration for 512 < m <= 4096: t = A (A^* w) (m complex128)
+// and the partial sums of ||A^* w||^2 (one per cluster), by clusters of ceil(m / 512) CTAs
+struct CgPairArgs {
+  const void *A;          // complex64, row-major m x n, leading dimension lda (even, 16-byte aligned)
+  int64_t lda, m, n;
+  const void *w32;        // m complex64
+  void *t;                // m complex128
+  void *tpart;            // nc x m complex64
+  double *qq_part;        // nc
+  int nc;                 // clusters (cg_pair_clusters)
+  int *err;
+  uint64_t limit_ns;
+  const int *skip;        // returns at once when *skip != 0
+};
+bool cg_pair_supported(int64_t m, int64_t n, int64_t lda, const void *A);
+int cg_pair_clusters(int64_t m, int64_t n);
+cudaError_t launch_cg_pair(const CgPairArgs &a, cudaStream_t st);
 
 // ---- ozaki.cu ----------------------------------------------------------------------
 // FP64-accurate complex products on the tensor cores (the trailing updates of the blocked

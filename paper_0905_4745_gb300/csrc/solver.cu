@@ -159,6 +159,7 @@ struct minnorm_plan_s {
   bool cg_tuned = false;
   // fused CG (mixed precision, m <= 512)
   bool fused_ok = false;
+  int pair_nc = 0;           // clusters of the one-pass CG product (mixed, 512 < m <= 4096), 0: two passes
   zf *d_tpart = nullptr;
   double *d_qqp = nullptr, *d_ggp = nullptr;
   // host staging (minnorm_solve_host): A arrives in row blocks on a copy stream
@@ -630,6 +631,9 @@ minnorm_status create_impl(minnorm_plan_t plan, int64_t m, int64_t n, int64_t l,
     ALLOC(plan->d_tpart, sizeof(zf) * (size_t)plan->sms * m);
     ALLOC(plan->d_qqp, sizeof(double) * plan->sms);
     ALLOC(plan->d_ggp, sizeof(double) * plan->sms);
+  } else if (plan->fp32 && (plan->pair_nc = cg_pair_clusters(m, n)) > 0) {
+    ALLOC(plan->d_tpart, sizeof(zf) * (size_t)plan->pair_nc * m);
+    ALLOC(plan->d_qqp, sizeof(double) * plan->pair_nc);
   }
   // Step 2 for tall sketches: the blocked QR with tensor-core trailing updates (its workspace now)
   plan->qr_blocked = l > kQrBlockedMinRows && !plan->pool && qrblk_panel_grid(l, plan->sms) > 0;
@@ -953,6 +957,7 @@ minnorm_status tune_cg_keep(minnorm_plan_t plan, CgFusedArgs a) {
 // ---- Steps 3-5 --------------------------------------------------------------
 // Inner solve: CG on (Wp^* A A^* Wp) du = g, Wp = P R^{-1}; dy = Wp du.
 minnorm_status enqueue_cg_iters(minnorm_plan_t plan, const void *Acg, double tol, int k);
+static bool cg_pair_on(minnorm_plan_t plan, const void *Acg);
 
 minnorm_status inner_cg(minnorm_plan_t plan, const void *Acg, double tol, int maxit, int *iters) {
   cudaStream_t st = plan->st;
@@ -1009,14 +1014,21 @@ minnorm_status inner_cg(minnorm_plan_t plan, const void *Acg, double tol, int ma
   }
   CK(launch_cg_init(m, plan->d_g, plan->d_u, plan->d_s, plan->d_p, plan->d_cg, st));
   const int chunk = plan->fp32 ? 4 : 8;
-  int it = 0;
+  const bool pair = cg_pair_on(plan, Acg);   // its loads' waits are bounded: their error word
+  if (pair) CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
+  int it = 0, err = 0;
   while (it < maxit) {
     const int todo = std::min(chunk, maxit - it);
     minnorm_status cs = enqueue_cg_iters(plan, Acg, tol, todo);
     if (cs != MINNORM_OK) return cs;
     it += todo;
     CK(cudaMemcpyAsync(plan->h_cg, plan->d_cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    if (pair) CK(cudaMemcpyAsync(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (err) {
+      plan->failed = true;
+      return MINNORM_ETIMEOUT;
+    }
     if (plan->h_cg->done) break;
   }
   *iters = plan->h_cg->iters;
@@ -1235,12 +1247,24 @@ minnorm_status solve_impl(minnorm_plan_t plan, const void *A, int64_t lda, const
 // plan that has not yet run a synchronous solve uses the default work splits. The status, the
 // step counts and the bound stay on the device until minnorm_solve_wait.
 // k iterations of the two-pass CG (each kernel returns once the CG's test has fired)
+// the one-pass product serves this plan's mixed CG (A's layout permitting)
+static bool cg_pair_on(minnorm_plan_t plan, const void *Acg) {
+  return plan->fp32 && plan->pair_nc > 0 && cg_pair_supported(plan->m, plan->n, plan->g_cg.ld, Acg);
+}
+
 minnorm_status enqueue_cg_iters(minnorm_plan_t plan, const void *Acg, double tol, int k) {
   cudaStream_t st = plan->st;
   const int *done = &plan->d_cg->done;
   const int mi = (int)plan->m;
+  const bool pair = cg_pair_on(plan, Acg);
   for (int i = 0; i < k; ++i) {
-    if (plan->fp32) {
+    if (pair) {
+      CK(launch_small_gemv(plan->d_Wp, mi, plan->d_p, plan->d_w, plan->d_w32, done, st));
+      CgPairArgs pa{Acg, plan->g_cg.ld, plan->m, plan->n, plan->d_w32, plan->d_t, plan->d_tpart, plan->d_qqp,
+                    plan->pair_nc, plan->d_err, plan->wait_limit_ns, done};
+      Timed tm(plan, 0);
+      CK(launch_cg_pair(pa, st));
+    } else if (plan->fp32) {
       CK(launch_small_gemv(plan->d_Wp, mi, plan->d_p, plan->d_w, plan->d_w32, done, st));
       { Timed tm(plan, 0); CK(launch_gemv_adj_f32(plan->g_cg, Acg, plan->d_w32, plan->d_q, plan->d_part, plan->d_qq, done, st)); }
       { Timed tm(plan, 1); CK(launch_gemv_fwd_f32(plan->g_cg, Acg, plan->d_q, plan->d_t, plan->d_part, done, st)); }
@@ -1250,8 +1274,8 @@ minnorm_status enqueue_cg_iters(minnorm_plan_t plan, const void *Acg, double tol
       { Timed tm(plan, 1); CK(launch_gemv_fwd(plan->g_cg, Acg, plan->d_q, plan->d_t, plan->d_part, done, st)); }
     }
     CK(launch_small_gemv(plan->d_WpH, mi, plan->d_t, plan->d_np, nullptr, done, st));
-    CK(launch_cg_update(mi, plan->d_qq, plan->nqq, plan->d_np, plan->d_u, plan->d_s, plan->d_p, plan->d_cg, tol * tol,
-                        st));
+    CK(launch_cg_update(mi, pair ? plan->d_qqp : plan->d_qq, pair ? plan->pair_nc : plan->nqq, plan->d_np, plan->d_u,
+                        plan->d_s, plan->d_p, plan->d_cg, tol * tol, st));
   }
   return MINNORM_OK;
 }
@@ -2036,6 +2060,21 @@ minnorm_status minnorm_cg_products(minnorm_plan_t plan, const void *A, int64_t l
   cudaStream_t st = plan->st;
   const int64_t m = plan->m, n = plan->n;
   const void *Acg = plan->d_A32 ? (const void *)plan->d_A32 : A;
+  if (!q && t && cg_pair_on(plan, Acg)) {   // t alone: the CG's one-pass form
+    CK(launch_narrow(m, w, plan->d_w32, st));
+    CK(cudaMemsetAsync(plan->d_err, 0, sizeof(int), st));
+    CgPairArgs pa{Acg, plan->g_cg.ld, m, n, plan->d_w32, t, plan->d_tpart, plan->d_qqp, plan->pair_nc, plan->d_err,
+                  plan->wait_limit_ns, nullptr};
+    CK(launch_cg_pair(pa, st));
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err) {
+      plan->failed = true;
+      return MINNORM_ETIMEOUT;
+    }
+    return MINNORM_OK;
+  }
   if (plan->fp32) {
     CK(launch_narrow(m, w, plan->d_w32, st));
     CK(launch_gemv_adj_f32(plan->g_cg, Acg, plan->d_w32, plan->d_q, plan->d_part, plan->d_qq, nullptr, st));

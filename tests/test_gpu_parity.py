@@ -258,6 +258,35 @@ def test_cg_products_match_oracle(mn, m, n, prec, dtype, pad):
     assert _rel(t, oracle.matvec(A64, q)) <= tol
 
 
+# The mixed CG's one-pass product for 512 < m <= 4096 (clusters of ceil(m / 512) CTAs, the
+# partial q of each CTA's rows added through distributed shared memory): t = A (A^* w) against the
+# oracle's FP64 products. Its FP32 sums run over at most a few thousand terms per thread, so the
+# error is held to 2e-5 of |A| (|A|^H |w|), the scale of every rounding in them; a lost sub-panel,
+# row block or rank would be off by O(1) of it. Cluster sizes 2, 3 and 4 with ragged row blocks
+# (700 = 512 + 188, 1100 = 2 x 512 + 76), and a ragged last 16-column sub-panel (n = 8200).
+@pytest.mark.parametrize("m,n", [(700, 8192), (1100, 16384), (2048, 8200)])
+def test_cg_one_pass_product_matches_oracle(mn, m, n):
+    import torch
+    s = synth.make_system(m, n, exponent=3, seed=900 + m, dtype="c64")
+    A64 = s.A.astype(np.complex128)
+    rng = np.random.default_rng(m)
+    w = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+    plan = _plan(mn, m, n, 1, seed=2, dtype=mn.C64)
+    try:
+        A = _t(s.A)
+        mn.minnorm_sketch(plan, A)
+        t = torch.empty(m, dtype=torch.complex128, device=_dev())
+        mn.minnorm_cg_products(plan, A, _t(w), None, t)
+        torch.cuda.synchronize()
+        t = t.cpu().numpy()
+    finally:
+        mn.minnorm_plan_destroy(plan)
+    w32 = w.astype(np.complex64).astype(np.complex128)      # the kernel's w is complex64
+    tref = oracle.matvec(A64, oracle.adj_matvec(A64, w32))
+    scale = np.abs(A64) @ (np.abs(A64).T @ np.abs(w32))
+    assert np.linalg.norm(t - tref) <= 2e-5 * np.linalg.norm(scale), (np.linalg.norm(t - tref), np.linalg.norm(scale))
+
+
 @pytest.mark.parametrize("m,n,dtype", [(24, 4096, "c128"), (128, 65536, "c128"), (50, 8192, "c64")])
 def test_residual_dd_matches_oracle(mn, m, n, dtype):
     import torch
