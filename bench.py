@@ -285,6 +285,23 @@ def class_amount(k, m, n, l, launches):
     return launches * (8.0 * m * n + 16.0 * l * m), "GB/s", "hbm"   # sketch: read A once, write Y
 
 
+def cg_pass_time(stats, cg_iters):
+    """Milliseconds per pass over A of the CG and passes per iteration, from the kernel classes'
+    (launches, ms) and the CG iterations the solves report: the fused solve (class 5) and the one-pass
+    product (class 0 alone) read A once per iteration, the two-pass form (classes 0 and 1) twice. The
+    two-pass and one-pass forms enqueue their iterations in chunks, and the launches after the CG's test
+    has fired return at once: the iterations, not the launches, count the passes (those launches' few
+    microseconds stay in the time, so the figure is conservative)."""
+    one_pass = stats[5][0] > 0 or (stats[0][0] > 0 and stats[1][0] == 0)
+    if stats[5][0] > 0:
+        ms = stats[5][1] / max(1, cg_iters)
+    elif one_pass:
+        ms = stats[0][1] / max(1, cg_iters)
+    else:
+        ms = (stats[0][1] + stats[1][1]) / max(1, 2 * cg_iters)
+    return ms, (1 if one_pass else 2)
+
+
 def side_roofline(shapes, stats_of, pk):
     """Roofline of the dominant kernel class over the last step: stats_of(i, k) -> (launches, ms)
     for system i; shapes: (m, n) per system."""
@@ -681,14 +698,7 @@ def main():
     # in chunks and the launches after the CG's test has fired return at once, so the launch count
     # overstates the passes (their few microseconds stay in the time: a conservative figure).
     cg_iters = sum(i["cg_iters"] for _, i in infos if i)
-    one_pass = stats[5][0] > 0 or (stats[0][0] > 0 and stats[1][0] == 0)
-    if stats[5][0] > 0:     # fused CG: one pass over A per iteration
-        cg_ms = stats[5][1] / max(1, cg_iters)
-    elif one_pass:          # both products in one pass over A per iteration
-        cg_ms = stats[0][1] / max(1, cg_iters)
-    else:                   # separate A^* w and A q passes
-        cg_ms = (stats[0][1] + stats[1][1]) / max(1, 2 * cg_iters)
-    cg_passes = 1 if one_pass else 2
+    cg_ms, cg_passes = cg_pass_time(stats, cg_iters)
     cg_gbs = m * n * esz / (cg_ms / 1000.0) / 1e9 if cg_ms > 0 else None
     cg_roof = None
     if cg_gbs:

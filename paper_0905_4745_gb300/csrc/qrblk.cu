@@ -60,7 +60,6 @@ qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ld
                 uint64_t limit_ns) {
   extern __shared__ zd s_P[];   // own rows, row-major with stride kPanelLd
   __shared__ zd s_acc[kPanelWarps][kPanel];
-  __shared__ zd s_tot[kPanel];
   __shared__ zd s_row[kPanel];
   __shared__ zd s_d[kPanel];
   __shared__ double s_scal[5];   // beta, Re/Im tau, Re/Im s
@@ -107,7 +106,6 @@ qr_panel_kernel(zd *P, int64_t ld, int L, int jb, zd *__restrict__ V, int64_t ld
     if (wid == 0) {
       zd t = {0.0, 0.0};
       for (int w = 0; w < kPanelWarps; ++w) t = t + s_acc[w][lane];
-      s_tot[lane] = t;
       // the reflector of column j (the same arithmetic in every CTA)
       const zd alpha = s_row[j];
       const double xn2 = __shfl_sync(0xffffffffu, t.re, j);

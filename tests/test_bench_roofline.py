@@ -53,3 +53,19 @@ def test_aggregate_and_batch_cost():
     import bench
     assert bench.aggregate_value(4, 10, 2000.0) == pytest.approx(20.0)    # 40 solves in 2 s
     assert bench.batch_cost(2, 10) == 8 + 40
+
+
+def test_cg_pass_time_counts_iterations_not_launches():
+    import bench
+    empty = {k: (0, 0.0) for k in range(8)}
+    # two passes: 48 launches of each product for 39 iterations (9 returned at once after the test fired)
+    st = {**empty, 0: (48, 24.2), 1: (48, 24.8)}
+    assert bench.cg_pass_time(st, 39) == (pytest.approx((24.2 + 24.8) / 78), 2)
+    # one pass (class 0 alone): 48 launches for 39 iterations
+    st = {**empty, 0: (48, 41.3)}
+    assert bench.cg_pass_time(st, 39) == (pytest.approx(41.3 / 39), 1)
+    # the fused solve (class 5 counts its iterations)
+    st = {**empty, 5: (61, 3.5)}
+    assert bench.cg_pass_time(st, 61) == (pytest.approx(3.5 / 61), 1)
+    # no CG run: no time
+    assert bench.cg_pass_time(empty, 0) == (0.0, 2)
